@@ -1,0 +1,295 @@
+"""Plain CPU oracle for the mixed-precision Gaussian log-likelihood.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this
+module: only the tests, the package smoke check and the CPU-baseline leg of
+the benchmark use it.  It shares no code with the CUDA path (the seeded input
+draws come from a separate module that holds none of the arithmetic below).
+
+Everything is float64 unless a step of Algorithm 1 fixes single precision.
+Library primitives (LAPACK's potrf and triangular solves through scipy,
+BLAS matrix products through numpy, the modified Bessel function K_nu from
+scipy.special) serve as steps; there is no blocking, fusion or reordering
+beyond what the paper's definitions and Algorithm 1 state.
+
+Paper: Abdulah, Ltaief, Sun, Genton, Keyes, "Geostatistical Modeling and
+Prediction Using Mixed-Precision Tile Cholesky Factorization" (2019).
+
+Function -> paper passage -> what pins it (tests/test_oracle_pins.py):
+  morton_keys / morton_order   "appropriate ordering" (Section IV, mixed-
+                               precision Cholesky); Z-order reading    hand-worked
+                                                                        keys, 2x2 grid
+  matern                       Eq. 1                                    closed forms
+                                                                        nu=1/2,3/2,5/2,
+                                                                        mpmath K_nu,
+                                                                        quadrature, r->0
+  covariance                   Eq. 1 with Sigma_ij = C(||s_i-s_j||)     symmetry, diag
+  loglik_dense                 Eq. 2                                    n<=8 exact
+                                                                        rational det and
+                                                                        solve; 1D Markov
+                                                                        closed form;
+                                                                        Sigma=I; sigma2
+                                                                        scaling
+  mp_tile_cholesky             Algorithm 1                              band=p equals the
+                                                                        dense factor;
+                                                                        Fig. 2 op trace
+  loglik_mp                    Eq. 2 on the Algorithm 1 factor          within FP32-level
+                                                                        error of dense
+  krige                        prediction (Section VI-B); simple        interpolation at
+                               kriging reading                          observed points
+  profile_sigma2               Eq. 3 and theta1_opt = Z'S~^-1 Z / n     argmax of Eq. 2
+                                                                        over theta1
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.special as sps
+
+__all__ = [
+    "morton_keys", "morton_order", "matern", "covariance", "loglik_dense",
+    "dense_factor", "mp_tile_cholesky", "loglik_mp", "factor_logdet_quad",
+    "krige", "profile_sigma2", "Theta", "tile_is_dp",
+]
+
+LOG_2PI = math.log(2.0 * math.pi)
+
+
+@dataclass(frozen=True)
+class Theta:
+    """theta1 (variance sigma2), theta2 (range beta), theta3 (smoothness nu) of Eq. 1,
+    plus a nugget tau2 added to the diagonal (reading: Sigma + tau2 I)."""
+    sigma2: float
+    beta: float
+    nu: float
+    nugget: float = 0.0
+
+
+# ---------------------------------------------------------------- ordering ---
+def morton_keys(x, y):
+    """Z-order key of each location (reading of the paper's 'appropriate ordering').
+
+    Each coordinate c in [0,1] is quantised to q = clamp(floor(c * 2^16), 0, 2^16-1);
+    the key interleaves the 16 bits of qx (even bit positions) with those of qy
+    (odd bit positions).  Bit by bit, plainly.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    keys = np.empty(x.shape[0], dtype=np.uint64)
+    for idx in range(x.shape[0]):
+        qx = min(max(int(math.floor(x[idx] * 65536.0)), 0), 65535)
+        qy = min(max(int(math.floor(y[idx] * 65536.0)), 0), 65535)
+        k = 0
+        for b in range(16):
+            k |= ((qx >> b) & 1) << (2 * b)
+            k |= ((qy >> b) & 1) << (2 * b + 1)
+        keys[idx] = k
+    return keys
+
+
+def morton_order(x, y):
+    """Permutation perm (new position -> old index) sorting by (key, old index)."""
+    keys = morton_keys(x, y)
+    return np.array(sorted(range(len(keys)), key=lambda i: (int(keys[i]), i)), dtype=np.int64)
+
+
+# ------------------------------------------------------------------ Eq. 1 ---
+def matern(r, sigma2, beta, nu):
+    """Eq. 1: C(r) = theta1 / (2^(theta3-1) Gamma(theta3)) (r/theta2)^theta3 K_theta3(r/theta2).
+
+    C(0) = theta1 (the limit of x^nu K_nu(x) at 0 is 2^(nu-1) Gamma(nu)); where
+    K_nu underflows to 0 the product is 0.
+    """
+    r = np.asarray(r, dtype=np.float64)
+    xr = r / beta
+    out = np.empty_like(xr)
+    zero = xr == 0.0
+    xs = xr[~zero]
+    kv = sps.kv(nu, xs)
+    with np.errstate(invalid="ignore", over="ignore"):
+        val = sigma2 / (2.0 ** (nu - 1.0) * sps.gamma(nu)) * np.power(xs, nu) * kv
+    val = np.where(kv == 0.0, 0.0, val)
+    out[~zero] = val
+    out[zero] = sigma2
+    return out
+
+
+def covariance(xa, ya, xb=None, yb=None, theta: Theta = None):
+    """Sigma_ab = C(||s_a - s_b||_2) by Eq. 1.  With one set of points the
+    nugget is added on the diagonal (a == b); a cross-covariance gets none."""
+    xa = np.asarray(xa, dtype=np.float64)
+    ya = np.asarray(ya, dtype=np.float64)
+    same = xb is None
+    if same:
+        xb, yb = xa, ya
+    dx = xa[:, None] - np.asarray(xb, dtype=np.float64)[None, :]
+    dy = ya[:, None] - np.asarray(yb, dtype=np.float64)[None, :]
+    r = np.sqrt(dx * dx + dy * dy)
+    S = matern(r, theta.sigma2, theta.beta, theta.nu)
+    if same:
+        S[np.diag_indices_from(S)] = theta.sigma2 + theta.nugget
+    return S
+
+
+# ------------------------------------------------------------------ Eq. 2 ---
+def dense_factor(S):
+    """Lower Cholesky factor by LAPACK dpotrf; info>0 is the 1-based order of
+    the first leading minor that is not positive definite."""
+    c, info = sla.lapack.dpotrf(np.asarray(S, dtype=np.float64), lower=1, clean=1)
+    return np.tril(c), int(info)
+
+
+def factor_logdet_quad(L, z):
+    """log|Sigma| = 2 sum log L_ii and Q = Z' Sigma^-1 Z = ||L^-1 Z||^2 (Eq. 2)."""
+    d = np.diag(L)
+    logdet = 2.0 * math.fsum(np.log(d).tolist())
+    yv = sla.solve_triangular(L, np.asarray(z, dtype=np.float64), lower=True)
+    quad = math.fsum((yv * yv).tolist())
+    return logdet, quad
+
+
+def _assemble(n, logdet, quad):
+    return -0.5 * n * LOG_2PI - 0.5 * logdet - 0.5 * quad
+
+
+def loglik_dense(x, y, z, theta: Theta):
+    """Eq. 2 in float64 on the dense covariance: l = -n/2 log 2pi - 1/2 log|S| - 1/2 Z'S^-1 Z."""
+    n = len(z)
+    S = covariance(x, y, theta=theta)
+    L, info = dense_factor(S)
+    if info != 0:
+        return dict(loglik=float("nan"), logdet=float("nan"), quad=float("nan"), info=info)
+    logdet, quad = factor_logdet_quad(L, z)
+    return dict(loglik=_assemble(n, logdet, quad), logdet=logdet, quad=quad, info=0)
+
+
+# ------------------------------------------------------------ Algorithm 1 ---
+def tile_is_dp(i, j, band):
+    """Precision map of Algorithm 1: lower tile (i, j), i >= j, is double
+    precision iff it lies within `band` (diag_thick) tiles of the diagonal."""
+    return abs(i - j) < band
+
+
+def mp_tile_cholesky(A, nb, band, trace=None):
+    """Algorithm 1 (mixed-precision tile Cholesky, lower case) on a dense SPD A.
+
+    Readings of the printed algorithm: the undefined `m` in the two precision
+    tests stands for the row index of the tile being written ((i,k) for the
+    triangular solve, (i,j) for the update), the loop bound `r` is p, and
+    diag_thick = `band` >= 1.  A is padded to p*nb with an identity block
+    (decoupled rows change neither log|A| nor the solve).  Single-precision
+    tiles keep only their float32 copy: after a strsm the double copy is the
+    exact promotion of the float32 result (sconv2d), so no information lives
+    in it beyond the float32 value.
+
+    Returns (L, info): L dense float64 (n x n, lower) with single-precision
+    tiles promoted exactly; info = 1-based global row of the first failing
+    pivot, 0 on success.  `trace`, if a list, receives (op, i, j, k) tuples
+    in execution order, op in {dpotrf, dtrsm, strsm, dsyrk, dconv2s, dgemm, sgemm}.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    p = -(-n // nb)
+    npad = p * nb
+    Ap = np.eye(npad, dtype=np.float64)
+    Ap[:n, :n] = A
+    T = {}
+    # lines 2-6: off-band tiles go to single precision (dlag2s)
+    for j in range(p):
+        for i in range(j, p):
+            blk = Ap[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb]
+            T[(i, j)] = blk.copy() if tile_is_dp(i, j, band) else blk.astype(np.float32)
+    S = {}  # single-precision copies of in-band panel tiles (line 21, dconv2s)
+
+    def rec(*t):
+        if trace is not None:
+            trace.append(t)
+
+    for k in range(p):
+        # line 8: dpotrf
+        c, info = sla.lapack.dpotrf(T[(k, k)], lower=1, clean=1)
+        rec("dpotrf", k, k, k)
+        if info != 0:
+            return None, k * nb + int(info)
+        Lkk = np.tril(c)
+        T[(k, k)] = Lkk
+        tmp = Lkk.astype(np.float32)  # line 9: tmp_0k <- dlag2s(A_kk)
+        # lines 10-17: triangular solves of column k
+        for i in range(k + 1, p):
+            if tile_is_dp(i, k, band):
+                T[(i, k)] = sla.solve_triangular(Lkk, T[(i, k)].T, lower=True).T
+                rec("dtrsm", i, k, k)
+            else:
+                T[(i, k)] = sla.solve_triangular(tmp, T[(i, k)].T, lower=True).T.astype(np.float32)
+                rec("strsm", i, k, k)
+        # lines 18-31: updates of the trailing matrix
+        for j in range(k + 1, p):
+            Ajk = T[(j, k)].astype(np.float64)
+            T[(j, j)] = T[(j, j)] - Ajk @ Ajk.T
+            rec("dsyrk", j, j, k)
+            if tile_is_dp(j, k, band):
+                S[(j, k)] = T[(j, k)].astype(np.float32)
+                rec("dconv2s", j, k, k)
+            for i in range(j + 1, p):
+                if tile_is_dp(i, j, band):
+                    Aik = T[(i, k)].astype(np.float64)
+                    T[(i, j)] = T[(i, j)] - Aik @ Ajk.T
+                    rec("dgemm", i, j, k)
+                else:
+                    Aik_s = T[(i, k)]  # off-band whenever (i, j) is off-band
+                    Ajk_s = S[(j, k)] if tile_is_dp(j, k, band) else T[(j, k)]
+                    T[(i, j)] = (T[(i, j)] - np.matmul(Aik_s, Ajk_s.T)).astype(np.float32)
+                    rec("sgemm", i, j, k)
+    L = np.zeros((npad, npad), dtype=np.float64)
+    for (i, j), blk in T.items():
+        L[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb] = blk.astype(np.float64)
+    return L[:n, :n], 0
+
+
+def loglik_mp(x, y, z, theta: Theta, nb, band):
+    """Eq. 2 with the covariance factored by Algorithm 1 (float64 log-det and solve)."""
+    n = len(z)
+    S = covariance(x, y, theta=theta)
+    L, info = mp_tile_cholesky(S, nb, band)
+    if info != 0:
+        return dict(loglik=float("nan"), logdet=float("nan"), quad=float("nan"), info=info)
+    logdet, quad = factor_logdet_quad(L, z)
+    return dict(loglik=_assemble(n, logdet, quad), logdet=logdet, quad=quad, info=0)
+
+
+# --------------------------------------------------------------- kriging ---
+def krige(xo, yo, z, theta: Theta, xn, yn):
+    """Simple (zero-mean) kriging predictor Z_new = Sigma_new,obs Sigma_obs^-1 Z.
+
+    The paper predicts missing values with the fitted model and scores them by
+    the prediction mean square error without printing the predictor; this is
+    the reading used.  Sigma_obs^-1 Z is formed by the two triangular solves
+    with the float64 factor.
+    """
+    S = covariance(xo, yo, theta=theta)
+    L, info = dense_factor(S)
+    if info != 0:
+        raise np.linalg.LinAlgError(f"covariance not positive definite (info={info})")
+    yv = sla.solve_triangular(L, np.asarray(z, dtype=np.float64), lower=True)
+    alpha = sla.solve_triangular(L.T, yv, lower=False)
+    C = covariance(xn, yn, xo, yo, theta=theta)
+    return C @ alpha
+
+
+# ------------------------------------------------------- profile (Eq. 3) ---
+def profile_sigma2(x, y, z, beta, nu, nugget_ratio=0.0):
+    """theta1_opt = Z' S~^-1 Z / n with S~ the covariance at unit variance
+    (Eq. 3 and the expression for theta1 following it).  Returns
+    (theta1_opt, profile loglik) where the profile loglik is Eq. 2 at theta1_opt,
+    i.e. -n/2 log 2pi - n/2 - n/2 log(Q/n) - 1/2 log|S~| (reading of the garbled
+    Eq. 3: its quadratic term at the optimum equals n)."""
+    n = len(z)
+    th = Theta(1.0, beta, nu, nugget_ratio)
+    S = covariance(x, y, theta=th)
+    L, info = dense_factor(S)
+    logdet, quad = factor_logdet_quad(L, z)
+    s2 = quad / n
+    prof = -0.5 * n * LOG_2PI - 0.5 * n - 0.5 * n * math.log(s2) - 0.5 * logdet
+    return s2, prof

@@ -1,0 +1,313 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's formula or re-calls its library routine
+as the reference: each compares against an independent closed form, an
+independent implementation (mpmath, exact rational arithmetic, quadrature),
+an invariant, or a hand-written trace of Algorithm 1.
+"""
+import math
+import os
+from fractions import Fraction
+from itertools import permutations
+
+import mpmath
+import numpy as np
+import pytest
+
+from oracle import geo_oracle as O
+from paper_2003_05324_b300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ Eq. 1 pins ---
+XS = np.concatenate([np.logspace(-6, 0, 25), np.linspace(1.5, 40, 30), [100.0, 300.0, 690.0]])
+
+
+@pytest.mark.parametrize("nu,closed", [
+    (0.5, lambda x: np.exp(-x)),
+    (1.5, lambda x: (1 + x) * np.exp(-x)),
+    (2.5, lambda x: (1 + x + x * x / 3.0) * np.exp(-x)),
+])
+def test_matern_half_integer_closed_forms(nu, closed):
+    # K_{1/2}, K_{3/2}, K_{5/2} are elementary, so Eq. 1 collapses to these.
+    sigma2, beta = 1.7, 0.3
+    r = XS * beta
+    got = O.matern(r, sigma2, beta, nu)
+    want = sigma2 * closed(XS)
+    np.testing.assert_allclose(got, want, rtol=2e-13, atol=0)
+
+
+@pytest.mark.parametrize("nu", [0.3, 1.0, 1.7, 2.2])
+def test_matern_general_nu_vs_mpmath(nu):
+    sigma2, beta = 1.3, 0.07
+    xs = np.array([1e-5, 1e-3, 0.05, 0.4, 1.0, 1.9, 2.1, 5.0, 17.0, 60.0, 300.0])
+    got = O.matern(xs * beta, sigma2, beta, nu)
+    mpmath.mp.dps = 40
+    want = [float(mpmath.mpf(sigma2) / (2 ** (mpmath.mpf(nu) - 1) * mpmath.gamma(nu))
+                  * mpmath.mpf(x) ** nu * mpmath.besselk(nu, x)) for x in xs]
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=0)
+
+
+def _k_quadrature(nu, x):
+    # K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt, trapezoid rule in mpmath;
+    # the integrand is analytic in a strip, so the rule converges geometrically.
+    mpmath.mp.dps = 30
+    h = mpmath.mpf(1) / 16
+    total = mpmath.mpf(0)
+    t = mpmath.mpf(0)
+    w = mpmath.mpf(1) / 2
+    while True:
+        term = mpmath.exp(-x * mpmath.cosh(t)) * mpmath.cosh(nu * t)
+        total += w * term
+        if t > 2 and term < mpmath.mpf(10) ** -40:
+            break
+        t += h
+        w = 1
+    return total * h
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.0, 1.37])
+def test_bessel_k_by_quadrature(nu):
+    for x in [0.01, 0.3, 1.0, 2.5, 9.0, 30.0]:
+        want = float(_k_quadrature(nu, x))
+        # oracle's C(r) at sigma2 = 2^(nu-1) Gamma(nu), beta = 1 is x^nu K_nu(x)
+        c = O.matern(np.array([x]), 2 ** (nu - 1) * math.gamma(nu), 1.0, nu)[0]
+        assert abs(c / x ** nu - want) <= 1e-13 * want, (nu, x)
+
+
+@pytest.mark.parametrize("nu", [0.3, 0.5, 1.0, 2.5])
+def test_matern_origin_limit(nu):
+    # x^nu K_nu(x) -> 2^(nu-1) Gamma(nu) as x -> 0, so C(r) -> theta1; C(0) = theta1.
+    s2 = 2.3
+    assert O.matern(np.array([0.0]), s2, 0.1, nu)[0] == s2
+    small = O.matern(np.array([1e-9]), s2, 0.1, nu)[0]
+    assert abs(small - s2) < 1e-3 * s2
+    # far field underflows to an exact 0, never NaN
+    far = O.matern(np.array([1e6]), s2, 0.1, nu)[0]
+    assert far == 0.0
+
+
+# ------------------------------------------------------------ Eq. 2 pins ---
+def _exact_loglik(S, z):
+    """Eq. 2 from exact rational det (Gaussian elimination over Q) and exact Z'S^-1 Z."""
+    n = len(z)
+    M = [[Fraction(float(S[i, j])) for j in range(n)] + [Fraction(float(z[i]))] for i in range(n)]
+    det = Fraction(1)
+    for c in range(n):
+        piv = max(range(c, n), key=lambda r: abs(M[r][c]))
+        if piv != c:
+            M[c], M[piv] = M[piv], M[c]
+            det = -det
+        det *= M[c][c]
+        for r in range(c + 1, n):
+            f = M[r][c] / M[c][c]
+            for cc in range(c, n + 1):
+                M[r][cc] -= f * M[c][cc]
+    sol = [Fraction(0)] * n
+    for r in reversed(range(n)):
+        acc = M[r][n] - sum(M[r][cc] * sol[cc] for cc in range(r + 1, n))
+        sol[r] = acc / M[r][r]
+    quad = sum(Fraction(float(z[i])) * sol[i] for i in range(n))
+    return -0.5 * n * math.log(2 * math.pi) - 0.5 * math.log(float(det)) - 0.5 * float(quad), det
+
+
+def _leibniz_det(S):
+    n = S.shape[0]
+    total = Fraction(0)
+    for perm in permutations(range(n)):
+        inv = sum(1 for a in range(n) for b in range(a + 1, n) if perm[a] > perm[b])
+        prod = Fraction(1)
+        for i in range(n):
+            prod *= Fraction(float(S[i, perm[i]]))
+        total += -prod if inv % 2 else prod
+    return total
+
+
+@pytest.mark.parametrize("n,nu", [(5, 0.5), (6, 1.0), (8, 1.5)])
+def test_loglik_brute_force_small(n, nu):
+    x, y = inputs.uniform_points(n, seed=11 + n)
+    z = inputs.white_noise(n, seed=3)
+    th = O.Theta(1.4, 0.25, nu, 1e-3)
+    got = O.loglik_dense(x, y, z, th)
+    S = O.covariance(x, y, theta=th)
+    want, det = _exact_loglik(S, z)
+    assert abs(got["loglik"] - want) <= 1e-12 * abs(want)
+    if n <= 6:
+        assert _leibniz_det(S) == det
+    L, info = O.dense_factor(S)
+    assert info == 0
+    assert np.linalg.norm(L @ L.T - S) / np.linalg.norm(S) <= 1e-15 * n
+
+
+def _markov_loglik(x, z, sigma2, beta):
+    # nu = 1/2 on sorted 1D points is a Markov (AR(1)-type) process:
+    # log|S| = log s2 + sum_{i>=2} log(s2 (1 - rho_i^2)),
+    # Z'S^-1 Z = Z_1^2/s2 + sum_{i>=2} (Z_i - rho_i Z_{i-1})^2 / (s2 (1 - rho_i^2)),
+    # rho_i = exp(-d_i / beta).
+    n = len(z)
+    d = np.diff(x)
+    rho = np.exp(-d / beta)
+    one_m = -np.expm1(-2 * d / beta)
+    logdet = math.log(sigma2) + math.fsum(np.log(sigma2 * one_m).tolist())
+    quad = z[0] ** 2 / sigma2 + math.fsum(((z[1:] - rho * z[:-1]) ** 2 / (sigma2 * one_m)).tolist())
+    return -0.5 * n * math.log(2 * math.pi) - 0.5 * logdet - 0.5 * quad, logdet, quad
+
+
+def test_loglik_markov_1d_closed_form():
+    n = 600
+    x, y = inputs.line_points(n, seed=5, min_gap=0.05)
+    z = inputs.white_noise(n, seed=6)
+    th = O.Theta(1.2, 0.05, 0.5, 0.0)
+    got = O.loglik_dense(x, y, z, th)
+    want, ld, q = _markov_loglik(x, z, th.sigma2, th.beta)
+    assert abs(got["logdet"] - ld) <= 1e-10 * abs(ld)
+    assert abs(got["quad"] - q) <= 1e-10 * abs(q)
+    assert abs(got["loglik"] - want) <= 1e-11 * abs(want)
+
+
+def test_loglik_identity_covariance():
+    # beta tiny and spacing >= 1e-3: every off-diagonal exp(-r/beta) underflows to 0.
+    x, y = inputs.jittered_grid(12, seed=2)
+    n = len(x)
+    z = inputs.white_noise(n, seed=4)
+    th = O.Theta(1.0, 1e-6, 0.5, 0.0)
+    S = O.covariance(x, y, theta=th)
+    assert np.array_equal(S, np.eye(n))
+    got = O.loglik_dense(x, y, z, th)
+    want = -0.5 * n * math.log(2 * math.pi) - 0.5 * math.fsum((z * z).tolist())
+    assert got["loglik"] == pytest.approx(want, rel=1e-15)
+
+
+def test_loglik_sigma2_scaling():
+    x, y = inputs.jittered_grid(10, seed=8)
+    n = len(x)
+    z = inputs.white_noise(n, seed=9)
+    base = O.loglik_dense(x, y, z, O.Theta(1.0, 0.2, 1.0, 0.0))
+    for s2 in [0.3, 2.0, 17.0]:
+        got = O.loglik_dense(x, y, z, O.Theta(s2, 0.2, 1.0, 0.0))["loglik"]
+        want = (-0.5 * n * math.log(2 * math.pi) - 0.5 * n * math.log(s2)
+                - 0.5 * base["logdet"] - 0.5 * base["quad"] / s2)
+        assert got == pytest.approx(want, rel=1e-12)
+
+
+def test_loglik_permutation_invariance():
+    x, y = inputs.jittered_grid(9, seed=10)
+    z = inputs.white_noise(len(x), seed=12)
+    th = O.Theta(1.0, 0.1, 0.5)
+    a = O.loglik_dense(x, y, z, th)["loglik"]
+    perm = np.random.default_rng(0).permutation(len(x))
+    b = O.loglik_dense(x[perm], y[perm], z[perm], th)["loglik"]
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_profile_sigma2_is_argmax():
+    # theta1_opt = Z'S~^-1 Z / n maximises Eq. 2 over theta1 (text after Eq. 3).
+    x, y = inputs.jittered_grid(10, seed=13)
+    z = inputs.white_noise(len(x), seed=14) * 1.7
+    s2, prof = O.profile_sigma2(x, y, z, 0.15, 0.5)
+    at = O.loglik_dense(x, y, z, O.Theta(s2, 0.15, 0.5))["loglik"]
+    assert prof == pytest.approx(at, rel=1e-12)
+    for f in [0.99, 1.01, 0.8, 1.25]:
+        assert O.loglik_dense(x, y, z, O.Theta(s2 * f, 0.15, 0.5))["loglik"] < at
+
+
+def test_not_spd_reports_first_failing_row():
+    S = np.diag([4.0, 1.0, -2.0, 3.0])
+    L, info = O.dense_factor(S)
+    assert info == 3
+    L2, info2 = O.mp_tile_cholesky(S, 2, 1)
+    assert info2 == 3
+
+
+# ------------------------------------------------------ Algorithm 1 pins ---
+def test_alg1_trace_5x5_band2_matches_hand_trace():
+    S = np.eye(50) * 3.0 + 0.01
+    trace = []
+    O.mp_tile_cholesky(S, 10, 2, trace=trace)
+    step0 = [t for t in trace if t[3] == 0]
+    want = []
+    with open(os.path.join(GOLDEN, "alg1_5x5_band2_step0.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                op, i, j, k = line.split()
+                want.append((op, int(i), int(j), int(k)))
+    assert step0 == want
+    # precision map: DP tiles are the diagonal and the first sub-diagonal
+    dp = {(i, j) for i in range(5) for j in range(i + 1) if O.tile_is_dp(i, j, 2)}
+    assert dp == {(0, 0), (1, 1), (2, 2), (3, 3), (4, 4), (1, 0), (2, 1), (3, 2), (4, 3)}
+    # every trailing update appears exactly once per step
+    for k in range(5):
+        ups = [t for t in trace if t[3] == k and t[0] in ("dgemm", "sgemm", "dsyrk")]
+        assert len(ups) == (4 - k) * (5 - k) // 2
+
+
+def test_alg1_full_band_equals_dense_factor():
+    x, y = inputs.jittered_grid(16, seed=15)
+    th = O.Theta(1.0, 0.1, 0.5)
+    S = O.covariance(x, y, theta=th)
+    Ld, _ = O.dense_factor(S)
+    p = -(-len(x) // 40)
+    Lm, info = O.mp_tile_cholesky(S, 40, p)
+    assert info == 0
+    assert np.max(np.abs(Lm - Ld)) <= 1e-12
+
+
+def test_alg1_padding_is_exact():
+    x, y = inputs.uniform_points(230, seed=16)
+    z = inputs.white_noise(230, seed=17)
+    th = O.Theta(1.0, 0.1, 1.0, 1e-6)
+    d = O.loglik_dense(x, y, z, th)
+    m = O.loglik_mp(x, y, z, th, nb=64, band=4)  # p = 4 (padded to 256), all DP
+    assert abs(m["loglik"] - d["loglik"]) <= 1e-11 * abs(d["loglik"])
+
+
+@pytest.mark.parametrize("band", [1, 2])
+def test_alg1_mixed_precision_error_is_fp32_level(band):
+    x, y = inputs.jittered_grid(24, seed=18)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.matern_field_rff(x, y, 1.0, 0.1, 0.5, seed=19)
+    th = O.Theta(1.0, 0.1, 0.5)
+    d = O.loglik_dense(x, y, z, th)
+    m = O.loglik_mp(x, y, z, th, nb=48, band=band)
+    rel = abs(m["loglik"] - d["loglik"]) / abs(d["loglik"])
+    assert 0 < rel < 1e-5
+
+
+# ------------------------------------------------------------ ordering ---
+def test_morton_keys_hand_values():
+    x = np.array([0.0, 0.5, 0.0, 1.0, 0.75, 1.0 / 65536])
+    y = np.array([0.0, 0.0, 0.5, 1.0, 0.25, 0.0])
+    k = O.morton_keys(x, y)
+    # 0.5 -> q = 0x8000 (bit 15): x bit 15 -> key bit 30, y bit 15 -> key bit 31
+    # 1.0 clamps to 0xFFFF: all 32 bits set
+    # 0.75 -> 0xC000 (bits 15,14 -> key bits 30,28); 0.25 -> 0x4000 (bit 14 -> key bit 29)
+    assert list(k) == [0, 1 << 30, 1 << 31, 0xFFFFFFFF, (1 << 30) | (1 << 28) | (1 << 29), 1]
+
+
+def test_morton_order_2x2_z_pattern():
+    x = np.array([0.75, 0.25, 0.75, 0.25])
+    y = np.array([0.75, 0.75, 0.25, 0.25])
+    # Z pattern: (lo x, lo y), (hi x, lo y), (lo x, hi y), (hi x, hi y)
+    assert list(O.morton_order(x, y)) == [3, 2, 1, 0]
+    # ties keep the original order
+    assert list(O.morton_order(np.array([0.1, 0.1]), np.array([0.2, 0.2]))) == [0, 1]
+
+
+# --------------------------------------------------------------- kriging ---
+def test_krige_interpolates_observed_points():
+    x, y = inputs.uniform_points(80, seed=20)
+    z = inputs.white_noise(80, seed=21)
+    th = O.Theta(1.0, 0.2, 1.5, 0.0)
+    pick = np.array([0, 7, 33, 79])
+    zhat = O.krige(x, y, z, th, x[pick], y[pick])
+    np.testing.assert_allclose(zhat, z[pick], atol=1e-7)
+
+
+def test_krige_far_point_predicts_zero_mean():
+    x, y = inputs.uniform_points(50, seed=22)
+    z = inputs.white_noise(50, seed=23)
+    th = O.Theta(1.0, 0.01, 0.5, 0.0)
+    zhat = O.krige(x, y, z, th, np.array([50.0]), np.array([50.0]))
+    assert zhat[0] == 0.0
