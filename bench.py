@@ -1,0 +1,390 @@
+"""Benchmark: mixed-precision tile-Cholesky Gaussian log-likelihood on one B300.
+
+Workload (one step = one evaluation of Eq. 2, all of generation, Algorithm 1,
+log-determinant and solve): n = 40,000 locations on a 200 x 200 jittered grid
+(seed 0) in Morton order, Matern sigma2 = 1, beta = 0.1, nu = 0.5, tile 500,
+FP64 band of `--band` tiles, off-band updates as split-BF16 products on the
+tensor cores.  Inputs are synthetic (measurements from a seeded spectral
+Matern-field simulation).  The working set (3.3 GB of tiles) is far larger than
+L2, so consecutive steps do not hit in L2.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+plain FP64/FP32 numpy implementation of Algorithm 1) on a bounded sample of the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M_GRID = 200          # 200 x 200 = 40,000 locations
+NB = 500
+THETA = (1.0, 0.1, 0.5, 0.0)
+FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 (profiling recipe); our probe measured 0.97 (DMMA)
+CPU_SAMPLE_M = 80            # oracle sample: 80 x 80 = 6,400 locations, tile 400, band 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--band", type=int, default=1)
+    ap.add_argument("--lp", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison evaluation")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sweep", action="store_true", help="also time bands 2, 4, 8 (slow)")
+    ap.add_argument("--gen64", action="store_true", help="generate off-band entries in FP64 and round")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(m=M_GRID, seed=0):
+    from paper_2003_05324_b300 import inputs
+    x, y = inputs.jittered_grid(m, seed=seed)
+    z = inputs.matern_field_rff(x, y, THETA[0], THETA[1], THETA[2], seed=seed + 1)
+    return x, y, z
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(steps=1):
+    """The oracle's Algorithm 1 (numpy/scipy, host BLAS threads) on a bounded sample."""
+    from oracle import geo_oracle as O
+    from paper_2003_05324_b300 import inputs
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    x, y, z = workload(CPU_SAMPLE_M, seed=0)
+    perm = O.morton_order(x, y)
+    x, y, z = x[perm], y[perm], z[perm]
+    th = O.Theta(*THETA)
+    n = len(z)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        O.loglik_mp(x, y, z, th, nb=400, band=1)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return {"value": n ** 3 / 3.0 / t / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle Algorithm 1 (numpy/scipy) on n={n} ({CPU_SAMPLE_M}x{CPU_SAMPLE_M} jittered grid, "
+                      f"Morton order), tile 400, band 1, same theta; {t:.2f} s per evaluation",
+            "seconds_per_eval": t}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(1)
+    t0 = time.perf_counter()
+    vals = [cpu_baseline(1) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    v = statistics.median([c["value"] for c in vals])
+    cb = dict(vals[0])
+    cb["value"] = v
+    n = CPU_SAMPLE_M ** 2
+    print(json.dumps({
+        "impl": "reference", "metric": "MP tile-Cholesky TFLOP/s (n^3/3 per log-likelihood evaluation)",
+        "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": f"loglik n={n} (bounded sample of the n=40000 workload), tile 400, band 1",
+                   "cache": "inputs larger than L2 not applicable (CPU)"},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2003_05324_b300 import geo
+    dev = torch.device("cuda", local)
+    # CPU oracle baseline first (before heavy GPU work; rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(2)
+
+    x, y, z = workload()
+    perm = geo.morton_order(x, y)
+    x, y, z = x[perm], y[perm], z[perm]
+    n = len(z)
+    th = geo.Theta(*THETA)
+    X = torch.as_tensor(x, device=dev)
+    Y = torch.as_tensor(y, device=dev)
+    Z = torch.as_tensor(z, device=dev)
+    lp = geo.GEO_LP_SPLIT_BF16 if args.lp == "bf16" else geo.GEO_LP_FP32
+    ts = geo.TileStore(n, NB, args.band, lp, device=dev)
+    gen_flags = geo.GEO_FLAG_FP64_OFFBAND_GEN if args.gen64 else 0
+    ts.set_flags(gen_flags)
+    stream = torch.cuda.current_stream(dev)
+    flops = n ** 3 / 3.0
+
+    # warm-up (also the accuracy reference for this band)
+    for _ in range(args.warmup):
+        ld, q = ts.loglik_async(X, Y, Z, th)
+    torch.cuda.synchronize(dev)
+    code, info = ts.status()
+    if code != 0:
+        raise SystemExit(f"device status {code} (info {info}) during warm-up")
+    l_mp = ts.assemble(float(ld), float(q))
+
+    # timed region: K steps back to back on the stream, CUDA events around them
+    geo.profile_reset()
+    geo.profile_enable(True)
+    launches0 = geo.kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev0.record(stream)
+    step_ev[0].record(stream)
+    for s in range(args.steps):
+        ts.loglik_async(X, Y, Z, th)
+        step_ev[s + 1].record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    geo.profile_enable(False)
+    launches = geo.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    step_ms = [step_ev[i].elapsed_time(step_ev[i + 1]) for i in range(args.steps)]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    code, info = ts.status()
+    if code != 0:
+        raise SystemExit(f"device status {code} (info {info}) in the timed region")
+    ms_step = ms / args.steps
+    evals_per_s = world * args.steps / (ms / 1000.0)
+    tflops = world * flops * args.steps / (ms / 1000.0) / 1e12
+
+    # per-kernel live timings (CUDA events on each kernel's own stream)
+    kern = {}
+    names = {0: "fp64_update (dsyrk+dgemm, DMMA)", 1: "offband_update (split-BF16 tcgen05)" if args.lp == "bf16"
+             else "offband_update (FP32 FMA)", 2: "potrf (FP64, cooperative)", 3: "trsm (panel)"}
+    for kind in range(4):
+        kms, kn = geo.profile_read(kind)
+        kern[kind] = (kms, kn)
+
+    # algorithmic work per kernel kind over the timed steps
+    p, b = ts.p, ts.band
+    f64_upd = 0.0
+    lp_upd = 0.0
+    for k in range(p):
+        for j in range(k + 1, p):
+            f64_upd += NB ** 3                      # dsyrk on (j,j): lower triangle n^3 (2n^3/2)
+            for i in range(j + 1, p):
+                if i - j < b:
+                    f64_upd += 2.0 * NB ** 3
+                else:
+                    lp_upd += 6 * 2.0 * NB ** 3        # six BF16 products per split update
+    f64_upd *= args.steps
+    lp_upd *= args.steps
+    sustained = None
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16_peak = 1800.0
+    peak_src = "fallback"
+    if os.path.exists(peaks_path):
+        pk = json.load(open(peaks_path))
+        bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", bf16_peak))
+        peak_src = "measured (sustained)"
+    rows = []
+    if kern[0][1]:
+        ach = f64_upd / (kern[0][0] / 1000.0) / 1e12
+        rows.append({"kernel": names[0], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "avg_ms": kern[0][0] / kern[0][1],
+                     "launches": kern[0][1], "total_ms": kern[0][0],
+                     "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s); probe measured 0.97"})
+    if kern[1][1] and args.lp == "bf16":
+        ach = lp_upd / (kern[1][0] / 1000.0) / 1e12
+        rows.append({"kernel": names[1], "bound": "tensor", "achieved": ach, "peak": bf16_peak,
+                     "unit": "TFLOP/s", "frac": ach / bf16_peak, "avg_ms": kern[1][0] / kern[1][1],
+                     "launches": kern[1][1], "total_ms": kern[1][0], "peak_source": f"bf16 {peak_src}"})
+    dominant = max(rows, key=lambda r: r["total_ms"]) if rows else None
+    roofline = None
+    if dominant:
+        roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+        roofline["kernel"] = dominant["kernel"]
+        roofline["traffic"] = None
+
+    # all-FP64 GPU path: accuracy reference and throughput comparison (one eval)
+    fp64 = None
+    if not args.no_fp64:
+        ts64 = geo.TileStore(n, NB, 10 ** 6, geo.GEO_LP_FP32, device=dev)
+        ld64, q64 = ts64.loglik_async(X, Y, Z, th)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ld64, q64 = ts64.loglik_async(X, Y, Z, th)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64 = e0.elapsed_time(e1) / 1000.0
+        l64 = ts64.assemble(float(ld64), float(q64))
+        fp64 = {"seconds_per_eval": t64, "tflops": flops / t64 / 1e12, "evals_per_s": 1.0 / t64, "loglik": l64,
+                "mp_speedup": t64 / (ms_step / 1000.0), "mp_rel_err": abs(l_mp - l64) / abs(l64)}
+        del ts64
+
+    # end to end through the public blocking call, host buffers copied every step
+    xh = torch.as_tensor(x).pin_memory()
+    yh = torch.as_tensor(y).pin_memory()
+    zh = torch.as_tensor(z).pin_memory()
+    Xe, Ye, Ze = torch.empty_like(X), torch.empty_like(Y), torch.empty_like(Z)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Xe.copy_(xh, non_blocking=True)
+        Ye.copy_(yh, non_blocking=True)
+        Ze.copy_(zh, non_blocking=True)
+        l_e2e = ts.loglik(Xe, Ye, Ze, th)[0]
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": flops / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 3 * 8 * n,
+           "d2h_bytes_per_step": 3 * 8 + 2 * 4, "seconds_per_eval": t_e2e}
+
+    sweep = None
+    if args.sweep:
+        sweep = []
+        for bb in (2, 4, 8):
+            tsb = geo.TileStore(n, NB, bb, lp, device=dev)
+            tsb.set_flags(gen_flags)
+            tsb.loglik_async(X, Y, Z, th)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ldb, qb = tsb.loglik_async(X, Y, Z, th)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tb = e0.elapsed_time(e1) / 1000.0
+            lb = tsb.assemble(float(ldb), float(qb))
+            ent = {"band": bb, "seconds_per_eval": tb, "tflops": flops / tb / 1e12}
+            if fp64:
+                ent["rel_err"] = abs(lb - fp64["loglik"]) / abs(fp64["loglik"])
+            sweep.append(ent)
+            del tsb
+
+    if rank != 0:
+        return
+    p50 = statistics.median(step_ms)
+    p99 = sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)]
+    out = {
+        "metric": "MP tile-Cholesky TFLOP/s (n^3/3 per log-likelihood evaluation); evals/s vs all-FP64 GPU path",
+        "value": tflops, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32(split-bf16)" if args.lp == "bf16" else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": f"loglik n={n} (200x200 jittered grid, Morton), Matern sigma2=1 beta=0.1 nu=0.5, "
+                               f"tile {NB}, band {ts.band}, off-band {args.lp}",
+                   "n": n, "nb": NB, "band": ts.band, "lp": args.lp,
+                   "offband_generation": "fp64-rounded" if args.gen64 else "compensated fp32",
+                   "cache": "working set 3.3 GB of tiles >> 126 MB L2 (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "evals_per_s": evals_per_s, "p50_ms": p50, "p99_ms": p99,
+        "loglik": l_mp, "loglik_e2e": l_e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roofline,
+        "kernels": rows,
+        "fp64_path": fp64,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if sweep is not None:
+        out["band_sweep"] = sweep
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

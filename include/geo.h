@@ -1,0 +1,181 @@
+/*
+ * geo.h -- C ABI of the mixed-precision Gaussian log-likelihood library (libgeo.so).
+ *
+ * The library evaluates, on one CUDA device (sm_103a), the Gaussian
+ * log-likelihood of Eq. 2,
+ *     l(theta) = -n/2 log(2 pi) - 1/2 log|Sigma(theta)| - 1/2 Z' Sigma(theta)^-1 Z,
+ * for the Matern covariance of Eq. 1 over 2D locations, by the mixed-precision
+ * tile Cholesky factorization of Algorithm 1: tiles within `band` (the paper's
+ * diag_thick) tiles of the diagonal are held and updated in FP64, all others in
+ * FP32 storage with FP32-accurate arithmetic.
+ *
+ * Conventions shared by every call
+ *  - Memory: the caller owns every buffer.  Pointers named d_* are device
+ *    pointers, h_* host pointers.  The library never allocates device memory and
+ *    never frees a caller's buffer (exception: geo_tiles_bind creates two CUDA
+ *    events and one stream, released by geo_tiles_release).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated otherwise.
+ *  - Layout: locations are structure-of-arrays FP64 x[n], y[n]; Z is FP64[n].
+ *    Inputs are expected in Morton order (geo_morton_order), which the
+ *    likelihood does not depend on but the mixed-precision error does.
+ *    Tiles: p = ceil(n/nb) tiles per side; the n x n matrix is padded to p*nb
+ *    with decoupled identity rows (which add 0 to log|Sigma| and to Z'Sigma^-1 Z).
+ *    Lower tile (i,j), i >= j, is FP64 iff i - j < band.  Every tile is stored
+ *    contiguously, column-major, leading dimension nb, in the FP64 store
+ *    (band tiles) or the FP32 store (off-band tiles).
+ *  - Errors: 0 = GEO_OK; a negative value -k means argument k (1-based) was
+ *    invalid (nothing was launched); positive values are the GEO_ERR_* codes.
+ *    Device-side failures (non-SPD pivot, scheduler timeout) are recorded in the
+ *    status words of the bound workspace and returned by the blocking calls or
+ *    read with geo_status.
+ */
+#ifndef GEO_H
+#define GEO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GEO_OK 0
+#define GEO_ERR_NOT_SPD 1      /* a diagonal pivot was <= 0 (or NaN); info = 1-based global row */
+#define GEO_ERR_TIMEOUT 2      /* a device-side wait exceeded its bound; work was abandoned */
+#define GEO_ERR_CUDA 3         /* a CUDA runtime call failed */
+#define GEO_ERR_UNSUPPORTED 4  /* a valid but unimplemented configuration */
+
+/* LP (off-band) arithmetic.  GEO_LP_SPLIT_BF16 runs the off-band updates as
+ * FP32-accurate products of three BF16 planes (six products) on the tcgen05
+ * tensor cores with FP32 accumulation; GEO_LP_FP32 runs them as FP32 FMA on
+ * the CUDA cores.  Both store off-band tiles in FP32. */
+#define GEO_LP_SPLIT_BF16 0
+#define GEO_LP_FP32 1
+
+/* Matern parameters (Eq. 1): theta1 = sigma2 (variance), theta2 = beta (range),
+ * theta3 = nu (smoothness); nugget tau2 >= 0 is added to the diagonal. */
+typedef struct geo_theta {
+    double sigma2, beta, nu, nugget;
+} geo_theta;
+
+/* Sizes of one problem's tile store and workspace, computed by geo_layout_init.
+ * All byte counts are for caller-allocated device buffers (256-byte aligned). */
+typedef struct geo_layout {
+    int n, nb, p, band, lp_mode;
+    int pp;                       /* BF16 plane edge: nb rounded up to a multiple of 64 */
+    long long n_dp_tiles, n_sp_tiles, n_slots;
+    size_t bytes_dp;              /* FP64 tile store */
+    size_t bytes_sp;              /* FP32 tile store */
+    size_t bytes_planes;          /* BF16 split planes of panel tiles (0 for GEO_LP_FP32) */
+    size_t bytes_meta;            /* offset tables and status words */
+} geo_layout;
+
+/* A bound problem: layout + the caller's device buffers + library stream/events. */
+typedef struct geo_tiles {
+    geo_layout lay;
+    double* d_dp;
+    float* d_sp;
+    void* d_planes;
+    void* d_meta;
+    void* aux_stream;             /* library-created stream for concurrent off-band work */
+    void* ev_fork;
+    void* ev_join;
+    unsigned long long tmap[16];  /* library-private: TMA descriptor of the BF16 planes */
+    int flags;                    /* GEO_FLAG_* options, set with geo_tiles_set_flags */
+} geo_tiles;
+
+/* Generation option: compute off-band (FP32-stored) covariance entries in FP64
+ * and round them to FP32 (Algorithm 1's dlag2s of the FP64 value) instead of
+ * computing them in compensated FP32 arithmetic (the default, ~8x fewer FP64
+ * operations; entries within (4x+8) 2^-24 relative, x = r/theta2). */
+#define GEO_FLAG_FP64_OFFBAND_GEN 1
+
+/* A1, "appropriate ordering" (Section IV): Z-order permutation of n locations.
+ * Each coordinate c (expected in [0,1]) is quantised to q = clamp(floor(c*2^16),
+ * 0, 2^16-1); the key interleaves qx (even bits) and qy (odd bits); perm[new] =
+ * old index, sorted by (key, old index).  Host-only; x, y, perm are host arrays.
+ * Returns 0 or -k for a bad argument k. */
+int geo_morton_order(const double* x, const double* y, int n, int* perm);
+
+/* Fill *out with the tile geometry and buffer sizes for n locations, tile size
+ * nb (16 <= nb <= 768) and band (1 <= band; band >= p means all tiles FP64).
+ * Pure host arithmetic. */
+int geo_layout_init(int n, int nb, int band, int lp_mode, geo_layout* out);
+
+/* Bind caller-owned device buffers (sizes from *lay) to t and write the offset
+ * tables into d_meta.  Blocks until the tables are on the device.  Creates one
+ * non-blocking stream and two events (released by geo_tiles_release).
+ * d_planes may be NULL when lay->bytes_planes == 0. */
+int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp,
+                   void* d_planes, void* d_meta, void* stream);
+int geo_tiles_release(geo_tiles* t);
+int geo_tiles_set_flags(geo_tiles* t, int flags);
+
+/* A2, Eq. 1: write Sigma_ab = C(||s_a - s_b||; theta) (+ nugget if a == b) into
+ * every lower tile, each directly in its own precision (the FP64 -> FP32
+ * conversion of Algorithm 1's first loop is fused into generation).
+ * d_x, d_y: device FP64[n].  Asynchronous. */
+int geo_matern_tiles(geo_tiles* t, const double* d_x, const double* d_y, geo_theta theta, void* stream);
+
+/* Scatter a dense symmetric n x n FP64 matrix (device, column-major, ld = n,
+ * lower triangle read) into the tile store, rounding off-band tiles to FP32.
+ * Test utility for factor parity.  Asynchronous. */
+int geo_tiles_load_dense(geo_tiles* t, const double* d_a, void* stream);
+
+/* Gather the lower triangle of the tile store into a dense n x n FP64 matrix
+ * (device, column-major, ld = n; FP32 tiles promoted exactly, upper triangle
+ * set to 0).  Asynchronous. */
+int geo_tiles_to_dense(const geo_tiles* t, double* d_out, void* stream);
+
+/* A3-A9, Algorithm 1: factor the tile store in place, A = L L', with the
+ * precision map of the bound layout (its band; band >= p is the all-FP64
+ * path).  On a non-positive pivot the factorization stops early and the status
+ * words record GEO_ERR_NOT_SPD with info = 1-based global row.  Asynchronous;
+ * read the outcome with geo_status. */
+int geo_potrf_mp(geo_tiles* t, void* stream);
+
+/* A10-A11, Eq. 2: from the factored store and Z (device FP64[n]), write
+ * d_logdet[0] = log|Sigma| = 2 sum log L_ii and d_quad[0] = ||L^-1 Z||^2
+ * (device FP64 scalars), and, if d_y != NULL, y = L^-1 Z (device FP64[p*nb]).
+ * FP64 accumulation.  Asynchronous. */
+int geo_logdet_trsv(const geo_tiles* t, const double* d_z, double* d_logdet, double* d_quad,
+                    double* d_y, void* stream);
+
+/* Copy the status words to the host (blocking on `stream`): *h_code = GEO_OK or
+ * a GEO_ERR_* code, *h_info = 1-based failing row for GEO_ERR_NOT_SPD. */
+int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream);
+
+/* A2-A12: full evaluation of Eq. 2 (generation, Algorithm 1, log-det, solve,
+ * assembly).  Blocking: returns after the scalars are on the host.
+ * h_out[0] = l(theta), h_out[1] = log|Sigma|, h_out[2] = Z' Sigma^-1 Z.
+ * Returns GEO_OK, GEO_ERR_NOT_SPD (with *h_info set, h_out undefined), or an error. */
+int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z,
+               geo_theta theta, double* h_out, int* h_info, void* stream);
+
+/* A13, prediction (Section VI-B; simple kriging reading): with t holding the
+ * factor of Sigma(theta) over the observed locations (d_x, d_y, n = t->lay.n)
+ * and observations d_z, write d_zhat[m] = Sigma_new,obs Sigma^-1 Z for the m
+ * new locations (d_xnew, d_ynew).  d_work: device FP64 scratch of
+ * 2 * p * nb doubles.  Asynchronous. */
+int geo_krige(const geo_tiles* t, const double* d_x, const double* d_y, const double* d_z,
+              geo_theta theta, const double* d_xnew, const double* d_ynew, int m,
+              double* d_zhat, double* d_work, void* stream);
+
+/* Instrumentation.  geo_kernel_launches returns the number of kernel launches
+ * this library has issued in the process (all entry points, all devices).
+ * geo_profile_enable(1) makes geo_potrf_mp bracket each launch of the two
+ * trailing-update kernels with CUDA events on the stream it launches them on;
+ * geo_profile_read (blocking: synchronizes those events) returns, for
+ * kind 0 = FP64 update (dsyrk/dgemm), 1 = off-band update (tensor-core or
+ * FP32), 2 = diagonal-tile potrf, 3 = panel trsm, the summed event time in ms
+ * and the launch count since the last geo_profile_reset. */
+unsigned long long geo_kernel_launches(void);
+int geo_profile_enable(int on);
+int geo_profile_reset(void);
+int geo_profile_read(int kind, double* h_ms, long long* h_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEO_H */

@@ -1,0 +1,383 @@
+// C ABI of libgeo (declared in include/geo.h): argument checking, workspace
+// layout, and the host-side sequencing of the device work.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "geo_internal.cuh"
+#include "lp_gemm.cuh"
+
+namespace geo {
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// meta buffer: off[p*p] int64 | slot[p*p] int32 | status[16] int32 | scal doubles
+struct MetaOffsets {
+    size_t off, slot, status, scal, total;
+};
+
+static MetaOffsets meta_offsets(int p, int nb) {
+    MetaOffsets m;
+    size_t b = 0;
+    m.off = b;
+    b = align256(b + sizeof(long long) * (size_t)p * p);
+    m.slot = b;
+    b = align256(b + sizeof(int) * (size_t)p * p);
+    m.status = b;
+    b = align256(b + sizeof(int) * ST_WORDS);
+    m.scal = b;
+    b = align256(b + sizeof(double) * ((size_t)2 * p + 8 + (size_t)p * nb));
+    m.total = b;
+    return m;
+}
+
+// ---- instrumentation ------------------------------------------------------
+static std::atomic<unsigned long long> g_launches{0};
+static bool g_prof = false;
+struct ProfSlot {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open;   // recorded, not yet summed
+    std::vector<cudaEvent_t> pool;
+    double ms = 0.0;
+    long long launches = 0;
+};
+static ProfSlot g_slots[4];
+static std::mutex g_prof_mu;
+
+void count_launch(int n) { g_launches += (unsigned long long)n; }
+bool prof_on() { return g_prof; }
+
+static cudaEvent_t take_event(ProfSlot& sl) {
+    if (!sl.pool.empty()) {
+        cudaEvent_t e = sl.pool.back();
+        sl.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(int kind, cudaStream_t s) {
+    if (!g_prof) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfSlot& sl = g_slots[kind];
+    cudaEvent_t e0 = take_event(sl), e1 = take_event(sl);
+    cudaEventRecord(e0, s);
+    sl.open.push_back({e0, e1});
+}
+
+void prof_end(int kind, cudaStream_t s) {
+    if (!g_prof) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfSlot& sl = g_slots[kind];
+    if (sl.open.empty()) return;
+    cudaEventRecord(sl.open.back().second, s);
+    sl.launches += 1;
+}
+
+static void prof_collect(ProfSlot& sl) {
+    for (auto& pr : sl.open) {
+        float ms = 0.0f;
+        cudaEventSynchronize(pr.second);
+        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) sl.ms += ms;
+        sl.pool.push_back(pr.first);
+        sl.pool.push_back(pr.second);
+    }
+    sl.open.clear();
+}
+
+Layout make_layout(const geo_tiles* t) {
+    Layout L;
+    const geo_layout& g = t->lay;
+    L.n = g.n;
+    L.nb = g.nb;
+    L.p = g.p;
+    L.band = g.band;
+    L.pp = g.pp;
+    L.lp_mode = g.lp_mode;
+    L.flags = t->flags;
+    L.dp = t->d_dp;
+    L.sp = t->d_sp;
+    MetaOffsets mo = meta_offsets(g.p, g.nb);
+    char* base = (char*)t->d_meta;
+    L.off = (const long long*)(base + mo.off);
+    L.slot = (const int*)(base + mo.slot);
+    L.status = (int*)(base + mo.status);
+    L.scal = (double*)(base + mo.scal);
+    L.planes = (__nv_bfloat16*)t->d_planes;
+    return L;
+}
+
+}  // namespace geo
+
+using namespace geo;
+
+extern "C" {
+
+int geo_morton_order(const double* x, const double* y, int n, int* perm) {
+    if (!x) return -1;
+    if (!y) return -2;
+    if (n < 0) return -3;
+    if (!perm && n > 0) return -4;
+    std::vector<std::pair<unsigned long long, int>> kv((size_t)n);
+    for (int idx = 0; idx < n; ++idx) {
+        long long qx = (long long)floor(x[idx] * 65536.0), qy = (long long)floor(y[idx] * 65536.0);
+        qx = std::min(std::max(qx, 0LL), 65535LL);
+        qy = std::min(std::max(qy, 0LL), 65535LL);
+        unsigned long long key = 0;
+        for (int b = 0; b < 16; ++b) {
+            key |= (unsigned long long)((qx >> b) & 1) << (2 * b);
+            key |= (unsigned long long)((qy >> b) & 1) << (2 * b + 1);
+        }
+        kv[(size_t)idx] = {key, idx};
+    }
+    std::sort(kv.begin(), kv.end());   // (key, index) pairs: ties keep the original order
+    for (int idx = 0; idx < n; ++idx) perm[idx] = kv[(size_t)idx].second;
+    return GEO_OK;
+}
+
+int geo_layout_init(int n, int nb, int band, int lp_mode, geo_layout* out) {
+    if (n < 1) return -1;
+    if (nb < 16 || nb > 768) return -2;
+    if (band < 1) return -3;
+    if (lp_mode != GEO_LP_SPLIT_BF16 && lp_mode != GEO_LP_FP32) return -4;
+    if (!out) return -5;
+    const int p = (n + nb - 1) / nb;
+    if ((long long)p * (p + 1) / 2 > 65535) return -1;   // grid-y bound of the per-tile launches
+    geo_layout g;
+    memset(&g, 0, sizeof(g));
+    g.n = n;
+    g.nb = nb;
+    g.p = p;
+    g.band = std::min(band, p);
+    g.lp_mode = lp_mode;
+    g.pp = (nb + 63) / 64 * 64;
+    long long ndp = 0, nsp = 0;
+    for (int j = 0; j < p; ++j)
+        for (int i = j; i < p; ++i) (is_dp(i, j, g.band) ? ndp : nsp) += 1;
+    g.n_dp_tiles = ndp;
+    g.n_sp_tiles = nsp;
+    g.n_slots = (long long)p * (p - 1) / 2;
+    const size_t tile = (size_t)nb * nb;
+    g.bytes_dp = align256(sizeof(double) * tile * (size_t)ndp);
+    g.bytes_sp = align256(sizeof(float) * tile * (size_t)std::max(nsp, 1LL));
+    g.bytes_planes = (lp_mode == GEO_LP_SPLIT_BF16 && nsp > 0)
+                         ? align256((size_t)3 * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots)
+                         : 0;
+    g.bytes_meta = meta_offsets(p, nb).total;
+    *out = g;
+    return GEO_OK;
+}
+
+int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp, void* d_planes, void* d_meta,
+                   void* stream) {
+    if (!t) return -1;
+    if (!lay || lay->p < 1) return -2;
+    if (!d_dp) return -3;
+    if (!d_sp) return -4;
+    if (lay->bytes_planes > 0 && !d_planes) return -5;
+    if (!d_meta) return -6;
+    memset(t, 0, sizeof(*t));
+    t->lay = *lay;
+    t->d_dp = (double*)d_dp;
+    t->d_sp = (float*)d_sp;
+    t->d_planes = d_planes;
+    t->d_meta = d_meta;
+    const int p = lay->p, nb = lay->nb;
+    const size_t tile = (size_t)nb * nb;
+    MetaOffsets mo = meta_offsets(p, nb);
+    std::vector<char> host(mo.scal, 0);
+    long long* off = (long long*)(host.data() + mo.off);
+    int* slot = (int*)(host.data() + mo.slot);
+    long long ndp = 0, nsp = 0;
+    int ns = 0;
+    for (int q = 0; q < p * p; ++q) {
+        off[q] = -1;
+        slot[q] = -1;
+    }
+    for (int j = 0; j < p; ++j)
+        for (int i = j; i < p; ++i) {
+            if (is_dp(i, j, lay->band)) off[i * p + j] = (long long)tile * ndp++;
+            else off[i * p + j] = (long long)tile * nsp++;
+            if (i > j) slot[i * p + j] = ns++;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(d_meta, host.data(), mo.scal, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    cudaStream_t aux = nullptr;
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    if (!e) e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&e2, cudaEventDisableTiming);
+    if (e) return GEO_ERR_CUDA;
+    t->aux_stream = aux;
+    t->ev_fork = e1;
+    t->ev_join = e2;
+    if (lay->bytes_planes > 0 && prepare_lp_gemm(t, make_layout(t)) != 0) return GEO_ERR_CUDA;
+    return GEO_OK;
+}
+
+int geo_tiles_release(geo_tiles* t) {
+    if (!t) return -1;
+    if (t->ev_fork) cudaEventDestroy((cudaEvent_t)t->ev_fork);
+    if (t->ev_join) cudaEventDestroy((cudaEvent_t)t->ev_join);
+    if (t->aux_stream) cudaStreamDestroy((cudaStream_t)t->aux_stream);
+    t->ev_fork = t->ev_join = t->aux_stream = nullptr;
+    return GEO_OK;
+}
+
+int geo_tiles_set_flags(geo_tiles* t, int flags) {
+    if (!t) return -1;
+    if (flags & ~GEO_FLAG_FP64_OFFBAND_GEN) return -2;
+    t->flags = flags;
+    return GEO_OK;
+}
+
+static int check_bound(const geo_tiles* t) { return (t && t->d_meta && t->d_dp && t->d_sp) ? 0 : 1; }
+
+static int check_theta(const geo_theta& th) {
+    return (th.sigma2 > 0 && th.beta > 0 && th.nu > 0 && th.nu <= 20 && th.nugget >= 0 && isfinite(th.sigma2) &&
+            isfinite(th.beta))
+               ? 0
+               : 1;
+}
+
+int geo_matern_tiles(geo_tiles* t, const double* d_x, const double* d_y, geo_theta theta, void* stream) {
+    if (check_bound(t)) return -1;
+    if (!d_x) return -2;
+    if (!d_y) return -3;
+    if (check_theta(theta)) return -4;
+    Layout L = make_layout(t);
+    return launch_matern_tiles(L, d_x, d_y, make_matern(theta), (cudaStream_t)stream) ? GEO_ERR_CUDA : GEO_OK;
+}
+
+int geo_tiles_load_dense(geo_tiles* t, const double* d_a, void* stream) {
+    if (check_bound(t)) return -1;
+    if (!d_a) return -2;
+    return launch_load_dense(make_layout(t), d_a, (cudaStream_t)stream) ? GEO_ERR_CUDA : GEO_OK;
+}
+
+int geo_tiles_to_dense(const geo_tiles* t, double* d_out, void* stream) {
+    if (check_bound(t)) return -1;
+    if (!d_out) return -2;
+    return launch_to_dense(make_layout(t), d_out, (cudaStream_t)stream) ? GEO_ERR_CUDA : GEO_OK;
+}
+
+static int reset_status(const Layout& L, cudaStream_t s) {
+    return cudaMemsetAsync(L.status, 0, sizeof(int) * ST_WORDS, s) ? GEO_ERR_CUDA : GEO_OK;
+}
+
+int geo_potrf_mp(geo_tiles* t, void* stream) {
+    if (check_bound(t)) return -1;
+    Layout L = make_layout(t);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = reset_status(L, s);
+    if (rc) return rc;
+    return run_potrf_mp(t, L, s) ? GEO_ERR_CUDA : GEO_OK;
+}
+
+int geo_logdet_trsv(const geo_tiles* t, const double* d_z, double* d_logdet, double* d_quad, double* d_y,
+                    void* stream) {
+    if (check_bound(t)) return -1;
+    if (!d_z) return -2;
+    if (!d_logdet) return -3;
+    if (!d_quad) return -4;
+    return run_logdet_trsv(make_layout(t), d_z, d_logdet, d_quad, d_y, (cudaStream_t)stream) ? GEO_ERR_CUDA
+                                                                                             : GEO_OK;
+}
+
+int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream) {
+    if (check_bound(t)) return -1;
+    if (!h_code) return -2;
+    Layout L = make_layout(t);
+    int st[2] = {0, 0};
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(st, L.status, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return GEO_ERR_CUDA;
+    *h_code = st[0];
+    if (h_info) *h_info = st[1];
+    return GEO_OK;
+}
+
+int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta,
+               double* h_out, int* h_info, void* stream) {
+    if (check_bound(t)) return -1;
+    if (!d_x) return -2;
+    if (!d_y) return -3;
+    if (!d_z) return -4;
+    if (check_theta(theta)) return -5;
+    if (!h_out) return -6;
+    Layout L = make_layout(t);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = reset_status(L, s);
+    if (rc) return rc;
+    if (launch_matern_tiles(L, d_x, d_y, make_matern(theta), s)) return GEO_ERR_CUDA;
+    if (run_potrf_mp(t, L, s)) return GEO_ERR_CUDA;
+    double* res = L.scal + 2 * L.p;
+    if (run_logdet_trsv(L, d_z, res, res + 1, nullptr, s)) return GEO_ERR_CUDA;
+    double hres[2];
+    int st[2];
+    cudaError_t e = cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(st, L.status, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return GEO_ERR_CUDA;
+    if (h_info) *h_info = st[1];
+    if (st[0] != 0) return st[0];
+    const double n = (double)L.n;
+    h_out[0] = -0.5 * n * log(2.0 * M_PI) - 0.5 * hres[0] - 0.5 * hres[1];
+    h_out[1] = hres[0];
+    h_out[2] = hres[1];
+    return GEO_OK;
+}
+
+int geo_krige(const geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta,
+              const double* d_xnew, const double* d_ynew, int m, double* d_zhat, double* d_work, void* stream) {
+    if (check_bound(t)) return -1;
+    if (!d_x) return -2;
+    if (!d_y) return -3;
+    if (!d_z) return -4;
+    if (check_theta(theta)) return -5;
+    if (m < 0) return -8;
+    if (m > 0 && (!d_xnew || !d_ynew)) return -6;
+    if (m > 0 && !d_zhat) return -9;
+    if (!d_work) return -10;
+    return run_krige(make_layout(t), d_x, d_y, d_z, make_matern(theta), d_xnew, d_ynew, m, d_zhat, d_work,
+                     (cudaStream_t)stream)
+               ? GEO_ERR_CUDA
+               : GEO_OK;
+}
+
+unsigned long long geo_kernel_launches(void) { return g_launches.load(); }
+
+int geo_profile_enable(int on) {
+    g_prof = on != 0;
+    return GEO_OK;
+}
+
+int geo_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& sl : g_slots) {
+        prof_collect(sl);
+        sl.ms = 0.0;
+        sl.launches = 0;
+    }
+    return GEO_OK;
+}
+
+int geo_profile_read(int kind, double* h_ms, long long* h_launches) {
+    if (kind < 0 || kind > 3) return -1;
+    if (!h_ms) return -2;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_collect(g_slots[kind]);
+    *h_ms = g_slots[kind].ms;
+    if (h_launches) *h_launches = g_slots[kind].launches;
+    return GEO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal device-side view of one problem's tile store and shared helpers.
+//
+// Tile (i, j), i >= j, of the p x p tile grid is an nb x nb column-major block
+// stored contiguously: in the FP64 store when i - j < band (Algorithm 1's
+// diag_thick), otherwise in the FP32 store.  `off[i*p + j]` is its element
+// offset inside the store of its precision (-1 for the upper triangle).
+// Panel tiles (i > j) also own a slot of three BF16 planes (hi, mid, lo of
+// their FP32 value), each pp x pp row-major with the column (the contraction
+// index of the off-band update) contiguous and zero padding beyond nb.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/geo.h"
+
+namespace geo {
+
+// status words in the workspace
+enum { ST_CODE = 0, ST_INFO = 1, ST_TIMEOUT_WHERE = 2, ST_BAR_COUNT = 4, ST_BAR_GEN = 5, ST_WORDS = 16 };
+
+struct Layout {
+    int n, nb, p, band, pp, lp_mode, flags;
+    double* dp;
+    float* sp;
+    const long long* off;
+    const int* slot;
+    __nv_bfloat16* planes;
+    int* status;
+    double* scal;   // scalar scratch: per-tile log-det and quad partials [2*p], results [2]
+};
+
+__host__ __device__ inline bool is_dp(int i, int j, int band) { return (i - j) < band; }
+
+__device__ __forceinline__ double* dp_tile(const Layout& L, int i, int j) { return L.dp + L.off[i * L.p + j]; }
+__device__ __forceinline__ float* sp_tile(const Layout& L, int i, int j) { return L.sp + L.off[i * L.p + j]; }
+__device__ __forceinline__ __nv_bfloat16* plane(const Layout& L, int i, int j, int s) {
+    return L.planes + ((size_t)L.slot[i * L.p + j] * 3 + s) * (size_t)L.pp * L.pp;
+}
+__device__ __forceinline__ bool failed(const Layout& L) {
+    return *((volatile int*)L.status + ST_CODE) != 0;
+}
+
+__device__ __forceinline__ long long gtimer() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Record a device-side timeout (first writer wins) with a code for where it happened.
+__device__ __forceinline__ void set_timeout(const Layout& L, int where) {
+    atomicCAS(L.status + ST_CODE, 0, GEO_ERR_TIMEOUT);
+    atomicCAS(L.status + ST_TIMEOUT_WHERE, 0, where);
+}
+
+// Matern parameters prepared on the host (Eq. 1): kind selects a closed form
+// for nu in {1/2, 3/2, 5/2}; log_c = (nu - 1) log 2 + log Gamma(nu).
+struct MaternP {
+    double sigma2, inv_beta, nu, nugget, log_c;
+    int kind;   // 0 general nu, 1: nu = 1/2, 2: nu = 3/2, 3: nu = 5/2
+};
+
+MaternP make_matern(const geo_theta& th);
+
+Layout make_layout(const geo_tiles* t);
+
+// Instrumentation (api.cu): a launch counter and optional event timing of
+// selected kernels (kinds: 0 FP64 update, 1 off-band update, 2 potrf, 3 trsm).
+void count_launch(int n = 1);
+bool prof_on();
+void prof_begin(int kind, cudaStream_t s);
+void prof_end(int kind, cudaStream_t s);
+
+// Launchers (defined in their own .cu files; all asynchronous on `s`).
+cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* y, const MaternP& mp,
+                                cudaStream_t s);
+cudaError_t launch_load_dense(const Layout& L, const double* a, cudaStream_t s);
+cudaError_t launch_to_dense(const Layout& L, double* out, cudaStream_t s);
+cudaError_t run_potrf_mp(const geo_tiles* t, const Layout& L, cudaStream_t s);
+cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, double* quad, double* y,
+                            cudaStream_t s);
+cudaError_t run_krige(const Layout& L, const double* x, const double* y, const double* z, const MaternP& mp,
+                      const double* xn, const double* yn, int m, double* zhat, double* work, cudaStream_t s);
+
+}  // namespace geo

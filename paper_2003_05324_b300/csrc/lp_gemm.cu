@@ -1,0 +1,431 @@
+// BF16 plane split of panel tiles and the tcgen05 off-band update (see lp_gemm.cuh).
+//
+// Off-band update kernel (one launch per outer step k, persistent, one CTA per SM):
+//   work item = (off-band target (i,j), 128-row block mb, 128-column block nc)
+//   warp 0      TMA producer: per K chunk of 64, the three planes of A(i,k) rows
+//               [mb*128, +128) and of A(j,k) rows [nc*128, +128) -> one smem stage
+//   warp 1      TMEM allocation and a single issuing thread: 6 plane pairs x 4
+//               UMMA (M=128, N=128, K=16, BF16 in, FP32 accumulate) per stage
+//   warps 2..5  epilogue: tcgen05.ld of the FP32 accumulator, C -= acc in place
+// Two smem stages (96 KB each) and two TMEM accumulators (2 x 128 columns) let the
+// epilogue of one item overlap the main loop of the next.  Every mbarrier wait is
+// bounded by a %globaltimer deadline; on expiry the CTA records GEO_ERR_TIMEOUT,
+// drains its outstanding copies and MMAs (also bounded), frees TMEM and exits.
+#include <cuda.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "lp_gemm.cuh"
+
+namespace geo {
+
+// ------------------------------------------------------------ split ---
+// 32 x 32 transpose tiles: read the column-major FP32 (or FP64 in-band) panel
+// tile coalesced down the rows, write the row-major planes coalesced along K.
+__global__ void __launch_bounds__(256) split_panel_kernel(Layout L, int k) {
+    if (failed(L)) return;
+    const int i = k + 1 + blockIdx.z;
+    const int nb = L.nb, pp = L.pp;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    __shared__ float t[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const bool dp = is_dp(i, k, L.band);
+    for (int q = ty; q < 32; q += 8) {
+        const int r = r0 + tx, c = c0 + q;
+        float v = 0.0f;
+        if (r < nb && c < nb)
+            v = dp ? (float)dp_tile(L, i, k)[(size_t)c * nb + r] : sp_tile(L, i, k)[(size_t)c * nb + r];
+        t[tx][q] = v;
+    }
+    __syncthreads();
+    __nv_bfloat16* P0 = plane(L, i, k, 0);
+    __nv_bfloat16* P1 = plane(L, i, k, 1);
+    __nv_bfloat16* P2 = plane(L, i, k, 2);
+    for (int q = ty; q < 32; q += 8) {
+        const int r = r0 + q, c = c0 + tx;
+        const float v = t[q][tx];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const float r1 = v - __bfloat162float(hi);
+        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(mid);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
+        const size_t e = (size_t)r * pp + c;
+        P0[e] = hi;
+        P1[e] = mid;
+        P2[e] = lo;
+    }
+}
+
+cudaError_t launch_split_panel(const Layout& L, int k, cudaStream_t s) {
+    const int m = L.p - k - 1;
+    dim3 grid(L.pp / 32, L.pp / 32, m);
+    split_panel_kernel<<<grid, 256, 0, s>>>(L, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- tcgen05 GEMM ---
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
+constexpr int TC_STAGES = 2;
+constexpr int TC_PLANE_BYTES = TC_BM * TC_BK * 2;   // 16 KB, one plane chunk (A or B)
+constexpr int TC_STAGE_BYTES = 6 * TC_PLANE_BYTES;  // A hi/mid/lo, B hi/mid/lo
+constexpr int TC_THREADS = 192;
+constexpr int TC_TMEM_COLS = 2 * TC_BN;
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long TC_WAIT_NS = 2000000000LL;      // 2 s per wait
+
+// pairs (a plane, b plane) whose products are kept: small terms first
+__constant__ int c_pair_a[6] = {1, 0, 2, 0, 1, 0};
+__constant__ int c_pair_b[6] = {1, 2, 0, 1, 0, 0};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false after the deadline
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long deadline) {
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 255u && gtimer() > deadline) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N, M
+constexpr uint32_t TC_IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+__device__ __forceinline__ void decode_lp_target(int t, int k, int p, int band, int& i, int& j) {
+    const int m = p - k - 1;
+    for (int d = band; d < m; ++d) {
+        const int cnt = m - d;
+        if (t < cnt) {
+            j = k + 1 + t;
+            i = j + d;
+            return;
+        }
+        t -= cnt;
+    }
+    i = j = -1;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    lp_gemm_tc_kernel(Layout L, const __grid_constant__ CUtensorMap tmap, int k, int nlp) {
+    extern __shared__ uint8_t tc_smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);
+    // bars: full[2], empty[2], tfull[2], tempty[2]; then tmem base + flags
+    volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 8);
+    volatile int* abort_flag = (volatile int*)(bars + 9);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto FULL = [&](int s) { return bar0 + 8u * s; };
+    auto EMPTY = [&](int s) { return bar0 + 8u * (2 + s); };
+    auto TFULL = [&](int a) { return bar0 + 8u * (4 + a); };
+    auto TEMPTY = [&](int a) { return bar0 + 8u * (6 + a); };
+
+    if (threadIdx.x == 0) {
+        *abort_flag = failed(L) ? 1 : 0;
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(FULL(s), 1);
+            mbar_init(EMPTY(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(TFULL(a), 1);
+            mbar_init(TEMPTY(a), 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (*abort_flag) return;   // uniform: decided before any allocation
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void*)tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int nb = L.nb, pp = L.pp, p = L.p;
+    const int nmb = (pp + TC_BM - 1) / TC_BM, nnc = (pp + TC_BN - 1) / TC_BN;
+    const int per_target = nmb * nnc;
+    const int total = nlp * per_target;
+    const int nk = pp / TC_BK;
+    const long long t_start = gtimer();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < total && ok; w += gridDim.x) {
+                int i, j;
+                decode_lp_target(w / per_target, k, p, L.band, i, j);
+                const int rem = w % per_target, mb = rem / nnc, nc = rem % nnc;
+                const int sa = L.slot[i * p + k] * 3, sb = L.slot[j * p + k] * 3;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int st = it % TC_STAGES;
+                    const uint32_t ph = (it / TC_STAGES) & 1;
+                    if (*abort_flag || !mbar_wait(EMPTY(st), ph ^ 1, gtimer() + TC_WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(FULL(st), TC_STAGE_BYTES);
+                    uint8_t* sbase = smem + st * TC_STAGE_BYTES;
+#pragma unroll
+                    for (int s = 0; s < 3; ++s)
+                        tma_load_3d(smem_u32(sbase + s * TC_PLANE_BYTES), &tmap, kc * TC_BK, mb * TC_BM, sa + s,
+                                    FULL(st));
+#pragma unroll
+                    for (int s = 0; s < 3; ++s)
+                        tma_load_3d(smem_u32(sbase + (3 + s) * TC_PLANE_BYTES), &tmap, kc * TC_BK, nc * TC_BN,
+                                    sb + s, FULL(st));
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                set_timeout(L, 1);
+            }
+            // drain: the copies of the last stages issued must land before exit
+            for (int q = max(0, it - TC_STAGES); q < it; ++q)
+                mbar_wait(FULL(q % TC_STAGES), (q / TC_STAGES) & 1, gtimer() + TC_WAIT_NS);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, tc = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < total && ok; w += gridDim.x, ++tc) {
+                const int acc = tc & 1;
+                const uint32_t aph = (tc >> 1) & 1;
+                if (*abort_flag || !mbar_wait(TEMPTY(acc), aph ^ 1, gtimer() + TC_WAIT_NS)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dst = tmem_base + acc * TC_BN;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int st = it % TC_STAGES;
+                    const uint32_t ph = (it / TC_STAGES) & 1;
+                    if (*abort_flag || !mbar_wait(FULL(st), ph, gtimer() + TC_WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sbase = smem_u32(smem + st * TC_STAGE_BYTES);
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const uint32_t a_addr = sbase + c_pair_a[q] * TC_PLANE_BYTES;
+                        const uint32_t b_addr = sbase + (3 + c_pair_b[q]) * TC_PLANE_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk)
+                            umma_bf16(dst, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32),
+                                      (kc | q | kk) != 0);
+                    }
+                    umma_commit(EMPTY(st));   // stage reusable once these MMAs complete
+                }
+                if (!ok) break;
+                umma_commit(TFULL(acc));     // accumulator ready for the epilogue
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                set_timeout(L, 2);
+            }
+            // drain: all issued MMAs retire before TMEM is released
+            if (it > 0) {
+                const int q = it - 1;
+                mbar_wait(EMPTY(q % TC_STAGES), (q / TC_STAGES) & 1, gtimer() + TC_WAIT_NS);
+            }
+        }
+    } else {
+        // epilogue warps 2..5 -> TMEM lane quadrant warp % 4.  Each thread owns one
+        // row of the 128 x 128 block; its 128 C values are loaded into registers
+        // before waiting for the accumulator, so the loads overlap the main loop.
+        const int quad = warp & 3;
+        const int row_in = quad * 32 + lane;
+        int tc = 0;
+        for (int w = blockIdx.x; w < total; w += gridDim.x, ++tc) {
+            const int acc = tc & 1;
+            const uint32_t aph = (tc >> 1) & 1;
+            int i, j;
+            decode_lp_target(w / per_target, k, p, L.band, i, j);
+            const int rem = w % per_target, mb = rem / nnc, nc = rem % nnc;
+            float* C = sp_tile(L, i, j);
+            const int r = mb * TC_BM + row_in;
+            const bool rv = r < nb;
+            // columns [c_begin, c_begin + ncol) of this block exist in the tile
+            const int c_begin = nc * TC_BN;
+            const int ncol = rv ? max(0, min(TC_BN, nb - c_begin)) : 0;
+            float* Crow = C + (size_t)c_begin * nb + (rv ? r : 0);
+            constexpr int HALF = TC_BN / 2;
+            float cpre[HALF];
+#pragma unroll
+            for (int e = 0; e < HALF; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0f;
+            if (*abort_flag || !mbar_wait(TFULL(acc), aph, gtimer() + TC_WAIT_NS)) {
+                if (!*abort_flag) {
+                    *abort_flag = 1;
+                    set_timeout(L, 3);
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * TC_BN;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1) {
+#pragma unroll
+                    for (int e = 0; e < HALF; ++e)
+                        cpre[e] = (HALF + e < ncol) ? Crow[(size_t)(HALF + e) * nb] : 0.0f;
+                }
+#pragma unroll
+                for (int cc = 0; cc < HALF; cc += 16) {
+                    float v[16];
+                    tmem_ld16(taddr + h * HALF + cc, v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) cpre[cc + e] -= v[e];
+                }
+#pragma unroll
+                for (int e = 0; e < HALF; ++e)
+                    if (h * HALF + e < ncol) Crow[(size_t)(h * HALF + e) * nb] = cpre[e];
+            }
+            tc_fence_before();
+            mbar_arrive(TEMPTY(acc));
+        }
+    }
+    (void)t_start;
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------- host side ---
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode() {
+    static PFN_encodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_encodeTiled)p;
+    }
+    return fn;
+}
+
+// 3D map over all planes: (K = pp, rows = pp, plane index = 3 * n_slots).
+static int make_plane_map(const Layout& L, long long nslots, CUtensorMap* map) {
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return 1;
+    cuuint64_t dims[3] = {(cuuint64_t)L.pp, (cuuint64_t)L.pp, (cuuint64_t)(3 * nslots)};
+    cuuint64_t strides[2] = {(cuuint64_t)L.pp * 2, (cuuint64_t)L.pp * L.pp * 2};
+    cuuint32_t box[3] = {TC_BK, TC_BM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)L.planes, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : 2;
+}
+
+int prepare_lp_gemm(geo_tiles* t, const Layout& L) {
+    static_assert(sizeof(CUtensorMap) <= sizeof(((geo_tiles*)0)->tmap), "tensor map storage");
+    if (!L.planes || t->lay.n_slots == 0) return 0;
+    CUtensorMap map;
+    int rc = make_plane_map(L, t->lay.n_slots, &map);
+    if (rc) return rc;
+    memcpy(t->tmap, &map, sizeof(map));
+    return 0;
+}
+
+static int g_num_sms = 0;
+
+cudaError_t launch_lp_gemm_tc(const geo_tiles* t, const Layout& L, int k, int nlp, cudaStream_t s) {
+    static bool attr_set = false;
+    cudaError_t e;
+    if (!attr_set) {
+        if ((e = cudaFuncSetAttribute(lp_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TC_SMEM)))
+            return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        attr_set = true;
+    }
+    const int per_target = ((L.pp + TC_BM - 1) / TC_BM) * ((L.pp + TC_BN - 1) / TC_BN);
+    const long long total = (long long)nlp * per_target;
+    const int grid = (int)std::min<long long>(total, g_num_sms > 0 ? g_num_sms : 148);
+    CUtensorMap map;
+    memcpy(&map, t->tmap, sizeof(map));
+    lp_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(L, map, k, nlp);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace geo

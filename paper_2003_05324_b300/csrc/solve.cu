@@ -1,0 +1,246 @@
+// A10-A11 and A13: log-determinant, forward solve and quadratic form of Eq. 2,
+// and the kriging predictor, from the factored tile store.
+//
+// Forward solve y = L^-1 Z by tile rows: for i = 0..p-1, solve the diagonal
+// tile (FP64, one CTA) and subtract L(l,i) y_i from every later block row
+// (one CTA per 128 rows of each tile; FP32 tiles promoted, FP64 accumulation).
+// The per-tile partial sums of log L_aa and y_a^2 are reduced in a fixed order,
+// so the result is bitwise reproducible.
+#include <math.h>
+
+#include "geo_internal.cuh"
+#include "matern_dev.cuh"
+
+namespace geo {
+
+constexpr int SV_THREADS = 256;
+constexpr int SV_BS = 32;
+
+// Solve L_ii y_i = r_i in place (r_i already holds Z_i minus the earlier block
+// rows' contributions); record sum log L_aa and sum y_a^2 of this tile.
+__global__ void __launch_bounds__(SV_THREADS) trsv_diag_kernel(Layout L, int i, double* __restrict__ yv,
+                                                               double* __restrict__ part) {
+    if (failed(L)) return;
+    const int nb = L.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double* A = dp_tile(L, i, i);
+    double* y = yv + (size_t)i * nb;
+    __shared__ double ys[SV_BS];
+    __shared__ double Db[SV_BS * (SV_BS + 1)];
+    __shared__ double rinv[SV_BS];
+    __shared__ double red[2][SV_THREADS / 32];
+    for (int c0 = 0; c0 < nb; c0 += SV_BS) {
+        const int w = min(SV_BS, nb - c0);
+        for (int idx = tid; idx < w * w; idx += SV_THREADS) {
+            const int r = idx % w, c = idx / w;
+            Db[r * (SV_BS + 1) + c] = A[(size_t)(c0 + c) * nb + c0 + r];
+        }
+        __syncthreads();
+        if (tid < w) rinv[tid] = 1.0 / Db[tid * (SV_BS + 1) + tid];
+        __syncthreads();
+        if (warp == 0) {
+            double v = lane < w ? y[c0 + lane] : 0.0;
+            for (int c = 0; c < w; ++c) {
+                const double xc = __shfl_sync(0xffffffffu, v, c) * rinv[c];
+                if (lane == c) v = xc;
+                if (lane > c && lane < w) v = fma(-Db[lane * (SV_BS + 1) + c], xc, v);
+            }
+            if (lane < w) {
+                ys[lane] = v;
+                y[c0 + lane] = v;
+            }
+        }
+        __syncthreads();
+        for (int r = c0 + w + tid; r < nb; r += SV_THREADS) {
+            double acc = 0.0;
+            for (int c = 0; c < w; ++c) acc = fma(A[(size_t)(c0 + c) * nb + r], ys[c], acc);
+            y[r] -= acc;
+        }
+        __syncthreads();
+    }
+    double ld = 0.0, q = 0.0;
+    for (int a = tid; a < nb; a += SV_THREADS) {
+        ld += log(A[(size_t)a * nb + a]);
+        q = fma(y[a], y[a], q);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ld += __shfl_down_sync(0xffffffffu, ld, o);
+        q += __shfl_down_sync(0xffffffffu, q, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = ld;
+        red[1][warp] = q;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int w2 = 0; w2 < SV_THREADS / 32; ++w2) {
+            s0 += red[0][w2];
+            s1 += red[1][w2];
+        }
+        part[2 * i] = 2.0 * s0;
+        part[2 * i + 1] = s1;
+    }
+}
+
+constexpr int GV_ROWS = 128;
+
+// y_l -= L(l,i) y_i for every block row l > i.
+__global__ void __launch_bounds__(GV_ROWS) trsv_update_kernel(Layout L, int i, double* __restrict__ yv) {
+    if (failed(L)) return;
+    const int nb = L.nb;
+    const int l = i + 1 + blockIdx.y;
+    const int r = blockIdx.x * GV_ROWS + threadIdx.x;
+    extern __shared__ double yi[];
+    for (int c = threadIdx.x; c < nb; c += GV_ROWS) yi[c] = yv[(size_t)i * nb + c];
+    __syncthreads();
+    if (r >= nb) return;
+    double acc = 0.0;
+    if (is_dp(l, i, L.band)) {
+        const double* A = dp_tile(L, l, i);
+        for (int c = 0; c < nb; ++c) acc = fma(A[(size_t)c * nb + r], yi[c], acc);
+    } else {
+        const float* A = sp_tile(L, l, i);
+        for (int c = 0; c < nb; ++c) acc = fma((double)A[(size_t)c * nb + r], yi[c], acc);
+    }
+    yv[(size_t)l * nb + r] -= acc;
+}
+
+__global__ void trsv_load_kernel(Layout L, const double* __restrict__ z, double* __restrict__ yv) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < L.p * L.nb) yv[g] = g < L.n ? z[g] : 0.0;
+}
+
+__global__ void trsv_finish_kernel(Layout L, const double* __restrict__ part, double* logdet, double* quad) {
+    if (threadIdx.x != 0) return;
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < L.p; ++i) {
+        s0 += part[2 * i];
+        s1 += part[2 * i + 1];
+    }
+    *logdet = s0;
+    *quad = s1;
+}
+
+static cudaError_t forward_solve(const Layout& L, double* yv, double* part, cudaStream_t s) {
+    const int p = L.p, nb = L.nb;
+    for (int i = 0; i < p; ++i) {
+        trsv_diag_kernel<<<1, SV_THREADS, 0, s>>>(L, i, yv, part);
+        count_launch();
+        if (i + 1 < p) {
+            trsv_update_kernel<<<dim3((nb + GV_ROWS - 1) / GV_ROWS, p - i - 1), GV_ROWS, nb * sizeof(double), s>>>(
+                L, i, yv);
+            count_launch();
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, double* quad, double* y,
+                            cudaStream_t s) {
+    double* yv = y ? y : L.scal + 2 * L.p + 8;
+    double* part = L.scal;
+    const int np = L.p * L.nb;
+    trsv_load_kernel<<<(np + 255) / 256, 256, 0, s>>>(L, z, yv);
+    count_launch();
+    cudaError_t e = forward_solve(L, yv, part, s);
+    if (e) return e;
+    trsv_finish_kernel<<<1, 32, 0, s>>>(L, part, logdet, quad);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- kriging ---
+// Back solve L' alpha = y, tile row by tile row from the bottom.
+__global__ void __launch_bounds__(256) trsv_t_diag_kernel(Layout L, int i, double* __restrict__ w) {
+    if (failed(L)) return;
+    const int nb = L.nb, tid = threadIdx.x;
+    const double* A = dp_tile(L, i, i);
+    double* v = w + (size_t)i * nb;
+    __shared__ double red[8];
+    // alpha_a = (v_a - sum_{b>a} L[b][a] alpha_b) / L[a][a], a from nb-1 down
+    for (int a = nb - 1; a >= 0; --a) {
+        double acc = 0.0;
+        for (int b = a + 1 + tid; b < nb; b += 256) acc = fma(A[(size_t)a * nb + b], v[b], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if ((tid & 31) == 0) red[tid >> 5] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            double sacc = 0.0;
+            for (int q = 0; q < 8; ++q) sacc += red[q];
+            v[a] = (v[a] - sacc) / A[(size_t)a * nb + a];
+        }
+        __syncthreads();
+    }
+}
+
+// w_j -= L(i,j)' alpha_i for every block row j < i; one warp per column.
+__global__ void __launch_bounds__(256) trsv_t_update_kernel(Layout L, int i, double* __restrict__ w) {
+    if (failed(L)) return;
+    const int nb = L.nb;
+    const int j = blockIdx.y;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= nb) return;
+    const double* al = w + (size_t)i * nb;
+    double acc = 0.0;
+    if (is_dp(i, j, L.band)) {
+        const double* A = dp_tile(L, i, j) + (size_t)c * nb;
+        for (int a = lane; a < nb; a += 32) acc = fma(A[a], al[a], acc);
+    } else {
+        const float* A = sp_tile(L, i, j) + (size_t)c * nb;
+        for (int a = lane; a < nb; a += 32) acc = fma((double)A[a], al[a], acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) w[(size_t)j * nb + c] -= acc;
+}
+
+// zhat_q = sum_a C(||s_new_q - s_a||) alpha_a, one CTA per new point.
+__global__ void __launch_bounds__(256) krige_cross_kernel(Layout L, const double* __restrict__ x,
+                                                          const double* __restrict__ y,
+                                                          const double* __restrict__ alpha, MaternP mp,
+                                                          const double* __restrict__ xn,
+                                                          const double* __restrict__ yn, double* __restrict__ zhat) {
+    const int q = blockIdx.x, tid = threadIdx.x;
+    const double xq = xn[q], yq = yn[q];
+    double acc = 0.0;
+    for (int a = tid; a < L.n; a += 256) {
+        const double dx = xq - x[a], dy = yq - y[a];
+        const double r = sqrt(dx * dx + dy * dy);
+        const double c = (r == 0.0) ? mp.sigma2 : matern_fp64(r * mp.inv_beta, mp);
+        acc = fma(c, alpha[a], acc);
+    }
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w2 = 0; w2 < 8; ++w2) s += red[w2];
+        zhat[q] = s;
+    }
+}
+
+cudaError_t run_krige(const Layout& L, const double* x, const double* y, const double* z, const MaternP& mp,
+                      const double* xn, const double* yn, int m, double* zhat, double* work, cudaStream_t s) {
+    const int p = L.p, nb = L.nb, np = p * nb;
+    double* w = work;             // y, then alpha, in place
+    double* part = work + np;     // per-tile partials (unused here)
+    trsv_load_kernel<<<(np + 255) / 256, 256, 0, s>>>(L, z, w);
+    count_launch();
+    cudaError_t e = forward_solve(L, w, part, s);
+    if (e) return e;
+    for (int i = p - 1; i >= 0; --i) {
+        trsv_t_diag_kernel<<<1, 256, 0, s>>>(L, i, w);
+        count_launch();
+        if (i > 0) {
+            trsv_t_update_kernel<<<dim3((nb + 7) / 8, i), 256, 0, s>>>(L, i, w);
+            count_launch();
+        }
+    }
+    if (m > 0) {
+        krige_cross_kernel<<<m, 256, 0, s>>>(L, x, y, w, mp, xn, yn, zhat);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace geo

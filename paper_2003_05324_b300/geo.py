@@ -1,0 +1,286 @@
+"""Thin Python binding of libgeo.so (include/geo.h): argument marshalling only.
+
+Every step of the likelihood runs in the library's CUDA kernels; torch is used
+only to own device memory and to name the current stream.  Importing this
+module loads the in-tree shared library and raises if it is missing: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgeo.so")
+
+LOG_2PI = math.log(2.0 * math.pi)
+
+GEO_OK = 0
+GEO_ERR_NOT_SPD = 1
+GEO_ERR_TIMEOUT = 2
+GEO_ERR_CUDA = 3
+GEO_ERR_UNSUPPORTED = 4
+GEO_LP_SPLIT_BF16 = 0
+GEO_LP_FP32 = 1
+GEO_FLAG_FP64_OFFBAND_GEN = 1
+
+
+class GeoError(RuntimeError):
+    def __init__(self, code: int, what: str, info: int = 0):
+        super().__init__(f"{what} failed with code {code}" + (f" (info={info})" if info else ""))
+        self.code = code
+        self.info = info
+
+
+class NotSPDError(GeoError):
+    pass
+
+
+class geo_theta(ctypes.Structure):
+    _fields_ = [("sigma2", ctypes.c_double), ("beta", ctypes.c_double),
+                ("nu", ctypes.c_double), ("nugget", ctypes.c_double)]
+
+
+class geo_layout(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nb", ctypes.c_int), ("p", ctypes.c_int), ("band", ctypes.c_int),
+                ("lp_mode", ctypes.c_int), ("pp", ctypes.c_int),
+                ("n_dp_tiles", ctypes.c_longlong), ("n_sp_tiles", ctypes.c_longlong),
+                ("n_slots", ctypes.c_longlong),
+                ("bytes_dp", ctypes.c_size_t), ("bytes_sp", ctypes.c_size_t),
+                ("bytes_planes", ctypes.c_size_t), ("bytes_meta", ctypes.c_size_t)]
+
+
+class geo_tiles(ctypes.Structure):
+    _fields_ = [("lay", geo_layout), ("d_dp", ctypes.c_void_p), ("d_sp", ctypes.c_void_p),
+                ("d_planes", ctypes.c_void_p), ("d_meta", ctypes.c_void_p),
+                ("aux_stream", ctypes.c_void_p), ("ev_fork", ctypes.c_void_p), ("ev_join", ctypes.c_void_p),
+                ("tmap", ctypes.c_uint64 * 16), ("flags", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgeo.so not built at {LIB_PATH}; run paper_2003_05324_b300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "geo_morton_order": [P, P, I, P],
+        "geo_layout_init": [I, I, I, I, ctypes.POINTER(geo_layout)],
+        "geo_tiles_bind": [ctypes.POINTER(geo_tiles), ctypes.POINTER(geo_layout), P, P, P, P, P],
+        "geo_tiles_release": [ctypes.POINTER(geo_tiles)],
+        "geo_tiles_set_flags": [ctypes.POINTER(geo_tiles), I],
+        "geo_matern_tiles": [ctypes.POINTER(geo_tiles), P, P, geo_theta, P],
+        "geo_tiles_load_dense": [ctypes.POINTER(geo_tiles), P, P],
+        "geo_tiles_to_dense": [ctypes.POINTER(geo_tiles), P, P],
+        "geo_potrf_mp": [ctypes.POINTER(geo_tiles), P],
+        "geo_logdet_trsv": [ctypes.POINTER(geo_tiles), P, P, P, P, P],
+        "geo_status": [ctypes.POINTER(geo_tiles), ctypes.POINTER(I), ctypes.POINTER(I), P],
+        "geo_loglik": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, ctypes.POINTER(D), ctypes.POINTER(I), P],
+        "geo_krige": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, P, P, I, P, P, P],
+    }
+    sig.update({
+        "geo_profile_enable": [I],
+        "geo_profile_reset": [],
+        "geo_profile_read": [I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
+    })
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.geo_kernel_launches.argtypes = []
+    lib.geo_kernel_launches.restype = ctypes.c_ulonglong
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc: int, what: str, info: int = 0):
+    if rc == GEO_OK:
+        return
+    if rc == GEO_ERR_NOT_SPD:
+        raise NotSPDError(rc, what, info)
+    raise GeoError(rc, what, info)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+@dataclass(frozen=True)
+class Theta:
+    """Matern parameters of Eq. 1 (theta1 = sigma2, theta2 = beta, theta3 = nu) and a nugget."""
+    sigma2: float
+    beta: float
+    nu: float
+    nugget: float = 0.0
+
+    def c(self) -> geo_theta:
+        return geo_theta(float(self.sigma2), float(self.beta), float(self.nu), float(self.nugget))
+
+
+def morton_order(x, y) -> np.ndarray:
+    """Z-order permutation (host), perm[new] = old index."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n = x.shape[0]
+    perm = np.empty(n, dtype=np.int32)
+    _check(lib.geo_morton_order(x.ctypes.data, y.ctypes.data, n, perm.ctypes.data), "geo_morton_order")
+    return perm.astype(np.int64)
+
+
+def layout(n: int, nb: int, band: int, lp_mode: int = GEO_LP_SPLIT_BF16) -> geo_layout:
+    lay = geo_layout()
+    _check(lib.geo_layout_init(int(n), int(nb), int(band), int(lp_mode), ctypes.byref(lay)), "geo_layout_init")
+    return lay
+
+
+class TileStore:
+    """One problem's tile store in device memory (owned by torch tensors)."""
+
+    def __init__(self, n: int, nb: int, band: int, lp_mode: int = GEO_LP_SPLIT_BF16, device="cuda"):
+        import torch
+        self.lay = layout(n, nb, band, lp_mode)
+        dev = torch.device(device)
+
+        def buf(nbytes):
+            return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+        self._dp = buf(self.lay.bytes_dp)
+        self._sp = buf(self.lay.bytes_sp)
+        self._planes = buf(self.lay.bytes_planes) if self.lay.bytes_planes else None
+        self._meta = buf(self.lay.bytes_meta)
+        self.t = geo_tiles()
+        _check(lib.geo_tiles_bind(ctypes.byref(self.t), ctypes.byref(self.lay), _ptr(self._dp), _ptr(self._sp),
+                                  _ptr(self._planes), _ptr(self._meta), _stream()), "geo_tiles_bind")
+
+    def set_flags(self, flags: int):
+        _check(lib.geo_tiles_set_flags(ctypes.byref(self.t), int(flags)), "geo_tiles_set_flags")
+
+    def __del__(self):
+        try:
+            lib.geo_tiles_release(ctypes.byref(self.t))
+        except Exception:
+            pass
+
+    @property
+    def n(self):
+        return self.lay.n
+
+    @property
+    def nb(self):
+        return self.lay.nb
+
+    @property
+    def p(self):
+        return self.lay.p
+
+    @property
+    def band(self):
+        return self.lay.band
+
+    def matern(self, x, y, theta: Theta, stream=None):
+        _check(lib.geo_matern_tiles(ctypes.byref(self.t), _ptr(x), _ptr(y), theta.c(), _stream(stream)),
+               "geo_matern_tiles")
+
+    def load_dense(self, a, stream=None):
+        _check(lib.geo_tiles_load_dense(ctypes.byref(self.t), _ptr(a), _stream(stream)), "geo_tiles_load_dense")
+
+    def to_dense(self, stream=None):
+        import torch
+        out = torch.empty((self.n, self.n), dtype=torch.float64, device=self._dp.device)
+        _check(lib.geo_tiles_to_dense(ctypes.byref(self.t), _ptr(out), _stream(stream)), "geo_tiles_to_dense")
+        return out.t()  # stored column-major: transpose the row-major view
+
+    def potrf(self, stream=None, check=True):
+        _check(lib.geo_potrf_mp(ctypes.byref(self.t), _stream(stream)), "geo_potrf_mp")
+        if check:
+            code, info = self.status(stream)
+            _check(code, "geo_potrf_mp", info)
+
+    def status(self, stream=None):
+        code, info = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib.geo_status(ctypes.byref(self.t), ctypes.byref(code), ctypes.byref(info), _stream(stream)),
+               "geo_status")
+        return code.value, info.value
+
+    def logdet_trsv(self, z, stream=None, want_y=False):
+        import torch
+        dev = self._dp.device
+        ld = torch.empty(1, dtype=torch.float64, device=dev)
+        q = torch.empty(1, dtype=torch.float64, device=dev)
+        yv = torch.empty(self.p * self.nb, dtype=torch.float64, device=dev) if want_y else None
+        _check(lib.geo_logdet_trsv(ctypes.byref(self.t), _ptr(z), _ptr(ld), _ptr(q), _ptr(yv), _stream(stream)),
+               "geo_logdet_trsv")
+        return ld, q, yv
+
+    def loglik_async(self, x, y, z, theta: Theta, stream=None):
+        """Generation, factorization, log-det and solve enqueued on the stream without
+        waiting; returns device scalars (logdet, quad).  Assembly of Eq. 2 from them
+        is two scalar operations (`assemble`)."""
+        self.matern(x, y, theta, stream)
+        _check(lib.geo_potrf_mp(ctypes.byref(self.t), _stream(stream)), "geo_potrf_mp")
+        ld, q, _ = self.logdet_trsv(z, stream)
+        return ld, q
+
+    def assemble(self, ld: float, q: float) -> float:
+        return -0.5 * self.n * LOG_2PI - 0.5 * ld - 0.5 * q
+
+    def loglik(self, x, y, z, theta: Theta, stream=None):
+        """Eq. 2 (blocking): returns (loglik, logdet, quad)."""
+        out = (ctypes.c_double * 3)()
+        info = ctypes.c_int(0)
+        rc = lib.geo_loglik(ctypes.byref(self.t), _ptr(x), _ptr(y), _ptr(z), theta.c(), out,
+                            ctypes.byref(info), _stream(stream))
+        _check(rc, "geo_loglik", info.value)
+        return out[0], out[1], out[2]
+
+    def krige(self, x, y, z, theta: Theta, xnew, ynew, stream=None):
+        """Simple-kriging prediction at (xnew, ynew) from the factored store."""
+        import torch
+        dev = self._dp.device
+        m = int(xnew.shape[0])
+        zhat = torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+        work = torch.empty(2 * self.p * self.nb, dtype=torch.float64, device=dev)
+        _check(lib.geo_krige(ctypes.byref(self.t), _ptr(x), _ptr(y), _ptr(z), theta.c(), _ptr(xnew), _ptr(ynew), m,
+                             _ptr(zhat), _ptr(work), _stream(stream)), "geo_krige")
+        return zhat[:m]
+
+
+PROF_FP64_UPDATE, PROF_LP_UPDATE, PROF_POTRF, PROF_TRSM = 0, 1, 2, 3
+
+
+def kernel_launches() -> int:
+    """Kernel launches issued by the library in this process."""
+    return int(lib.geo_kernel_launches())
+
+
+def profile_enable(on: bool = True):
+    _check(lib.geo_profile_enable(1 if on else 0), "geo_profile_enable")
+
+
+def profile_reset():
+    _check(lib.geo_profile_reset(), "geo_profile_reset")
+
+
+def profile_read(kind: int):
+    """(total ms, launches) of one instrumented kernel kind since the last reset."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
+    _check(lib.geo_profile_read(int(kind), ctypes.byref(ms), ctypes.byref(n)), "geo_profile_read")
+    return ms.value, n.value
+
+
+def loglik_flops(n: int) -> float:
+    """Algorithmic flop count of one factorization, n^3/3."""
+    return n ** 3 / 3.0
+
+

@@ -1,0 +1,85 @@
+"""CPU-side checks of the C ABI: the library loads, exports every declared
+symbol, sizes layouts as documented, rejects bad arguments before touching
+the device, and its host-side Morton order matches the oracle bit for bit."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import geo_oracle as O
+from paper_2003_05324_b300 import geo, inputs
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "geo.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^int\s+(geo_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert len(names) >= 12
+    lib = ctypes.CDLL(geo.LIB_PATH)
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def test_struct_sizes_match_header():
+    # geo_theta: 4 doubles; geo_tiles = layout + 7 pointers + 16 u64 + int flags (padded)
+    assert ctypes.sizeof(geo.geo_theta) == 32
+    assert ctypes.sizeof(geo.geo_tiles) == ctypes.sizeof(geo.geo_layout) + 7 * 8 + 128 + 8  # int + pad
+
+
+@pytest.mark.parametrize("n,nb,band", [(1600, 200, 8), (40000, 500, 1), (1000, 96, 2), (50, 64, 1), (1, 16, 1),
+                                       (129600, 720, 3)])
+def test_layout_counts(n, nb, band):
+    lay = geo.layout(n, nb, band)
+    p = -(-n // nb)
+    assert lay.p == p and lay.nb == nb and lay.band == min(band, p)
+    ndp = sum(1 for j in range(p) for i in range(j, p) if i - j < lay.band)
+    assert lay.n_dp_tiles == ndp
+    assert lay.n_dp_tiles + lay.n_sp_tiles == p * (p + 1) // 2
+    assert lay.bytes_dp >= ndp * nb * nb * 8
+    assert lay.bytes_sp >= lay.n_sp_tiles * nb * nb * 4
+    assert lay.pp % 64 == 0 and lay.pp >= nb
+    if lay.n_sp_tiles:
+        assert lay.bytes_planes >= 3 * lay.pp ** 2 * 2 * p * (p - 1) // 2
+    assert geo.layout(n, nb, band, geo.GEO_LP_FP32).bytes_planes == 0
+
+
+def test_layout_rejects_bad_arguments():
+    lay = geo.geo_layout()
+    L = geo.lib
+    assert L.geo_layout_init(0, 64, 1, 0, ctypes.byref(lay)) == -1
+    assert L.geo_layout_init(100, 8, 1, 0, ctypes.byref(lay)) == -2
+    assert L.geo_layout_init(100, 2048, 1, 0, ctypes.byref(lay)) == -2
+    assert L.geo_layout_init(100, 64, 0, 0, ctypes.byref(lay)) == -3
+    assert L.geo_layout_init(100, 64, 1, 7, ctypes.byref(lay)) == -4
+    assert L.geo_layout_init(100, 64, 1, 0, None) == -5
+
+
+def test_entry_points_reject_null_arguments_without_device_work():
+    L = geo.lib
+    t = geo.geo_tiles()   # unbound: null device buffers
+    th = geo.Theta(1.0, 0.1, 0.5).c()
+    assert L.geo_matern_tiles(ctypes.byref(t), None, None, th, None) == -1
+    assert L.geo_potrf_mp(None, None) == -1
+    assert L.geo_logdet_trsv(ctypes.byref(t), None, None, None, None, None) == -1
+    assert L.geo_loglik(None, None, None, None, th, None, None, None) == -1
+    assert L.geo_krige(None, None, None, None, th, None, None, 0, None, None, None) == -1
+    assert L.geo_tiles_bind(None, None, None, None, None, None, None) == -1
+    assert L.geo_morton_order(None, None, 3, None) == -1
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_morton_order_matches_oracle(seed):
+    x, y = inputs.jittered_grid(23, seed=seed)
+    # add exact ties and out-of-range values to exercise clamping and tie order
+    x = np.concatenate([x, [0.5, 0.5, -0.1, 1.3]])
+    y = np.concatenate([y, [0.25, 0.25, 0.2, 0.9]])
+    got = geo.morton_order(x, y)
+    want = O.morton_order(x, y)
+    assert np.array_equal(got, want)

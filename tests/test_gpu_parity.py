@@ -1,0 +1,277 @@
+"""GPU parity of the CUDA path against the oracle, through the C ABI.
+
+Tolerances:
+  * FP64 Matern entries: 1e-13 relative (+1e-15 sigma2 absolute) -- the
+    trapezoid K_nu and CUDA's exp/log each contribute ~1e-14.
+  * FP32 Matern entries: computed in FP32 from coordinates pre-scaled by 1/beta
+    and split into float hi + lo.  With u = 2^-24: the scaled difference carries
+    <= 2u, its square and the sum <= 6u, the square root halves that and adds
+    <= 1u, so x = r/beta carries <= 4u; exp(-x) has condition number x and
+    CUDA's expf <= 2 ulp (<= 4u); sigma2's rounding and the product add 2u, the
+    closed-form polynomials <= 2u more: |dv| <= (4x + 8) u |v|.  The
+    trapezoid K_nu adds the errors of its exponents (<= 20 in the cut-off
+    terms, <= a few in the dominant ones) and of its sum: (4x + 40) u |v|.
+  * all-FP64 log-likelihood: |dl|/|l| <= 1e-10 (the stated gate).
+  * mixed precision: |dl|/|l| <= 1e-6 against the FP64 oracle (the stated gate).
+    Element-wise, the GPU's and the oracle's Algorithm 1 factors are two
+    FP32-level approximations of the FP64 factor that differ in rounding order
+    only; the GPU's distance to the FP64 factor must stay within twice the
+    oracle's, hence (triangle inequality) within three times of the oracle's
+    factor itself.  Its log-likelihood error must stay within four times the
+    oracle's (plus 1e-9 relative).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import geo_oracle as O  # noqa: E402
+from paper_2003_05324_b300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_05324_b300 import geo
+    return geo
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def problem(m, seed, theta, morton=True):
+    x, y = inputs.jittered_grid(m, seed=seed)
+    if morton:
+        perm = O.morton_order(x, y)
+        x, y = x[perm], y[perm]
+    z = inputs.matern_field_rff(x, y, theta.sigma2, theta.beta, theta.nu, seed=seed + 1, nugget=theta.nugget)
+    return x, y, z
+
+
+def oracle_theta(th):
+    return O.Theta(th.sigma2, th.beta, th.nu, th.nugget)
+
+
+# ------------------------------------------------------------- A2: Eq. 1 ---
+@pytest.mark.parametrize("nu", [0.5, 1.0, 1.5, 0.8, 2.5])
+def test_matern_tiles_match_oracle(G, nu):
+    th = G.Theta(1.3, 0.07, nu, 1e-4)
+    x, y = inputs.uniform_points(700, seed=3)
+    ts = G.TileStore(700, 96, 2, G.GEO_LP_FP32)   # ragged: p = 8, last tile 28 rows
+    ts.matern(dev(x), dev(y), th)
+    got = ts.to_dense().cpu().numpy()
+    want = np.tril(O.covariance(x, y, theta=oracle_theta(th)))
+    nb, band = 96, 2
+    I, J = np.indices(want.shape)
+    dpm = (I // nb - J // nb) < band
+    lower = I >= J
+    m64 = dpm & lower
+    err = np.abs(got - want)
+    assert np.all(err[m64] <= 1e-13 * np.abs(want[m64]) + 1e-15 * th.sigma2)
+    m32 = (~dpm) & lower
+    r = np.sqrt((x[I] - x[J]) ** 2 + (y[I] - y[J]) ** 2)
+    xr = r / th.beta
+    cnu = 8.0 if nu in (0.5, 1.5, 2.5) else 40.0
+    bound = (4.0 * xr + cnu) * 2.0 ** -24 * np.abs(want) + 2.0 ** -126
+    viol = m32 & (err > bound)
+    if viol.any():
+        idx = np.argsort(-(err / bound)[viol])[:5]
+        worst = [(float(xr[viol][q]), float(err[viol][q] / max(abs(want[viol][q]), 1e-300) / 2.0 ** -24))
+                 for q in idx]
+        raise AssertionError(f"{int(viol.sum())} FP32 entries over the bound; worst (x, ulps): {worst}")
+    assert np.all(got[~lower] == 0.0)
+
+
+# --------------------------------------------------- A3-A9 factor parity ---
+def spd_matrix(n, seed, nu=0.5, beta=0.1, nugget=1e-3):
+    x, y = inputs.uniform_points(n, seed=seed)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    return O.covariance(x, y, theta=O.Theta(1.0, beta, nu, nugget))
+
+
+@pytest.mark.parametrize("n,nb", [(640, 128), (700, 96), (500, 500), (37, 64)])
+def test_fp64_factor_matches_oracle(G, n, nb):
+    S = spd_matrix(n, seed=n)
+    p = -(-n // nb)
+    ts = G.TileStore(n, nb, p, G.GEO_LP_FP32)   # band = p: all FP64
+    ts.load_dense(dev(S.T))                      # column-major upload
+    ts.potrf()
+    got = ts.to_dense().cpu().numpy()
+    Lo, info = O.dense_factor(S)
+    assert info == 0
+    assert np.max(np.abs(got - Lo)) <= 1e-12 * np.max(np.abs(Lo))
+
+
+@pytest.mark.parametrize("band,lp", [(1, "fp32"), (2, "fp32"), (1, "bf16"), (3, "bf16")])
+def test_mixed_factor_matches_algorithm1(G, band, lp):
+    n, nb = 768, 96   # p = 8
+    S = spd_matrix(n, seed=5)
+    mode = G.GEO_LP_FP32 if lp == "fp32" else G.GEO_LP_SPLIT_BF16
+    ts = G.TileStore(n, nb, band, mode)
+    ts.load_dense(dev(S.T))
+    ts.potrf()
+    got = ts.to_dense().cpu().numpy()
+    Lmp, info = O.mp_tile_cholesky(S, nb, band)
+    Ldp, _ = O.dense_factor(S)
+    assert info == 0
+    ref_err = np.max(np.abs(Lmp - Ldp))
+    assert ref_err > 0
+    assert np.max(np.abs(got - Ldp)) <= 2.0 * ref_err
+    assert np.max(np.abs(got - Lmp)) <= 3.0 * ref_err
+    # in-band tiles of the first block column see no FP32 input: FP64-exact parity
+    assert np.max(np.abs(got[:band * nb, :nb] - Ldp[:band * nb, :nb])) <= 1e-12
+
+
+def test_not_spd_reports_failing_row(G):
+    S = spd_matrix(300, seed=9)
+    S[211, 211] = -1.0
+    for band in (1, 5):
+        ts = G.TileStore(300, 64, band, G.GEO_LP_FP32)
+        ts.load_dense(dev(S.T))
+        with pytest.raises(G.NotSPDError) as ei:
+            ts.potrf()
+        _, info = O.dense_factor(S)
+        assert ei.value.info == info == 212
+
+
+# ------------------------------------------------------ A10-A12: Eq. 2 ---
+def test_loglik_fp64_config_n1600(G):
+    # 40 x 40 jittered grid, Morton order, sigma2=1, beta=0.1, nu=0.5, Z = L w;
+    # tile 200, all 8 x 8 tiles FP64
+    th = G.Theta(1.0, 0.1, 0.5)
+    x, y = inputs.jittered_grid(40, seed=0)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    S = O.covariance(x, y, theta=oracle_theta(th))
+    Lo, _ = O.dense_factor(S)
+    z = Lo @ inputs.white_noise(1600, seed=1)
+    want = O.loglik_dense(x, y, z, oracle_theta(th))
+    ts = G.TileStore(1600, 200, 8, G.GEO_LP_SPLIT_BF16)
+    l, ld, q = ts.loglik(dev(x), dev(y), dev(z), th)
+    assert abs(l - want["loglik"]) <= 1e-10 * abs(want["loglik"])
+    assert abs(ld - want["logdet"]) <= 1e-10 * abs(want["logdet"])
+    assert abs(q - want["quad"]) <= 1e-10 * abs(want["quad"])
+
+
+@pytest.mark.parametrize("band", [1, 2, 4])
+@pytest.mark.parametrize("lp", ["fp32", "bf16"])
+def test_loglik_mixed_precision_gate(G, band, lp):
+    # n = 1600 geometry with the n = 40,000 workload's parameters: the stated
+    # gate |dl|/|l| <= 1e-6 against the FP64 oracle, generation included
+    th = G.Theta(1.0, 0.1, 0.5)
+    x, y, z = problem(40, 0, th)
+    want = O.loglik_dense(x, y, z, oracle_theta(th))["loglik"]
+    mode = G.GEO_LP_FP32 if lp == "fp32" else G.GEO_LP_SPLIT_BF16
+    ts = G.TileStore(1600, 200, band, mode)
+    l, _, _ = ts.loglik(dev(x), dev(y), dev(z), th)
+    assert abs(l - want) / abs(want) <= 1e-6
+
+
+def oracle_mp_from_matrix(S, z, nb, band):
+    L, info = O.mp_tile_cholesky(S, nb, band)
+    assert info == 0
+    ld, q = O.factor_logdet_quad(L, z)
+    return -0.5 * len(z) * math.log(2 * math.pi) - 0.5 * ld - 0.5 * q
+
+
+@pytest.mark.parametrize("band", [1, 2, 4])
+@pytest.mark.parametrize("lp", ["fp32", "bf16"])
+def test_factor_solve_matches_algorithm1(G, band, lp):
+    # same rounded covariance on both sides: potrf + log-det + solve of the GPU
+    # against the oracle's Algorithm 1 (error vs FP64 within 4x the oracle's)
+    th = O.Theta(1.0, 0.1, 0.5)
+    x, y, z = problem(40, 0, G.Theta(1.0, 0.1, 0.5))
+    S = O.covariance(x, y, theta=th)
+    Ld, _ = O.dense_factor(S)
+    ld, q = O.factor_logdet_quad(Ld, z)
+    want = -0.5 * 1600 * math.log(2 * math.pi) - 0.5 * ld - 0.5 * q
+    mp = oracle_mp_from_matrix(S, z, 200, band)
+    mode = G.GEO_LP_FP32 if lp == "fp32" else G.GEO_LP_SPLIT_BF16
+    ts = G.TileStore(1600, 200, band, mode)
+    ts.load_dense(dev(S.T))
+    ts.potrf()
+    gld, gq, _ = ts.logdet_trsv(dev(z))
+    got = -0.5 * 1600 * math.log(2 * math.pi) - 0.5 * float(gld) - 0.5 * float(gq)
+    assert abs(got - want) <= 4 * abs(mp - want) + 1e-12 * abs(want)
+
+
+@pytest.mark.parametrize("n,nb,band", [(1000, 96, 2), (50, 64, 1), (1, 16, 1), (333, 32, 3)])
+def test_loglik_ragged_sizes(G, n, nb, band):
+    th = G.Theta(0.8, 0.05, 1.0, 1e-4)
+    x, y = inputs.uniform_points(n, seed=n)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.matern_field_rff(x, y, 0.8, 0.05, 1.0, seed=2, nugget=1e-4)
+    want = O.loglik_dense(x, y, z, oracle_theta(th))["loglik"]
+    mp = O.loglik_mp(x, y, z, oracle_theta(th), nb, band)["loglik"]
+    p = -(-n // nb)
+    ts = G.TileStore(n, nb, p, G.GEO_LP_FP32)
+    l, _, _ = ts.loglik(dev(x), dev(y), dev(z), th)
+    assert abs(l - want) <= 1e-10 * abs(want)
+    for mode in (G.GEO_LP_FP32, G.GEO_LP_SPLIT_BF16):
+        ts2 = G.TileStore(n, nb, band, mode)
+        l2, _, _ = ts2.loglik(dev(x), dev(y), dev(z), th)
+        assert abs(l2 - want) <= max(1e-6 * abs(want), 4 * abs(mp - want))
+
+
+def test_loglik_identity_covariance_is_exact(G):
+    th = G.Theta(1.0, 1e-6, 0.5)
+    x, y = inputs.jittered_grid(30, seed=4)
+    z = inputs.white_noise(900, seed=5)
+    want = -0.5 * 900 * math.log(2 * math.pi) - 0.5 * math.fsum((z * z).tolist())
+    for band in (1, 3):
+        ts = G.TileStore(900, 128, band, G.GEO_LP_SPLIT_BF16)
+        l, ld, q = ts.loglik(dev(x), dev(y), dev(z), th)
+        assert ld == 0.0
+        assert abs(l - want) <= 1e-13 * abs(want)
+
+
+def markov(x, z, s2, beta):
+    d = np.diff(x)
+    rho = np.exp(-d / beta)
+    one_m = -np.expm1(-2 * d / beta)
+    logdet = math.log(s2) + math.fsum(np.log(s2 * one_m).tolist())
+    quad = z[0] ** 2 / s2 + math.fsum(((z[1:] - rho * z[:-1]) ** 2 / (s2 * one_m)).tolist())
+    return -0.5 * len(z) * math.log(2 * math.pi) - 0.5 * logdet - 0.5 * quad
+
+
+def test_loglik_markov_closed_form_fp64(G):
+    n = 6000
+    x, y = inputs.line_points(n, seed=7, min_gap=0.2)
+    z = inputs.white_noise(n, seed=8)
+    want = markov(x, z, 1.1, 0.002)
+    ts = G.TileStore(n, 500, 100, G.GEO_LP_FP32)
+    l, _, _ = ts.loglik(dev(x), dev(y), dev(z), G.Theta(1.1, 0.002, 0.5))
+    assert abs(l - want) <= 1e-10 * abs(want)
+
+
+def test_loglik_deterministic(G):
+    th = G.Theta(1.0, 0.1, 1.0)
+    x, y, z = problem(30, 3, th)
+    ts = G.TileStore(900, 128, 2, G.GEO_LP_SPLIT_BF16)
+    a = ts.loglik(dev(x), dev(y), dev(z), th)
+    b = ts.loglik(dev(x), dev(y), dev(z), th)
+    assert a == b
+
+
+# ------------------------------------------------------------ A13: kriging ---
+@pytest.mark.parametrize("nu", [0.5, 1.5])
+def test_krige_matches_oracle(G, nu):
+    th = G.Theta(1.0, 0.1, nu, 1e-6)
+    x, y = inputs.uniform_points(1200, seed=11)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.matern_field_rff(x, y, 1.0, 0.1, nu, seed=12)
+    xn, yn = inputs.uniform_points(40, seed=13)
+    want = O.krige(x, y, z, oracle_theta(th), xn, yn)
+    ts = G.TileStore(1200, 128, 10, G.GEO_LP_FP32)
+    ts.matern(dev(x), dev(y), th)
+    ts.potrf()
+    got = ts.krige(dev(x), dev(y), dev(z), th, dev(xn), dev(yn)).cpu().numpy()
+    np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-9)
