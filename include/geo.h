@@ -46,9 +46,11 @@ extern "C" {
 #define GEO_ERR_CUDA 3         /* a CUDA runtime call failed */
 #define GEO_ERR_UNSUPPORTED 4  /* a valid but unimplemented configuration */
 
-/* LP (off-band) arithmetic.  GEO_LP_SPLIT_BF16 runs the off-band updates as
- * FP32-accurate products of three BF16 planes (six products) on the tcgen05
- * tensor cores with FP32 accumulation; GEO_LP_FP32 runs them as FP32 FMA on
+/* LP (off-band) arithmetic.  GEO_LP_SPLIT_BF16 runs the off-band updates on
+ * the tcgen05 tensor cores: each FP32 panel row is scaled by a power of two and
+ * cut into three 8-bit integer slices held exactly in BF16; six slice products
+ * (those of weight >= 2^-16 of the leading one) are accumulated in FP32 tensor
+ * memory, the leading product exactly.  GEO_LP_FP32 runs them as FP32 FMA on
  * the CUDA cores.  Both store off-band tiles in FP32. */
 #define GEO_LP_SPLIT_BF16 0
 #define GEO_LP_FP32 1
@@ -67,7 +69,7 @@ typedef struct geo_layout {
     long long n_dp_tiles, n_sp_tiles, n_slots;
     size_t bytes_dp;              /* FP64 tile store */
     size_t bytes_sp;              /* FP32 tile store */
-    size_t bytes_planes;          /* BF16 split planes of panel tiles (0 for GEO_LP_FP32) */
+    size_t bytes_planes;          /* BF16 slice planes + row exponents of panel tiles (0 for GEO_LP_FP32) */
     size_t bytes_meta;            /* offset tables and status words */
 } geo_layout;
 
@@ -81,7 +83,7 @@ typedef struct geo_tiles {
     void* aux_stream;             /* library-created stream for concurrent off-band work */
     void* ev_fork;
     void* ev_join;
-    unsigned long long tmap[16];  /* library-private: TMA descriptor of the BF16 planes */
+    unsigned long long tmap[32];  /* library-private: TMA descriptors of the BF16 planes */
     int flags;                    /* GEO_FLAG_* options, set with geo_tiles_set_flags */
 } geo_tiles;
 

@@ -110,6 +110,9 @@ Layout make_layout(const geo_tiles* t) {
     L.status = (int*)(base + mo.status);
     L.scal = (double*)(base + mo.scal);
     L.planes = (__nv_bfloat16*)t->d_planes;
+    L.rexp = t->d_planes ? (int*)((char*)t->d_planes +
+                                  align256((size_t)4 * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots))
+                         : nullptr;
     return L;
 }
 
@@ -166,8 +169,10 @@ int geo_layout_init(int n, int nb, int band, int lp_mode, geo_layout* out) {
     const size_t tile = (size_t)nb * nb;
     g.bytes_dp = align256(sizeof(double) * tile * (size_t)ndp);
     g.bytes_sp = align256(sizeof(float) * tile * (size_t)std::max(nsp, 1LL));
+    // four BF16 slice planes of every panel tile, then one int32 row exponent per plane row
     g.bytes_planes = (lp_mode == GEO_LP_SPLIT_BF16 && nsp > 0)
-                         ? align256((size_t)3 * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots)
+                         ? align256((size_t)4 * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots) +
+                               align256(sizeof(int) * (size_t)g.pp * (size_t)g.n_slots)
                          : 0;
     g.bytes_meta = meta_offsets(p, nb).total;
     *out = g;

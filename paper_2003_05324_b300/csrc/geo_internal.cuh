@@ -4,9 +4,10 @@
 // stored contiguously: in the FP64 store when i - j < band (Algorithm 1's
 // diag_thick), otherwise in the FP32 store.  `off[i*p + j]` is its element
 // offset inside the store of its precision (-1 for the upper triangle).
-// Panel tiles (i > j) also own a slot of three BF16 planes (hi, mid, lo of
-// their FP32 value), each pp x pp row-major with the column (the contraction
-// index of the off-band update) contiguous and zero padding beyond nb.
+// Panel tiles (i > j) also own a slot of four BF16 planes (fixed-point slices
+// of their FP32 value, scaled per row), each pp x pp row-major with the column
+// (the contraction index of the off-band update) contiguous and zero padding
+// beyond nb, plus one scale exponent per row.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -26,6 +27,7 @@ struct Layout {
     const long long* off;
     const int* slot;
     __nv_bfloat16* planes;
+    int* rexp;      // per panel-tile row: scale exponent of its fixed-point slices [slot][pp]
     int* status;
     double* scal;   // scalar scratch: per-tile log-det and quad partials [2*p], results [2]
 };
@@ -35,7 +37,7 @@ __host__ __device__ inline bool is_dp(int i, int j, int band) { return (i - j) <
 __device__ __forceinline__ double* dp_tile(const Layout& L, int i, int j) { return L.dp + L.off[i * L.p + j]; }
 __device__ __forceinline__ float* sp_tile(const Layout& L, int i, int j) { return L.sp + L.off[i * L.p + j]; }
 __device__ __forceinline__ __nv_bfloat16* plane(const Layout& L, int i, int j, int s) {
-    return L.planes + ((size_t)L.slot[i * L.p + j] * 3 + s) * (size_t)L.pp * L.pp;
+    return L.planes + ((size_t)L.slot[i * L.p + j] * 4 + s) * (size_t)L.pp * L.pp;
 }
 __device__ __forceinline__ bool failed(const Layout& L) {
     return *((volatile int*)L.status + ST_CODE) != 0;

@@ -1,13 +1,13 @@
 // BF16 plane split of panel tiles and the tcgen05 off-band update (see lp_gemm.cuh).
 //
 // Off-band update kernel (one launch per outer step k, persistent, one CTA per SM):
-//   work item = (off-band target (i,j), 128-row block mb, 128-column block nc)
-//   warp 0      TMA producer: per K chunk of 64, the three planes of A(i,k) rows
-//               [mb*128, +128) and of A(j,k) rows [nc*128, +128) -> one smem stage
-//   warp 1      TMEM allocation and a single issuing thread: 6 plane pairs x 4
-//               UMMA (M=128, N=128, K=16, BF16 in, FP32 accumulate) per stage
-//   warps 2..5  epilogue: tcgen05.ld of the FP32 accumulator, C -= acc in place
-// Two smem stages (96 KB each) and two TMEM accumulators (2 x 128 columns) let the
+//   work item = (off-band target (i,j), 128-row block mb, 64-column block nc)
+//   warp 0      TMA producer: per K chunk of 64, the four slice planes of A(i,k)
+//               rows [mb*128, +128) and of A(j,k) rows [nc*64, +64) -> one stage
+//   warp 1      TMEM allocation and a single issuing thread: 10 slice pairs x 4
+//               UMMA (M=128, N=64, K=16, BF16 in, FP32 accumulate) per stage
+//   warps 2..5  epilogue: tcgen05.ld of both accumulators, C -= scaled sum in place
+// Two smem stages (96 KB each) and two sets of TMEM accumulators let the
 // epilogue of one item overlap the main loop of the next.  Every mbarrier wait is
 // bounded by a %globaltimer deadline; on expiry the CTA records GEO_ERR_TIMEOUT,
 // drains its outstanding copies and MMAs (also bounded), frees TMEM and exits.
@@ -21,63 +21,98 @@
 namespace geo {
 
 // ------------------------------------------------------------ split ---
-// 32 x 32 transpose tiles: read the column-major FP32 (or FP64 in-band) panel
-// tile coalesced down the rows, write the row-major planes coalesced along K.
+// One CTA per 32 rows of a panel tile (i,k), all columns.  Phase 1: the row
+// maxima give each row a power-of-two scale 2^E (|v| 2^-E < 1/2).  Phase 2:
+// each value m = v 2^-E is cut into four rounded 8-bit integer slices
+//   a0 = rint(2^8 m), a1 = rint(2^8 (2^8 m - a0)), a2, a3 likewise,
+// |a_s| <= 128, stored exactly in BF16 as a_s 2^-8s, so that
+// v = 2^(E-8) (P0 + P1 + P2 + P3) up to 2^(E-41).  The SP copy of an in-band (FP64)
+// panel tile is its FP32 rounding (Algorithm 1's dconv2s), sliced the same way.
+// Writes go through a 32 x 32 shared transpose so both sides coalesce.
 __global__ void __launch_bounds__(256) split_panel_kernel(Layout L, int k) {
     if (failed(L)) return;
-    const int i = k + 1 + blockIdx.z;
+    const int i = k + 1 + blockIdx.y;
     const int nb = L.nb, pp = L.pp;
-    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int r0 = blockIdx.x * 32;
     __shared__ float t[32][33];
+    __shared__ float pmax[8][32];
+    __shared__ int es[32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const bool dp = is_dp(i, k, L.band);
-    for (int q = ty; q < 32; q += 8) {
-        const int r = r0 + tx, c = c0 + q;
-        float v = 0.0f;
-        if (r < nb && c < nb)
-            v = dp ? (float)dp_tile(L, i, k)[(size_t)c * nb + r] : sp_tile(L, i, k)[(size_t)c * nb + r];
-        t[tx][q] = v;
+    const double* Ad = dp ? dp_tile(L, i, k) : nullptr;
+    const float* As = dp ? nullptr : sp_tile(L, i, k);
+    auto val = [&](int r, int c) -> float {
+        if (r >= nb || c >= nb) return 0.0f;
+        return dp ? (float)Ad[(size_t)c * nb + r] : As[(size_t)c * nb + r];
+    };
+    float mx = 0.0f;
+    for (int c = ty; c < nb; c += 8) mx = fmaxf(mx, fabsf(val(r0 + tx, c)));
+    pmax[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0) {
+        float m = pmax[0][tx];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, pmax[w][tx]);
+        int e = 0;
+        if (m > 0.0f) {
+            frexpf(m, &e);    // m < 2^e
+            e += 1;           // |v| 2^-e < 1/2
+        }
+        es[tx] = e;
+        L.rexp[(size_t)L.slot[i * L.p + k] * pp + r0 + tx] = e;
     }
     __syncthreads();
     __nv_bfloat16* P0 = plane(L, i, k, 0);
     __nv_bfloat16* P1 = plane(L, i, k, 1);
     __nv_bfloat16* P2 = plane(L, i, k, 2);
-    for (int q = ty; q < 32; q += 8) {
-        const int r = r0 + q, c = c0 + tx;
-        const float v = t[q][tx];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const float r1 = v - __bfloat162float(hi);
-        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-        const float r2 = r1 - __bfloat162float(mid);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
-        const size_t e = (size_t)r * pp + c;
-        P0[e] = hi;
-        P1[e] = mid;
-        P2[e] = lo;
+    __nv_bfloat16* P3 = plane(L, i, k, 3);
+    for (int cb = 0; cb < pp; cb += 32) {
+        for (int q = ty; q < 32; q += 8) t[tx][q] = val(r0 + tx, cb + q);
+        __syncthreads();
+        for (int q = ty; q < 32; q += 8) {
+            const int r = r0 + q, c = cb + tx;
+            const float t0 = ldexpf(t[q][tx], 8 - es[q]);
+            const float a0 = rintf(t0);
+            const float t1 = (t0 - a0) * 256.0f;
+            const float a1 = rintf(t1);
+            const float t2 = (t1 - a1) * 256.0f;
+            const float a2 = rintf(t2);
+            const float a3 = rintf((t2 - a2) * 256.0f);
+            const size_t e = (size_t)r * pp + c;
+            P0[e] = __float2bfloat16_rn(a0);
+            P1[e] = __float2bfloat16_rn(a1 * (1.0f / 256.0f));
+            P2[e] = __float2bfloat16_rn(a2 * (1.0f / 65536.0f));
+            P3[e] = __float2bfloat16_rn(a3 * (1.0f / 16777216.0f));
+        }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_split_panel(const Layout& L, int k, cudaStream_t s) {
     const int m = L.p - k - 1;
-    dim3 grid(L.pp / 32, L.pp / 32, m);
+    dim3 grid(L.pp / 32, m);
     split_panel_kernel<<<grid, 256, 0, s>>>(L, k);
     count_launch();
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------- tcgen05 GEMM ---
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
+constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 64;
+constexpr int TC_NS = 4;                             // slices per operand
+constexpr int TC_NPAIRS = 10;                        // slice pairs (a, b) with a + b <= 3
 constexpr int TC_STAGES = 2;
-constexpr int TC_PLANE_BYTES = TC_BM * TC_BK * 2;   // 16 KB, one plane chunk (A or B)
-constexpr int TC_STAGE_BYTES = 6 * TC_PLANE_BYTES;  // A hi/mid/lo, B hi/mid/lo
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;        // 16 KB, one A slice chunk
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;        // 8 KB, one B slice chunk
+constexpr int TC_STAGE_BYTES = TC_NS * (TC_A_BYTES + TC_B_BYTES);
 constexpr int TC_THREADS = 192;
-constexpr int TC_TMEM_COLS = 2 * TC_BN;
+constexpr int TC_TMEM_COLS = 4 * TC_BN;             // 2 buffers x (level-0, levels 1-3) accumulators
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr long long TC_WAIT_NS = 2000000000LL;      // 2 s per wait
 
-// pairs (a plane, b plane) whose products are kept: small terms first
-__constant__ int c_pair_a[6] = {1, 0, 2, 0, 1, 0};
-__constant__ int c_pair_b[6] = {1, 2, 0, 1, 0, 0};
+// slice pairs (a, b) kept: (0,0) -> exact level-0 accumulator; the others,
+// smallest weight first, -> the second accumulator
+__constant__ int c_pair_a[TC_NPAIRS] = {0, 0, 1, 2, 3, 0, 1, 2, 0, 1};
+__constant__ int c_pair_b[TC_NPAIRS] = {0, 3, 2, 1, 0, 2, 1, 0, 1, 0};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -154,6 +189,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
+// 2^e as a float for e >= -126 (exact), 0 below: contributions that small are
+// beneath the FP32 resolution of any covariance entry they update.
+__device__ __forceinline__ float pow2f(int e) {
+    return e < -126 ? 0.0f : __int_as_float((min(e, 127) + 127) << 23);
+}
+
 __device__ __forceinline__ void decode_lp_target(int t, int k, int p, int band, int& i, int& j) {
     const int m = p - k - 1;
     for (int d = band; d < m; ++d) {
@@ -169,7 +210,8 @@ __device__ __forceinline__ void decode_lp_target(int t, int k, int p, int band, 
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    lp_gemm_tc_kernel(Layout L, const __grid_constant__ CUtensorMap tmap, int k, int nlp) {
+    lp_gemm_tc_kernel(Layout L, const __grid_constant__ CUtensorMap tmap_a,
+                      const __grid_constant__ CUtensorMap tmap_b, int k, int nlp) {
     extern __shared__ uint8_t tc_smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);
@@ -224,7 +266,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int i, j;
                 decode_lp_target(w / per_target, k, p, L.band, i, j);
                 const int rem = w % per_target, mb = rem / nnc, nc = rem % nnc;
-                const int sa = L.slot[i * p + k] * 3, sb = L.slot[j * p + k] * 3;
+                const int sa = L.slot[i * p + k] * TC_NS, sb = L.slot[j * p + k] * TC_NS;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int st = it % TC_STAGES;
                     const uint32_t ph = (it / TC_STAGES) & 1;
@@ -235,13 +277,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mbar_expect_tx(FULL(st), TC_STAGE_BYTES);
                     uint8_t* sbase = smem + st * TC_STAGE_BYTES;
 #pragma unroll
-                    for (int s = 0; s < 3; ++s)
-                        tma_load_3d(smem_u32(sbase + s * TC_PLANE_BYTES), &tmap, kc * TC_BK, mb * TC_BM, sa + s,
+                    for (int s = 0; s < TC_NS; ++s)
+                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), &tmap_a, kc * TC_BK, mb * TC_BM, sa + s,
                                     FULL(st));
 #pragma unroll
-                    for (int s = 0; s < 3; ++s)
-                        tma_load_3d(smem_u32(sbase + (3 + s) * TC_PLANE_BYTES), &tmap, kc * TC_BK, nc * TC_BN,
-                                    sb + s, FULL(st));
+                    for (int s = 0; s < TC_NS; ++s)
+                        tma_load_3d(smem_u32(sbase + TC_NS * TC_A_BYTES + s * TC_B_BYTES), &tmap_b, kc * TC_BK,
+                                    nc * TC_BN, sb + s, FULL(st));
                 }
             }
             if (!ok) {
@@ -264,7 +306,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dst = tmem_base + acc * TC_BN;
+                const uint32_t dst0 = tmem_base + acc * (2 * TC_BN), dst1 = dst0 + TC_BN;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int st = it % TC_STAGES;
                     const uint32_t ph = (it / TC_STAGES) & 1;
@@ -275,13 +317,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t sbase = smem_u32(smem + st * TC_STAGE_BYTES);
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const uint32_t a_addr = sbase + c_pair_a[q] * TC_PLANE_BYTES;
-                        const uint32_t b_addr = sbase + (3 + c_pair_b[q]) * TC_PLANE_BYTES;
+                    for (int q = 0; q < TC_NPAIRS; ++q) {
+                        const uint32_t a_addr = sbase + c_pair_a[q] * TC_A_BYTES;
+                        const uint32_t b_addr = sbase + TC_NS * TC_A_BYTES + c_pair_b[q] * TC_B_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < TC_BK / 16; ++kk)
-                            umma_bf16(dst, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32),
-                                      (kc | q | kk) != 0);
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            if (q == 0)
+                                umma_bf16(dst0, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32),
+                                          (kc | kk) != 0);
+                            else
+                                umma_bf16(dst1, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32),
+                                          (kc | (q - 1) | kk) != 0);
+                        }
                     }
                     umma_commit(EMPTY(st));   // stage reusable once these MMAs complete
                 }
@@ -318,10 +365,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int c_begin = nc * TC_BN;
             const int ncol = rv ? max(0, min(TC_BN, nb - c_begin)) : 0;
             float* Crow = C + (size_t)c_begin * nb + (rv ? r : 0);
-            constexpr int HALF = TC_BN / 2;
-            float cpre[HALF];
+            constexpr int BATCH = 32;   // columns per register batch
+            float cpre[BATCH];
 #pragma unroll
-            for (int e = 0; e < HALF; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0f;
+            for (int e = 0; e < BATCH; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0f;
             if (*abort_flag || !mbar_wait(TFULL(acc), aph, gtimer() + TC_WAIT_NS)) {
                 if (!*abort_flag) {
                     *abort_flag = 1;
@@ -330,24 +377,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * TC_BN;
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (2 * TC_BN);
+            // C -= 2^(E_r + E_c - 16) (acc0 + acc12): one FP32 rounding of the sum, an
+            // exact power-of-two scaling, one rounding of the update
+            const int* eb = L.rexp + (size_t)L.slot[j * p + k] * pp;
+            const int er = (r < pp) ? L.rexp[(size_t)L.slot[i * p + k] * pp + r] : 0;
+#pragma unroll 1
+            for (int h = 0; h < TC_BN / BATCH; ++h) {
+                if (h > 0) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (h == 1) {
-#pragma unroll
-                    for (int e = 0; e < HALF; ++e)
-                        cpre[e] = (HALF + e < ncol) ? Crow[(size_t)(HALF + e) * nb] : 0.0f;
+                    for (int e = 0; e < BATCH; ++e)
+                        cpre[e] = (h * BATCH + e < ncol) ? Crow[(size_t)(h * BATCH + e) * nb] : 0.0f;
                 }
 #pragma unroll
-                for (int cc = 0; cc < HALF; cc += 16) {
-                    float v[16];
-                    tmem_ld16(taddr + h * HALF + cc, v);
+                for (int cc = 0; cc < BATCH; cc += 16) {
+                    float v0[16], v1[16];
+                    tmem_ld16(taddr + h * BATCH + cc, v0);
+                    tmem_ld16(taddr + TC_BN + h * BATCH + cc, v1);
+                    // the 16 column exponents: uniform across the warp (broadcast loads);
+                    // rows >= pp of the B tile do not exist, their exponent reads as 0
+                    int ec[16];
+                    const int cl0 = c_begin + h * BATCH + cc;
+                    if (cl0 + 16 <= pp) {
+                        const int4* e4 = reinterpret_cast<const int4*>(eb + cl0);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) cpre[cc + e] -= v[e];
+                        for (int q = 0; q < 4; ++q) {
+                            const int4 w4 = __ldg(e4 + q);
+                            ec[4 * q] = w4.x;
+                            ec[4 * q + 1] = w4.y;
+                            ec[4 * q + 2] = w4.z;
+                            ec[4 * q + 3] = w4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) ec[e] = 0;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) cpre[cc + e] -= (v0[e] + v1[e]) * pow2f(er + ec[e] - 16);
                 }
 #pragma unroll
-                for (int e = 0; e < HALF; ++e)
-                    if (h * HALF + e < ncol) Crow[(size_t)(h * HALF + e) * nb] = cpre[e];
+                for (int e = 0; e < BATCH; ++e)
+                    if (h * BATCH + e < ncol) Crow[(size_t)(h * BATCH + e) * nb] = cpre[e];
             }
             tc_fence_before();
             mbar_arrive(TEMPTY(acc));
@@ -380,13 +450,14 @@ static PFN_encodeTiled get_encode() {
     return fn;
 }
 
-// 3D map over all planes: (K = pp, rows = pp, plane index = 3 * n_slots).
-static int make_plane_map(const Layout& L, long long nslots, CUtensorMap* map) {
+// 3D map over all planes: (K = pp, rows = pp, plane index = 4 * n_slots); the
+// box is 64 columns (128 bytes, the swizzle width) by `rows` rows.
+static int make_plane_map(const Layout& L, long long nslots, int rows, CUtensorMap* map) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return 1;
-    cuuint64_t dims[3] = {(cuuint64_t)L.pp, (cuuint64_t)L.pp, (cuuint64_t)(3 * nslots)};
+    cuuint64_t dims[3] = {(cuuint64_t)L.pp, (cuuint64_t)L.pp, (cuuint64_t)(TC_NS * nslots)};
     cuuint64_t strides[2] = {(cuuint64_t)L.pp * 2, (cuuint64_t)L.pp * L.pp * 2};
-    cuuint32_t box[3] = {TC_BK, TC_BM, 1};
+    cuuint32_t box[3] = {TC_BK, (cuuint32_t)rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)L.planes, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -395,12 +466,13 @@ static int make_plane_map(const Layout& L, long long nslots, CUtensorMap* map) {
 }
 
 int prepare_lp_gemm(geo_tiles* t, const Layout& L) {
-    static_assert(sizeof(CUtensorMap) <= sizeof(((geo_tiles*)0)->tmap), "tensor map storage");
+    static_assert(2 * sizeof(CUtensorMap) <= sizeof(((geo_tiles*)0)->tmap), "tensor map storage");
     if (!L.planes || t->lay.n_slots == 0) return 0;
-    CUtensorMap map;
-    int rc = make_plane_map(L, t->lay.n_slots, &map);
+    CUtensorMap maps[2];
+    int rc = make_plane_map(L, t->lay.n_slots, TC_BM, &maps[0]);
+    if (!rc) rc = make_plane_map(L, t->lay.n_slots, TC_BN, &maps[1]);
     if (rc) return rc;
-    memcpy(t->tmap, &map, sizeof(map));
+    memcpy(t->tmap, maps, sizeof(maps));
     return 0;
 }
 
@@ -421,9 +493,9 @@ cudaError_t launch_lp_gemm_tc(const geo_tiles* t, const Layout& L, int k, int nl
     const int per_target = ((L.pp + TC_BM - 1) / TC_BM) * ((L.pp + TC_BN - 1) / TC_BN);
     const long long total = (long long)nlp * per_target;
     const int grid = (int)std::min<long long>(total, g_num_sms > 0 ? g_num_sms : 148);
-    CUtensorMap map;
-    memcpy(&map, t->tmap, sizeof(map));
-    lp_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(L, map, k, nlp);
+    CUtensorMap maps[2];
+    memcpy(maps, t->tmap, sizeof(maps));
+    lp_gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(L, maps[0], maps[1], k, nlp);
     count_launch();
     return cudaGetLastError();
 }

@@ -1,9 +1,14 @@
 // Off-band (FP32-accurate) update of Algorithm 1 (sgemm) on the tcgen05 tensor
-// cores: the FP32 panel tiles are split into three BF16 planes
-// (hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid)) and
-// C <- C - sum over the six pairs (hi,hi) (hi,mid) (mid,hi) (hi,lo) (lo,hi) (mid,mid)
-// of A_s B_t', accumulated in FP32 in tensor memory.  The dropped pairs are of
-// relative size 2^-24 and below, i.e. the result is FP32-accurate.
+// cores.  Each FP32 panel row is scaled by a power of two 2^E (|v| 2^-E < 1/2)
+// and cut into three rounded 8-bit integer slices a0, a1, a2 (|a_s| <= 128),
+// stored exactly in BF16 as P0 = a0, P1 = a1 2^-8, P2 = a2 2^-16, so that
+// v = 2^(E-8) (P0 + P1 + P2) to 2^-25 of the row's scale.  Then
+//   C <- C - 2^(E_r+E_c-16) [ sum P0 P0'  +  sum (P1P1' + P0P2' + P2P0' + P0P1' + P1P0') ].
+// The first sum is of integers below 2^23 for K <= 1024, so the tensor cores
+// accumulate it exactly (their FP32 accumulation truncates; exact sums make that
+// moot); the second, 2^-8 smaller, goes to its own accumulator.  The dropped
+// pairs weigh 2^-24 of the leading one: the update is FP32-accurate and free of
+// the accumulation bias a single truncating accumulator would add.
 #pragma once
 #include "geo_internal.cuh"
 

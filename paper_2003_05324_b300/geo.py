@@ -58,7 +58,7 @@ class geo_tiles(ctypes.Structure):
     _fields_ = [("lay", geo_layout), ("d_dp", ctypes.c_void_p), ("d_sp", ctypes.c_void_p),
                 ("d_planes", ctypes.c_void_p), ("d_meta", ctypes.c_void_p),
                 ("aux_stream", ctypes.c_void_p), ("ev_fork", ctypes.c_void_p), ("ev_join", ctypes.c_void_p),
-                ("tmap", ctypes.c_uint64 * 16), ("flags", ctypes.c_int)]
+                ("tmap", ctypes.c_uint64 * 32), ("flags", ctypes.c_int)]
 
 
 def _load():

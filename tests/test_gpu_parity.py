@@ -183,22 +183,52 @@ def oracle_mp_from_matrix(S, z, nb, band):
 @pytest.mark.parametrize("band", [1, 2, 4])
 @pytest.mark.parametrize("lp", ["fp32", "bf16"])
 def test_factor_solve_matches_algorithm1(G, band, lp):
-    # same rounded covariance on both sides: potrf + log-det + solve of the GPU
-    # against the oracle's Algorithm 1 (error vs FP64 within 4x the oracle's)
+    # Same rounded covariance on both sides: GPU potrf + log-det + solve against
+    # the oracle's Algorithm 1.  A single instance's signed error is a sum of
+    # many roundings of either sign (it varies ~10x between seeds for either
+    # implementation), so the accuracy class is compared over four datasets:
+    # the GPU's mean |dl| must stay within twice the oracle's.
     th = O.Theta(1.0, 0.1, 0.5)
-    x, y, z = problem(40, 0, G.Theta(1.0, 0.1, 0.5))
+    mode = G.GEO_LP_FP32 if lp == "fp32" else G.GEO_LP_SPLIT_BF16
+    eg, eo = [], []
+    for seed in range(4):
+        x, y, z = problem(40, seed, G.Theta(1.0, 0.1, 0.5))
+        S = O.covariance(x, y, theta=th)
+        Ld, _ = O.dense_factor(S)
+        ld, q = O.factor_logdet_quad(Ld, z)
+        want = -0.5 * 1600 * math.log(2 * math.pi) - 0.5 * ld - 0.5 * q
+        mp = oracle_mp_from_matrix(S, z, 200, band)
+        ts = G.TileStore(1600, 200, band, mode)
+        ts.load_dense(dev(S.T))
+        ts.potrf()
+        gld, gq, _ = ts.logdet_trsv(dev(z))
+        got = -0.5 * 1600 * math.log(2 * math.pi) - 0.5 * float(gld) - 0.5 * float(gq)
+        eg.append(abs(got - want))
+        eo.append(abs(mp - want))
+    assert np.mean(eg) <= 2.0 * np.mean(eo) + 1e-12 * 1600, (eg, eo)
+
+
+@pytest.mark.parametrize("lp", ["fp32", "bf16"])
+def test_offband_updates_are_unbiased(G, lp):
+    # Round-to-nearest FP32 arithmetic leaves errors of either sign; a truncating
+    # accumulation would bias every tile it updates.  Per off-band tile the mean
+    # signed error over the mean absolute error (vs the FP64 factor) must stay
+    # at the level of the oracle's Algorithm 1 (whose values here are <= 0.05).
+    th = O.Theta(1.0, 0.1, 0.5)
+    x, y, z = problem(40, 1, G.Theta(1.0, 0.1, 0.5))
     S = O.covariance(x, y, theta=th)
     Ld, _ = O.dense_factor(S)
-    ld, q = O.factor_logdet_quad(Ld, z)
-    want = -0.5 * 1600 * math.log(2 * math.pi) - 0.5 * ld - 0.5 * q
-    mp = oracle_mp_from_matrix(S, z, 200, band)
     mode = G.GEO_LP_FP32 if lp == "fp32" else G.GEO_LP_SPLIT_BF16
-    ts = G.TileStore(1600, 200, band, mode)
+    ts = G.TileStore(1600, 200, 1, mode)
     ts.load_dense(dev(S.T))
     ts.potrf()
-    gld, gq, _ = ts.logdet_trsv(dev(z))
-    got = -0.5 * 1600 * math.log(2 * math.pi) - 0.5 * float(gld) - 0.5 * float(gq)
-    assert abs(got - want) <= 4 * abs(mp - want) + 1e-12 * abs(want)
+    L = ts.to_dense().cpu().numpy()
+    bias = []
+    for i in range(2, 8):
+        for j in range(1, i):
+            e = L[i * 200:(i + 1) * 200, j * 200:(j + 1) * 200] - Ld[i * 200:(i + 1) * 200, j * 200:(j + 1) * 200]
+            bias.append(e.mean() / np.abs(e).mean())
+    assert abs(np.mean(bias)) <= 0.05, bias
 
 
 @pytest.mark.parametrize("n,nb,band", [(1000, 96, 2), (50, 64, 1), (1, 16, 1), (333, 32, 3)])
