@@ -16,7 +16,7 @@ namespace geo {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// meta buffer: off[p*p] int64 | slot[p*p] int32 | status[16] int32 | scal doubles
+// meta buffer: off[p*p] int64 | slot[p*p] int32 | status[16] + tickets[2p] int32 | scal doubles
 struct MetaOffsets {
     size_t off, slot, status, scal, total;
 };
@@ -29,7 +29,7 @@ static MetaOffsets meta_offsets(int p, int nb) {
     m.slot = b;
     b = align256(b + sizeof(int) * (size_t)p * p);
     m.status = b;
-    b = align256(b + sizeof(int) * ST_WORDS);
+    b = align256(b + sizeof(int) * ((size_t)ST_WORDS + 2 * (size_t)p));
     m.scal = b;
     b = align256(b + sizeof(double) * ((size_t)2 * p + 8 + (size_t)p * nb));
     m.total = b;
@@ -108,6 +108,7 @@ Layout make_layout(const geo_tiles* t) {
     L.off = (const long long*)(base + mo.off);
     L.slot = (const int*)(base + mo.slot);
     L.status = (int*)(base + mo.status);
+    L.tickets = L.status + ST_WORDS;
     L.scal = (double*)(base + mo.scal);
     L.planes = (__nv_bfloat16*)t->d_planes;
     L.rexp = t->d_planes ? (int*)((char*)t->d_planes +
@@ -273,8 +274,10 @@ int geo_tiles_to_dense(const geo_tiles* t, double* d_out, void* stream) {
     return launch_to_dense(make_layout(t), d_out, (cudaStream_t)stream) ? GEO_ERR_CUDA : GEO_OK;
 }
 
+// status words and the per-step work tickets of the persistent update kernels
 static int reset_status(const Layout& L, cudaStream_t s) {
-    return cudaMemsetAsync(L.status, 0, sizeof(int) * ST_WORDS, s) ? GEO_ERR_CUDA : GEO_OK;
+    return cudaMemsetAsync(L.status, 0, sizeof(int) * ((size_t)ST_WORDS + 2 * (size_t)L.p), s) ? GEO_ERR_CUDA
+                                                                                                 : GEO_OK;
 }
 
 int geo_potrf_mp(geo_tiles* t, void* stream) {

@@ -257,8 +257,9 @@ __global__ void __launch_bounds__(TR_THREADS) trsm_panel_sp_kernel(Layout L, int
 // grid of m8n8k4 FP64 MMAs.  Sources in FP32 storage are promoted exactly.
 constexpr int U64_THREADS = 128;
 constexpr int U64_BM = 64;
-constexpr int U64_BK = 16;
+constexpr int U64_BK = 8;                 // K chunk per smem buffer (two buffers)
 constexpr int U64_LD = U64_BK + 4;
+constexpr int U64_PER_T = U64_BM * U64_BK / U64_THREADS;   // staged values per thread and operand
 
 __device__ __forceinline__ void dmma_884(double& c0, double& c1, double a, double b) {
     asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
@@ -281,64 +282,103 @@ __device__ __forceinline__ bool decode_target(int t, int k, int p, int d_lo, int
     return false;
 }
 
+// Register-staged loads of one K chunk (rows row0..row0+63, columns kc..kc+BK-1)
+// of a column-major tile, promoted to FP64; then stored to shared memory.
 template <typename T>
-__device__ __forceinline__ void stage_rows64(double* S, const T* __restrict__ src, int nb, int row0, int kc) {
-    for (int idx = threadIdx.x; idx < U64_BM * U64_BK; idx += U64_THREADS) {
+__device__ __forceinline__ void load_chunk(double (&v)[U64_PER_T], const T* __restrict__ src, int nb, int row0,
+                                           int kc) {
+#pragma unroll
+    for (int q = 0; q < U64_PER_T; ++q) {
+        const int idx = threadIdx.x + q * U64_THREADS;
         const int rr = idx % U64_BM, tt = idx / U64_BM;
         const int r = row0 + rr, t = kc + tt;
-        S[rr * U64_LD + tt] = (r < nb && t < nb) ? (double)src[(size_t)t * nb + r] : 0.0;
+        v[q] = (r < nb && t < nb) ? (double)src[(size_t)t * nb + r] : 0.0;
+    }
+}
+__device__ __forceinline__ void store_chunk(double* S, const double (&v)[U64_PER_T]) {
+#pragma unroll
+    for (int q = 0; q < U64_PER_T; ++q) {
+        const int idx = threadIdx.x + q * U64_THREADS;
+        S[(idx % U64_BM) * U64_LD + idx / U64_BM] = v[q];
     }
 }
 
-__global__ void __launch_bounds__(U64_THREADS) update_fp64_kernel(Layout L, int k) {
-    if (failed(L)) return;
-    int i, j;
-    if (!decode_target(blockIdx.y, k, L.p, 0, L.band, i, j)) return;
+// Persistent: CTAs take (target, sub-block) items from a per-step ticket counter,
+// so late-starting CTAs (sharing SMs with the tensor-core update) just take fewer.
+__global__ void __launch_bounds__(U64_THREADS) update_fp64_kernel(Layout L, int k, int n_items) {
     const int nb = L.nb, nsb = (nb + U64_BM - 1) / U64_BM;
-    const int sbr = blockIdx.x / nsb, sbc = blockIdx.x % nsb;
-    const bool syrk = (i == j);
-    if (syrk && sbr < sbc) return;
-    const int R0 = sbr * U64_BM, C0 = sbc * U64_BM;
-    __shared__ double As[U64_BM * U64_LD], Bs[U64_BM * U64_LD];
+    __shared__ double As[2][U64_BM * U64_LD], Bs[2][U64_BM * U64_LD];
+    __shared__ int item_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, tq = lane & 3;
     const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;
-    double acc[4][4][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
-    const bool a_dp = is_dp(i, k, L.band), b_dp = is_dp(j, k, L.band);
-    for (int kc = 0; kc < nb; kc += U64_BK) {
-        if (a_dp) stage_rows64(As, dp_tile(L, i, k), nb, R0, kc);
-        else stage_rows64(As, sp_tile(L, i, k), nb, R0, kc);
-        if (b_dp) stage_rows64(Bs, dp_tile(L, j, k), nb, C0, kc);
-        else stage_rows64(Bs, sp_tile(L, j, k), nb, C0, kc);
+    for (;;) {
+        if (threadIdx.x == 0) item_s = failed(L) ? n_items : atomicAdd(L.tickets + k, 1);
         __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < U64_BK; kk += 4) {
-            double af[4], bf[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) af[a] = As[(wr + a * 8 + g) * U64_LD + kk + tq];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) bf[b] = Bs[(wc + b * 8 + g) * U64_LD + kk + tq];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) dmma_884(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
-        }
+        const int item = item_s;
         __syncthreads();
-    }
-    double* C = dp_tile(L, i, j);
+        if (item >= n_items) return;
+        int i, j;
+        decode_target(item / (nsb * nsb), k, L.p, 0, L.band, i, j);
+        const int sb = item % (nsb * nsb);
+        const int sbr = sb / nsb, sbc = sb % nsb;
+        const bool syrk = (i == j);
+        if (syrk && sbr < sbc) continue;
+        const int R0 = sbr * U64_BM, C0 = sbc * U64_BM;
+        double acc[4][4][2];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
+            for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+        const bool a_dp = is_dp(i, k, L.band), b_dp = is_dp(j, k, L.band);
+        const double* Ad = a_dp ? dp_tile(L, i, k) : nullptr;
+        const float* As32 = a_dp ? nullptr : sp_tile(L, i, k);
+        const double* Bd = b_dp ? dp_tile(L, j, k) : nullptr;
+        const float* Bs32 = b_dp ? nullptr : sp_tile(L, j, k);
+        double va[U64_PER_T], vb[U64_PER_T];
+        auto fetch = [&](int kc) {
+            if (a_dp) load_chunk(va, Ad, nb, R0, kc);
+            else load_chunk(va, As32, nb, R0, kc);
+            if (b_dp) load_chunk(vb, Bd, nb, C0, kc);
+            else load_chunk(vb, Bs32, nb, C0, kc);
+        };
+        fetch(0);
+        store_chunk(As[0], va);
+        store_chunk(Bs[0], vb);
+        __syncthreads();
+        int buf = 0;
+        for (int kc = 0; kc < nb; kc += U64_BK, buf ^= 1) {
+            const bool more = kc + U64_BK < nb;
+            if (more) fetch(kc + U64_BK);   // global loads in flight during the MMAs below
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int r = R0 + wr + a * 8 + g, c = C0 + wc + b * 8 + 2 * tq + e;
-                if (r < nb && c < nb && (!syrk || r >= c)) C[(size_t)c * nb + r] -= acc[a][b][e];
+            for (int kk = 0; kk < U64_BK; kk += 4) {
+                double af[4], bf[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) af[a] = As[buf][(wr + a * 8 + g) * U64_LD + kk + tq];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) bf[b] = Bs[buf][(wc + b * 8 + g) * U64_LD + kk + tq];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) dmma_884(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
             }
+            if (more) {
+                store_chunk(As[buf ^ 1], va);
+                store_chunk(Bs[buf ^ 1], vb);
+            }
+            __syncthreads();
+        }
+        double* C = dp_tile(L, i, j);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int r = R0 + wr + a * 8 + g, c = C0 + wc + b * 8 + 2 * tq + e;
+                    if (r < nb && c < nb && (!syrk || r >= c)) C[(size_t)c * nb + r] -= acc[a][b][e];
+                }
+    }
 }
 
 // ------------------------------------------- off-band update, FP32 SIMT ---
@@ -477,7 +517,10 @@ cudaError_t run_potrf_mp(const geo_tiles* t, const Layout& L, cudaStream_t s) {
         }
         if (n64 > 0) {
             prof_begin(0, s);
-            update_fp64_kernel<<<dim3(nsb64 * nsb64, n64), U64_THREADS, 0, s>>>(L, k);
+            const int items = nsb64 * nsb64 * n64;
+            // one CTA per SM while the tensor-core update shares the SMs (both fit on
+            // every SM side by side), two when the FP64 update runs alone
+            update_fp64_kernel<<<std::min(items, (nlp > 0 ? 1 : 2) * nsm), U64_THREADS, 0, s>>>(L, k, items);
             prof_end(0, s);
             count_launch();
         }

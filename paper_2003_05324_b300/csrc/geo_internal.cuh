@@ -29,6 +29,7 @@ struct Layout {
     __nv_bfloat16* planes;
     int* rexp;      // per panel-tile row: scale exponent of its fixed-point slices [slot][pp]
     int* status;
+    int* tickets;   // [2p] work counters of the persistent update kernels (FP64: k, off-band: p + k)
     double* scal;   // scalar scratch: per-tile log-det and quad partials [2*p], results [2]
 };
 

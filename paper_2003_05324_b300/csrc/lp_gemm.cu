@@ -1,14 +1,15 @@
 // BF16 plane split of panel tiles and the tcgen05 off-band update (see lp_gemm.cuh).
 //
 // Off-band update kernel (one launch per outer step k, persistent, one CTA per SM):
-//   work item = (off-band target (i,j), 128-row block mb, 64-column block nc)
-//   warp 0      TMA producer: per K chunk of 64, the four slice planes of A(i,k)
-//               rows [mb*128, +128) and of A(j,k) rows [nc*64, +64) -> one stage
-//   warp 1      TMEM allocation and a single issuing thread: 10 slice pairs x 4
-//               UMMA (M=128, N=64, K=16, BF16 in, FP32 accumulate) per stage
+//   work item = (off-band target (i,j), 128-row block mb, 128-column block nc)
+//   warp 0      TMA producer: per K chunk of 32, the four slice planes of A(i,k)
+//               rows [mb*128, +128) and of A(j,k) rows [nc*128, +128) -> one stage
+//   warp 1      TMEM allocation and a single issuing thread: 10 slice pairs x 2
+//               UMMA (M=128, N=128, K=16, BF16 in, FP32 accumulate) per stage
 //   warps 2..5  epilogue: tcgen05.ld of both accumulators, C -= scaled sum in place
-// Two smem stages (96 KB each) and two sets of TMEM accumulators let the
-// epilogue of one item overlap the main loop of the next.  Every mbarrier wait is
+// Three smem stages (64 KB each, two loads in flight while one computes) and two
+// sets of TMEM accumulators (all 512 columns) let the epilogue of one item
+// overlap the main loop of the next.  Every mbarrier wait is
 // bounded by a %globaltimer deadline; on expiry the CTA records GEO_ERR_TIMEOUT,
 // drains its outstanding copies and MMAs (also bounded), frees TMEM and exits.
 #include <cuda.h>
@@ -97,11 +98,11 @@ cudaError_t launch_split_panel(const Layout& L, int k, cudaStream_t s) {
 }
 
 // ------------------------------------------------------- tcgen05 GEMM ---
-constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 64;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;  // K chunk of 32 BF16 = one 64-byte swizzle row
 constexpr int TC_NS = 4;                             // slices per operand
 constexpr int TC_NPAIRS = 10;                        // slice pairs (a, b) with a + b <= 3
-constexpr int TC_STAGES = 2;
-constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;        // 16 KB, one A slice chunk
+constexpr int TC_STAGES = 3;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;        // 8 KB, one A slice chunk
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;        // 8 KB, one B slice chunk
 constexpr int TC_STAGE_BYTES = TC_NS * (TC_A_BYTES + TC_B_BYTES);
 constexpr int TC_THREADS = 192;
@@ -150,11 +151,12 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
 }
-// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// UMMA shared-memory descriptor: K-major operand, 64-byte swizzle (rows of 64
+// bytes as written by TMA with SWIZZLE_64B), 8-row groups 512 bytes apart (SBO),
+// descriptor version 1.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N, M
 constexpr uint32_t TC_IDESC =
@@ -215,15 +217,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ uint8_t tc_smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);
-    // bars: full[2], empty[2], tfull[2], tempty[2]; then tmem base + flags
-    volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 8);
-    volatile int* abort_flag = (volatile int*)(bars + 9);
+    // bars: full[S], empty[S], tfull[2], tempty[2]; then tmem base + flags
+    volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * TC_STAGES + 4);
+    volatile int* abort_flag = (volatile int*)(bars + 2 * TC_STAGES + 5);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = smem_u32(bars);
     auto FULL = [&](int s) { return bar0 + 8u * s; };
-    auto EMPTY = [&](int s) { return bar0 + 8u * (2 + s); };
-    auto TFULL = [&](int a) { return bar0 + 8u * (4 + a); };
-    auto TEMPTY = [&](int a) { return bar0 + 8u * (6 + a); };
+    auto EMPTY = [&](int s) { return bar0 + 8u * (TC_STAGES + s); };
+    auto TFULL = [&](int a) { return bar0 + 8u * (2 * TC_STAGES + a); };
+    auto TEMPTY = [&](int a) { return bar0 + 8u * (2 * TC_STAGES + 2 + a); };
 
     if (threadIdx.x == 0) {
         *abort_flag = failed(L) ? 1 : 0;
@@ -323,10 +325,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; ++kk) {
                             if (q == 0)
-                                umma_bf16(dst0, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32),
+                                umma_bf16(dst0, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
                                           (kc | kk) != 0);
                             else
-                                umma_bf16(dst1, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32),
+                                umma_bf16(dst1, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
                                           (kc | (q - 1) | kk) != 0);
                         }
                     }
@@ -451,7 +453,7 @@ static PFN_encodeTiled get_encode() {
 }
 
 // 3D map over all planes: (K = pp, rows = pp, plane index = 4 * n_slots); the
-// box is 64 columns (128 bytes, the swizzle width) by `rows` rows.
+// box is 32 columns (64 bytes, the swizzle width) by `rows` rows.
 static int make_plane_map(const Layout& L, long long nslots, int rows, CUtensorMap* map) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return 1;
@@ -460,7 +462,7 @@ static int make_plane_map(const Layout& L, long long nslots, int rows, CUtensorM
     cuuint32_t box[3] = {TC_BK, (cuuint32_t)rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)L.planes, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : 2;
 }
