@@ -45,6 +45,7 @@ extern "C" {
 #define GEO_ERR_TIMEOUT 2      /* a device-side wait exceeded its bound; work was abandoned */
 #define GEO_ERR_CUDA 3         /* a CUDA runtime call failed */
 #define GEO_ERR_UNSUPPORTED 4  /* a valid but unimplemented configuration */
+#define GEO_ERR_TOO_LARGE 5    /* the problem exceeds a fixed-size internal buffer */
 
 /* LP (off-band) arithmetic.  GEO_LP_SPLIT_BF16 runs the off-band updates on
  * the tcgen05 tensor cores: each FP32 panel row is scaled by a power of two and
@@ -143,6 +144,26 @@ int geo_potrf_mp(geo_tiles* t, void* stream);
  * FP64 accumulation.  Asynchronous. */
 int geo_logdet_trsv(const geo_tiles* t, const double* d_z, double* d_logdet, double* d_quad,
                     double* d_y, void* stream);
+
+/* Allocation-free variant of geo_logdet_trsv (the paper has no counterpart:
+ * this is an interface for callers that cannot allocate device memory).
+ * Callers that cannot call cudaMalloc -- code running while a CUDA graph is
+ * being captured, or inside a framework whose memory pool owns the device and
+ * forbids side allocations -- would otherwise have to size and pass the
+ * solve's scratch themselves.  Here the scratch (the forward-solve vector and
+ * the per-tile partial sums) lives in a fixed array in the library's device
+ * memory: at most GEO_NOALLOC_MAX_N padded locations (p * nb) and
+ * GEO_NOALLOC_MAX_P tiles per side; larger problems return GEO_ERR_TOO_LARGE
+ * without launching anything.  The caller still passes the factored store, Z
+ * and the two output scalars (device FP64), exactly as for geo_logdet_trsv.
+ * The array is shared by every call in the process: calls whose work overlaps
+ * on the GPU (different streams, no ordering between them) race on it.  The
+ * first call on each device looks up the array's device address (no
+ * allocation); make that first call before any stream capture.  Asynchronous. */
+#define GEO_NOALLOC_MAX_N 262144
+#define GEO_NOALLOC_MAX_P 4096
+int geo_logdet_trsv_noalloc(const geo_tiles* t, const double* d_z, double* d_logdet, double* d_quad,
+                            void* stream);
 
 /* Copy the status words to the host (blocking on `stream`): *h_code = GEO_OK or
  * a GEO_ERR_* code, *h_info = 1-based failing row for GEO_ERR_NOT_SPD. */

@@ -299,6 +299,18 @@ int geo_logdet_trsv(const geo_tiles* t, const double* d_z, double* d_logdet, dou
                                                                                              : GEO_OK;
 }
 
+int geo_logdet_trsv_noalloc(const geo_tiles* t, const double* d_z, double* d_logdet, double* d_quad,
+                            void* stream) {
+    if (check_bound(t)) return -1;
+    if (!d_z) return -2;
+    if (!d_logdet) return -3;
+    if (!d_quad) return -4;
+    const long long np = (long long)t->lay.p * t->lay.nb;
+    if (np > GEO_NOALLOC_MAX_N || t->lay.p > GEO_NOALLOC_MAX_P) return GEO_ERR_TOO_LARGE;
+    return run_logdet_trsv_noalloc(make_layout(t), d_z, d_logdet, d_quad, (cudaStream_t)stream) ? GEO_ERR_CUDA
+                                                                                                : GEO_OK;
+}
+
 int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream) {
     if (check_bound(t)) return -1;
     if (!h_code) return -2;

@@ -82,6 +82,8 @@ cudaError_t launch_to_dense(const Layout& L, double* out, cudaStream_t s);
 cudaError_t run_potrf_mp(const geo_tiles* t, const Layout& L, cudaStream_t s);
 cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, double* quad, double* y,
                             cudaStream_t s);
+cudaError_t run_logdet_trsv_noalloc(const Layout& L, const double* z, double* logdet, double* quad,
+                                    cudaStream_t s);
 cudaError_t run_krige(const Layout& L, const double* x, const double* y, const double* z, const MaternP& mp,
                       const double* xn, const double* yn, int m, double* zhat, double* work, cudaStream_t s);
 

@@ -8,6 +8,8 @@
 // so the result is bitwise reproducible.
 #include <math.h>
 
+#include <mutex>
+
 #include "geo_internal.cuh"
 #include "matern_dev.cuh"
 
@@ -143,6 +145,52 @@ cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, do
     trsv_load_kernel<<<(np + 255) / 256, 256, 0, s>>>(L, z, yv);
     count_launch();
     cudaError_t e = forward_solve(L, yv, part, s);
+    if (e) return e;
+    trsv_finish_kernel<<<1, 32, 0, s>>>(L, part, logdet, quad);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------ allocation-free forward solve ---
+// Scratch of geo_logdet_trsv_noalloc: y (padded length) followed by the per-tile
+// partial sums.  Every entry the solve reads is written first in the same call
+// (the load kernel fills all of y, each tile writes its own partials), so
+// nothing needs clearing between calls.  The array is process-wide and shared
+// by all calls: calls that overlap on the GPU race on it.
+static __device__ __align__(256) double g_noalloc_scratch[GEO_NOALLOC_MAX_N + 2 * GEO_NOALLOC_MAX_P];
+
+// Device address of the array, looked up once per device (with that device
+// current); the host-side symbol is only a stand-in and never a device address.
+static double* noalloc_scratch_ptr(cudaError_t* err) {
+    static double* ptrs[64] = {nullptr};
+    static std::mutex mu;
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess || dev < 0 || dev >= 64) {
+        if (*err == cudaSuccess) *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        ptrs[dev] = (double*)p;
+    }
+    return ptrs[dev];
+}
+
+cudaError_t run_logdet_trsv_noalloc(const Layout& L, const double* z, double* logdet, double* quad,
+                                    cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    double* base = noalloc_scratch_ptr(&e);
+    if (!base) return e;
+    double* yv = base;
+    double* part = base + GEO_NOALLOC_MAX_N;
+    const int np = L.p * L.nb;
+    trsv_load_kernel<<<(np + 255) / 256, 256, 0, s>>>(L, z, yv);
+    count_launch();
+    e = forward_solve(L, yv, part, s);
     if (e) return e;
     trsv_finish_kernel<<<1, 32, 0, s>>>(L, part, logdet, quad);
     count_launch();

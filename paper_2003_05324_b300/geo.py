@@ -24,6 +24,9 @@ GEO_ERR_NOT_SPD = 1
 GEO_ERR_TIMEOUT = 2
 GEO_ERR_CUDA = 3
 GEO_ERR_UNSUPPORTED = 4
+GEO_ERR_TOO_LARGE = 5
+GEO_NOALLOC_MAX_N = 262144
+GEO_NOALLOC_MAX_P = 4096
 GEO_LP_SPLIT_BF16 = 0
 GEO_LP_FP32 = 1
 GEO_FLAG_FP64_OFFBAND_GEN = 1
@@ -77,6 +80,7 @@ def _load():
         "geo_tiles_to_dense": [ctypes.POINTER(geo_tiles), P, P],
         "geo_potrf_mp": [ctypes.POINTER(geo_tiles), P],
         "geo_logdet_trsv": [ctypes.POINTER(geo_tiles), P, P, P, P, P],
+        "geo_logdet_trsv_noalloc": [ctypes.POINTER(geo_tiles), P, P, P, P],
         "geo_status": [ctypes.POINTER(geo_tiles), ctypes.POINTER(I), ctypes.POINTER(I), P],
         "geo_loglik": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, ctypes.POINTER(D), ctypes.POINTER(I), P],
         "geo_krige": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, P, P, I, P, P, P],
