@@ -86,13 +86,29 @@ typedef struct geo_tiles {
     void* ev_join;
     unsigned long long tmap[32];  /* library-private: TMA descriptors of the BF16 planes */
     int flags;                    /* GEO_FLAG_* options, set with geo_tiles_set_flags */
+    void* trace;                  /* optional device trace buffer (geo_tiles_set_trace) */
+    long long trace_cap;          /* its capacity in records */
 } geo_tiles;
+
+/* One record of the device-side task trace (tensor-core mode scheduler):
+ * type 0..4 = potrf sub-block factor / solve / update, panel trsm, FP64 update
+ * item; 10 = tensor-core update item.  Times are %globaltimer nanoseconds:
+ * claimed, dependencies satisfied, finished. */
+typedef struct geo_trace_rec {
+    int type, sm, k, a, b, c;
+    long long t_claim, t_ready, t_end;
+} geo_trace_rec;
 
 /* Generation option: compute off-band (FP32-stored) covariance entries in FP64
  * and round them to FP32 (Algorithm 1's dlag2s of the FP64 value) instead of
  * computing them in compensated FP32 arithmetic (the default, ~8x fewer FP64
  * operations; entries within (4x+8) 2^-24 relative, x = r/theta2). */
 #define GEO_FLAG_FP64_OFFBAND_GEN 1
+/* Scheduling option (tensor-core mode only): run Algorithm 1 as host-sequenced
+ * outer steps (per step: potrf, trsm, slicing, then the FP64 and tensor-core
+ * updates concurrently) instead of the persistent device-side task scheduler.
+ * Same arithmetic; kept for comparison. */
+#define GEO_FLAG_STEPWISE 2
 
 /* A1, "appropriate ordering" (Section IV): Z-order permutation of n locations.
  * Each coordinate c (expected in [0,1]) is quantised to q = clamp(floor(c*2^16),
@@ -114,6 +130,11 @@ int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp,
                    void* d_planes, void* d_meta, void* stream);
 int geo_tiles_release(geo_tiles* t);
 int geo_tiles_set_flags(geo_tiles* t, int flags);
+/* Record every scheduler task of the following factorizations into d_trace
+ * (device memory: one unsigned long long record counter, padded to 64 bytes,
+ * then `capacity` geo_trace_rec).  The caller zeroes the counter; records past
+ * the capacity are dropped (the counter keeps counting).  NULL disables. */
+int geo_tiles_set_trace(geo_tiles* t, void* d_trace, long long capacity);
 
 /* A2, Eq. 1: write Sigma_ab = C(||s_a - s_b||; theta) (+ nugget if a == b) into
  * every lower tile, each directly in its own precision (the FP64 -> FP32
@@ -133,7 +154,9 @@ int geo_tiles_to_dense(const geo_tiles* t, double* d_out, void* stream);
 
 /* A3-A9, Algorithm 1: factor the tile store in place, A = L L', with the
  * precision map of the bound layout (its band; band >= p is the all-FP64
- * path).  On a non-positive pivot the factorization stops early and the status
+ * path).  In GEO_LP_SPLIT_BF16 mode the tile tasks run in one persistent
+ * cooperative kernel that schedules them on the device by dependency counters
+ * (one CTA per SM; the device must be otherwise idle enough to host it).  On a non-positive pivot the factorization stops early and the status
  * words record GEO_ERR_NOT_SPD with info = 1-based global row.  Asynchronous;
  * read the outcome with geo_status. */
 int geo_potrf_mp(geo_tiles* t, void* stream);

@@ -10,18 +10,22 @@
 #include <vector>
 
 #include "geo_internal.cuh"
+#include "dag.cuh"
 #include "lp_gemm.cuh"
 
 namespace geo {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// meta buffer: off[p*p] int64 | slot[p*p] int32 | status[16] + tickets[2p] int32 | scal doubles
+// meta buffer: off[p*p] int64 | slot[p*p] int32 | status[16] + tickets[2p] int32 |
+// scal doubles | (tensor-core mode) scheduler counters | CUDA-core tasks | tensor targets
 struct MetaOffsets {
-    size_t off, slot, status, scal, total;
+    size_t off, slot, status, scal, sched_ctr, sched_g2, sched_bulk, sched_end, sched_tct, total;
+    SchedGeom geom;
+    bool dag;
 };
 
-static MetaOffsets meta_offsets(int p, int nb) {
+static MetaOffsets meta_offsets(int p, int nb, int band, int lp_mode, int pp) {
     MetaOffsets m;
     size_t b = 0;
     m.off = b;
@@ -32,9 +36,26 @@ static MetaOffsets meta_offsets(int p, int nb) {
     b = align256(b + sizeof(int) * ((size_t)ST_WORDS + 2 * (size_t)p));
     m.scal = b;
     b = align256(b + sizeof(double) * ((size_t)2 * p + 8 + (size_t)p * nb));
+    m.dag = (lp_mode == GEO_LP_SPLIT_BF16);
+    m.geom = sched_geom(p, nb, band, pp);
+    m.sched_ctr = m.sched_g2 = m.sched_bulk = m.sched_end = m.sched_tct = b;
+    if (m.dag) {
+        m.sched_ctr = b;
+        b = align256(b + sizeof(int) * (size_t)m.geom.n_counters);
+        m.sched_g2 = b;
+        b = align256(b + sizeof(G2Task) * (size_t)m.geom.n_prio);
+        m.sched_bulk = b;
+        b = align256(b + sizeof(G2Task) * (size_t)std::max(m.geom.n_bulk, 1LL));
+        m.sched_end = b;
+        b = align256(b + sizeof(int) * (size_t)p);
+        m.sched_tct = b;
+        b = align256(b + sizeof(int4) * (size_t)std::max(m.geom.n_tct, 1LL));
+    }
     m.total = b;
     return m;
 }
+
+static MetaOffsets meta_offsets(const geo_layout& g) { return meta_offsets(g.p, g.nb, g.band, g.lp_mode, g.pp); }
 
 // ---- instrumentation ------------------------------------------------------
 static std::atomic<unsigned long long> g_launches{0};
@@ -103,7 +124,7 @@ Layout make_layout(const geo_tiles* t) {
     L.flags = t->flags;
     L.dp = t->d_dp;
     L.sp = t->d_sp;
-    MetaOffsets mo = meta_offsets(g.p, g.nb);
+    MetaOffsets mo = meta_offsets(g);
     char* base = (char*)t->d_meta;
     L.off = (const long long*)(base + mo.off);
     L.slot = (const int*)(base + mo.slot);
@@ -175,7 +196,7 @@ int geo_layout_init(int n, int nb, int band, int lp_mode, geo_layout* out) {
                          ? align256((size_t)4 * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots) +
                                align256(sizeof(int) * (size_t)g.pp * (size_t)g.n_slots)
                          : 0;
-    g.bytes_meta = meta_offsets(p, nb).total;
+    g.bytes_meta = meta_offsets(g).total;
     *out = g;
     return GEO_OK;
 }
@@ -196,7 +217,7 @@ int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp, 
     t->d_meta = d_meta;
     const int p = lay->p, nb = lay->nb;
     const size_t tile = (size_t)nb * nb;
-    MetaOffsets mo = meta_offsets(p, nb);
+    MetaOffsets mo = meta_offsets(*lay);
     std::vector<char> host(mo.scal, 0);
     long long* off = (long long*)(host.data() + mo.off);
     int* slot = (int*)(host.data() + mo.slot);
@@ -214,6 +235,26 @@ int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp, 
         }
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(d_meta, host.data(), mo.scal, cudaMemcpyHostToDevice, s);
+    std::vector<G2Task> prio, bulk;
+    std::vector<int> trsm_end;
+    std::vector<int4> tct;
+    if (!e && mo.dag) {
+        sched_build(mo.geom, lay->band, prio, bulk, trsm_end, tct);
+        if (!prio.empty())
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_g2, prio.data(), sizeof(G2Task) * prio.size(),
+                                cudaMemcpyHostToDevice, s);
+        if (!e && !bulk.empty())
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_bulk, bulk.data(), sizeof(G2Task) * bulk.size(),
+                                cudaMemcpyHostToDevice, s);
+        if (!e)
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_end, trsm_end.data(), sizeof(int) * trsm_end.size(),
+                                cudaMemcpyHostToDevice, s);
+        if (!e && !tct.empty())
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_tct, tct.data(), sizeof(int4) * tct.size(),
+                                cudaMemcpyHostToDevice, s);
+    }
+    // padding rows of the slice planes are never written by the solves: zero them once
+    if (!e && d_planes && lay->bytes_planes) e = cudaMemsetAsync(d_planes, 0, lay->bytes_planes, s);
     if (!e) e = cudaStreamSynchronize(s);
     cudaStream_t aux = nullptr;
     cudaEvent_t e1 = nullptr, e2 = nullptr;
@@ -239,8 +280,16 @@ int geo_tiles_release(geo_tiles* t) {
 
 int geo_tiles_set_flags(geo_tiles* t, int flags) {
     if (!t) return -1;
-    if (flags & ~GEO_FLAG_FP64_OFFBAND_GEN) return -2;
+    if (flags & ~(GEO_FLAG_FP64_OFFBAND_GEN | GEO_FLAG_STEPWISE)) return -2;
     t->flags = flags;
+    return GEO_OK;
+}
+
+int geo_tiles_set_trace(geo_tiles* t, void* d_trace, long long capacity) {
+    if (!t) return -1;
+    if (d_trace && capacity < 0) return -3;
+    t->trace = d_trace;
+    t->trace_cap = d_trace ? capacity : 0;
     return GEO_OK;
 }
 
@@ -280,13 +329,29 @@ static int reset_status(const Layout& L, cudaStream_t s) {
                                                                                                  : GEO_OK;
 }
 
+static cudaError_t factor(const geo_tiles* t, const Layout& L, cudaStream_t s) {
+    if (L.lp_mode == GEO_LP_SPLIT_BF16 && !(t->flags & GEO_FLAG_STEPWISE)) {
+        MetaOffsets mo = meta_offsets(t->lay);
+        SchedView sv;
+        sv.geom = mo.geom;
+        char* base = (char*)t->d_meta;
+        sv.counters = (int*)(base + mo.sched_ctr);
+        sv.prio = (const G2Task*)(base + mo.sched_g2);
+        sv.bulk = (const G2Task*)(base + mo.sched_bulk);
+        sv.trsm_end = (const int*)(base + mo.sched_end);
+        sv.tct = (const int4*)(base + mo.sched_tct);
+        return run_potrf_dag(t, L, sv, s);
+    }
+    return run_potrf_mp(t, L, s);
+}
+
 int geo_potrf_mp(geo_tiles* t, void* stream) {
     if (check_bound(t)) return -1;
     Layout L = make_layout(t);
     cudaStream_t s = (cudaStream_t)stream;
     int rc = reset_status(L, s);
     if (rc) return rc;
-    return run_potrf_mp(t, L, s) ? GEO_ERR_CUDA : GEO_OK;
+    return factor(t, L, s) ? GEO_ERR_CUDA : GEO_OK;
 }
 
 int geo_logdet_trsv(const geo_tiles* t, const double* d_z, double* d_logdet, double* d_quad, double* d_y,
@@ -338,7 +403,7 @@ int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double*
     int rc = reset_status(L, s);
     if (rc) return rc;
     if (launch_matern_tiles(L, d_x, d_y, make_matern(theta), s)) return GEO_ERR_CUDA;
-    if (run_potrf_mp(t, L, s)) return GEO_ERR_CUDA;
+    if (factor(t, L, s)) return GEO_ERR_CUDA;
     double* res = L.scal + 2 * L.p;
     if (run_logdet_trsv(L, d_z, res, res + 1, nullptr, s)) return GEO_ERR_CUDA;
     double hres[2];

@@ -1,0 +1,1019 @@
+// A9: a persistent device-side tile-DAG scheduler for Algorithm 1 (replaces the
+// paper's StarPU runtime).
+//
+// One cooperative launch, one CTA per SM, runs the whole factorization.  Each
+// CTA hosts two worker groups that take tasks from two global queues:
+//   tensor group (warps 0..5)  off-band updates (sgemm) on the tensor cores: TMA
+//                              warp, single-thread MMA issue, 4 epilogue warps
+//                              (the pipeline of lp_gemm.cu), items taken one at a
+//                              time from the tensor queue;
+//   CUDA-core group (warps 6..9) everything else, from the CUDA-core queue:
+//       PF(k,s)      dpotrf of 32 x 32 sub-block (s,s) of diagonal tile k
+//       PT(k,r,s)    solve of sub-block (r,s) against it
+//       PU(k,r,c,s)  sub-block update (r,c) -= (r,s)(c,s)'      (DMMA f64)
+//       TRSM(k,i,q)  rows of panel tile (i,k): dtrsm (band) or strsm (off band),
+//                    followed, for tensor-core mode, by the fixed-point slicing
+//                    of the solved rows (row exponent + four BF16 planes)
+//       UPD(k,i,j,q) 64 x 64 sub-block of a dsyrk / in-band dgemm    (DMMA f64)
+// Dependencies are integer counters in global memory, raised with release
+// atomics and awaited with acquire loads (bounded by %globaltimer):
+//   upd[i][j]   update items applied to tile (i,j) (all steps)
+//   sub[i][j][q] steps applied to update sub-block q of tile (i,j) (an update
+//               of step k waits only for step k-1 on its own sub-block)
+//   tcnt[i][k]  solved row chunks of panel tile (i,k)
+//   pot[k][r][c] operations applied to sub-block (r,c) of diagonal tile k, in
+//               order: PU for s = 0..min(r,c)-1, then PT (r > c) or PF (r == c)
+// The queues are ordered topologically:
+//   priority:  A(0) C(0) A(1) C(1) ...     A(k) = potrf(k) sub-tasks + trsm(k),
+//                                          C(k) = FP64 items of step k on column k+1
+//   bulk:      B(0) B(1) ...               B(k) = FP64 items of step k on columns >= k+2
+//   tensor:    C'(0) B'(0) C'(1) B'(1) ... (off-band items, same split by column)
+// At most PRIO_LIMIT CUDA-core groups work in the priority queue at once (its
+// tasks form narrow dependency chains; the others keep the FP64 pipes busy with
+// bulk items), and a bulk item of step k is claimed only after the priority head
+// has passed A(k)'s solves.  Every wait is therefore on a task already taken by
+// a co-resident worker whose own waits resolve earlier: the schedule cannot
+// deadlock.  Failure (non-SPD pivot, timeout) sets the status words; all
+// workers poll them and leave, the tensor group draining its copies and MMAs
+// and freeing tensor memory first.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "dag.cuh"
+#include "tc_common.cuh"
+
+namespace geo {
+
+// ------------------------------------------------------------- host side ---
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+SchedGeom sched_geom(int p, int nb, int band, int pp) {
+    SchedGeom g;
+    g.p = p;
+    g.ns = ceil_div(nb, 32);
+    g.nsb64 = ceil_div(nb, 64);
+    g.items64 = g.nsb64 * g.nsb64;
+    g.items_tc = ceil_div(pp, TC_BM) * ceil_div(pp, TC_BN);
+    g.chunks_dp = ceil_div(nb, 32);
+    g.chunks_sp = ceil_div(nb, 128);
+    // counters: grab counters, upd[p*p], tcnt[p*p], pot[p*ns*ns], sub[p*p*maxitems]
+    g.max_items = std::max(g.items64, g.items_tc);
+    g.n_counters = 16 + 2 * (long long)p * p + (long long)p * g.ns * g.ns + (long long)p * p * g.max_items;
+    long long n_prio = 0, n_bulk = 0, n_tct = 0;
+    for (int k = 0; k < p; ++k) {
+        const int ns = g.ns;
+        n_prio += ns + ns * (ns - 1) / 2 + (long long)ns * (ns - 1) * (ns + 1) / 6;   // PF, PT, PU
+        for (int i = k + 1; i < p; ++i) n_prio += is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
+        for (int j = k + 1; j < p; ++j)
+            for (int i = j; i < p; ++i) {
+                if (is_dp(i, j, band)) (j == k + 1 ? n_prio : n_bulk) += g.items64;
+                else n_tct += 1;
+            }
+    }
+    g.n_prio = n_prio;
+    g.n_bulk = n_bulk;
+    g.n_g2 = n_prio + n_bulk;
+    g.n_tct = n_tct;
+    (void)band;
+    return g;
+}
+
+// Fill the CUDA-core queues and the tensor-queue targets in their queue order.
+// Priority queue: A(k) C(k) for k = 0, 1, ...; bulk queue: B(0) B(1) ...;
+// trsm_end[k] = priority-queue index just past A(k)'s triangular solves.
+void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
+                 std::vector<int>& trsm_end, std::vector<int4>& tct) {
+    const int p = g.p, ns = g.ns;
+    prio.clear();
+    bulk.clear();
+    tct.clear();
+    trsm_end.assign((size_t)p, 0);
+    auto A = [&](int k) {
+        for (int s = 0; s < ns; ++s) {
+            prio.push_back({T_PF, k, s, 0, 0});
+            for (int r = s + 1; r < ns; ++r) prio.push_back({T_PT, k, r, s, 0});
+            for (int c = s + 1; c < ns; ++c)
+                for (int r = c; r < ns; ++r) prio.push_back({T_PU, k, r, c, s});
+        }
+        for (int i = k + 1; i < p; ++i) {
+            const int nq = is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
+            for (int q = 0; q < nq; ++q) prio.push_back({T_TRSM, k, i, q, 0});
+        }
+        trsm_end[(size_t)k] = (int)prio.size();
+    };
+    auto fp64_items = [&](std::vector<G2Task>& out, int k, int jlo, int jhi) {
+        for (int j = jlo; j < jhi; ++j)
+            for (int i = j; i < p; ++i)
+                if (is_dp(i, j, band))
+                    for (int q = 0; q < g.items64; ++q) out.push_back({T_UPD, k, i, j, q});
+    };
+    for (int k = 0; k < p; ++k) {
+        A(k);
+        if (k + 1 < p) fp64_items(prio, k, k + 1, k + 2);   // C(k): column k+1
+        fp64_items(bulk, k, k + 2, p);                      // B(k): columns >= k+2
+    }
+    for (int k = 0; k < p; ++k) {
+        for (int i = k + 1; i < p; ++i)                  // C'(k): column k+1
+            if (!is_dp(i, k + 1, band)) tct.push_back(make_int4(i, k + 1, k, 0));
+        for (int j = k + 2; j < p; ++j)                  // B'(k): columns >= k+2
+            for (int i = j; i < p; ++i)
+                if (!is_dp(i, j, band)) tct.push_back(make_int4(i, j, k, 0));
+    }
+}
+
+// ----------------------------------------------------------- device side ---
+constexpr int G2_THREADS = 128;
+constexpr int G2_WARP0 = TC_THREADS / 32;   // 6
+constexpr int DAG_THREADS = TC_THREADS + G2_THREADS;
+constexpr long long DAG_WAIT_NS = 10000000000LL;   // 10 s per wait (legitimate waits are ms)
+constexpr int RING = 8;
+constexpr size_t DAG_DYN_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ring*/;
+
+constexpr int PRIO_LIMIT = 48;   // workers allowed inside priority tasks at once
+
+struct DagArgs {
+    Layout L;
+    const G2Task* prio;
+    const G2Task* bulk;
+    const int* trsm_end;
+    long long n_prio, n_bulk;
+    const int4* tct;
+    long long n_tc_items;
+    int* ctr;    // [0] priority head, [1] tensor head, [2] bulk head, [3] workers in priority tasks
+    int* upd;
+    int* tcnt;
+    int* pot;
+    int* sub;    // [p*p*max_items]: steps applied to each update sub-block of a tile
+    SchedGeom g;
+    unsigned long long* trace_ctr;   // optional task trace (nullptr: off)
+    geo_trace_rec* trace;
+    long long trace_cap;
+};
+
+__device__ __forceinline__ int smid() {
+    int s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
+
+__device__ __forceinline__ void trace_put(const DagArgs& A, int type, int k, int a, int b, int c, long long t0,
+                                          long long t1, long long t2) {
+    if (!A.trace) return;
+    const unsigned long long q = atomicAdd(A.trace_ctr, 1ull);
+    if ((long long)q >= A.trace_cap) return;
+    geo_trace_rec r;
+    r.type = type;
+    r.sm = smid();
+    r.k = k;
+    r.a = a;
+    r.b = b;
+    r.c = c;
+    r.t_claim = t0;
+    r.t_ready = t1;
+    r.t_end = t2;
+    A.trace[q] = r;
+}
+
+__device__ __forceinline__ void g2_sync() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Wait until *p >= v (acquire).  False once the status records a failure or the
+// wait exceeds its bound (then it records GEO_ERR_TIMEOUT with `where`).
+__device__ bool wait_ge(const Layout& L, const int* p, int v, int where) {
+    if (ld_acquire_s32(p) >= v) return true;
+    const long long dl = gtimer() + DAG_WAIT_NS;
+    for (unsigned it = 1;; ++it) {
+        __nanosleep(64);
+        if (ld_acquire_s32(p) >= v) return true;
+        if ((it & 31u) == 0) {
+            if (failed(L)) return false;
+            if (gtimer() > dl) {
+                set_timeout(L, where);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int items_of(const DagArgs& A, int i, int j) {
+    return is_dp(i, j, A.L.band) ? A.g.items64 : A.g.items_tc;
+}
+__device__ __forceinline__ int chunks_of(const DagArgs& A, int i, int k) {
+    return is_dp(i, k, A.L.band) ? A.g.chunks_dp : A.g.chunks_sp;
+}
+__device__ __forceinline__ int* sub_at(const DagArgs& A, int i, int j, int q) {
+    return A.sub + ((size_t)i * A.L.p + j) * A.g.max_items + q;
+}
+__device__ __forceinline__ int* pot_at(const DagArgs& A, int k, int r, int c) {
+    return A.pot + ((size_t)k * A.g.ns + r) * A.g.ns + c;
+}
+
+// ---- CUDA-core group: shared memory of one task at a time
+struct G2Smem {
+    union {
+        struct {
+            double As[2][64 * 12], Bs[2][64 * 12];   // UPD: double-buffered K chunks of 8
+        } upd;
+        struct {
+            double D[32 * 33], X[32 * 33];           // PF / PT / PU operands
+        } pot;
+        struct {
+            double Lb[(16 * 32 + 32 * 33) / 2 + 8];  // TRSM: 16 x SB stage + SB x SB diagonal block
+        } tr;
+    };
+    int task, ok;
+};
+
+// PF(k,s): FP64 Cholesky of the 32 x 32 sub-block (s,s); warp 0 of the group.
+__device__ bool g2_pf(const DagArgs& A, G2Smem& S, int k, int s, int g) {
+    const Layout& L = A.L;
+    const int nb = L.nb, c0 = s * 32, w = min(32, nb - c0), lane = g & 31;
+    double* T = dp_tile(L, k, k);
+    double* D = S.pot.D;
+    for (int idx = g; idx < w * w; idx += G2_THREADS) {
+        const int r = idx % w, c = idx / w;
+        D[r * 33 + c] = T[(size_t)(c0 + c) * nb + c0 + r];
+    }
+    g2_sync();
+    if (g == 0) S.ok = 1;
+    g2_sync();
+    if (g < 32) {
+        for (int c = 0; c < w; ++c) {
+            double d = D[c * 33 + c];
+            if (!(d > 0.0)) {
+                if (lane == 0) {
+                    S.ok = 0;
+                    if (atomicCAS(L.status + ST_CODE, 0, GEO_ERR_NOT_SPD) == 0) L.status[ST_INFO] = k * nb + c0 + c + 1;
+                }
+                break;
+            }
+            d = sqrt(d);
+            __syncwarp();
+            if (lane == c) D[c * 33 + c] = d;
+            if (lane > c && lane < w) D[lane * 33 + c] /= d;
+            __syncwarp();
+            if (lane > c && lane < w) {
+                const double lc = D[lane * 33 + c];
+                for (int j = c + 1; j <= lane; ++j) D[lane * 33 + j] -= lc * D[j * 33 + c];
+            }
+            __syncwarp();
+        }
+    }
+    g2_sync();
+    if (!S.ok) return false;
+    for (int idx = g; idx < w * w; idx += G2_THREADS) {
+        const int r = idx % w, c = idx / w;
+        if (r >= c) T[(size_t)(c0 + c) * nb + c0 + r] = D[r * 33 + c];
+    }
+    return true;
+}
+
+// PT(k,r,s): X(r,s) <- X(r,s) L(s,s)^-T; thread per row (32 rows).
+__device__ void g2_pt(const DagArgs& A, G2Smem& S, int k, int r, int s, int g) {
+    const Layout& L = A.L;
+    const int nb = L.nb, c0 = s * 32, r0 = r * 32, w = min(32, nb - c0), h = min(32, nb - r0);
+    double* T = dp_tile(L, k, k);
+    double* D = S.pot.D;
+    double* X = S.pot.X;
+    for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
+        const int a = idx % 32, b = idx / 32;
+        D[a * 33 + b] = (a < w && b < w && a >= b) ? T[(size_t)(c0 + b) * nb + c0 + a] : 0.0;
+        X[a * 33 + b] = (a < h && b < w) ? T[(size_t)(c0 + b) * nb + r0 + a] : 0.0;
+    }
+    g2_sync();
+    if (g < h) {
+        for (int c = 0; c < w; ++c) {
+            double acc = X[g * 33 + c];
+            for (int t = 0; t < c; ++t) acc = fma(-X[g * 33 + t], D[c * 33 + t], acc);
+            X[g * 33 + c] = acc / D[c * 33 + c];
+        }
+    }
+    g2_sync();
+    for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
+        const int a = idx % 32, b = idx / 32;
+        if (a < h && b < w) T[(size_t)(c0 + b) * nb + r0 + a] = X[a * 33 + b];
+    }
+}
+
+__device__ __forceinline__ void dmma884(double& c0, double& c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
+
+// PU(k,r,c,s): sub-block (r,c) -= (r,s)(c,s)'; 4 warps x 16 x 16, DMMA.
+__device__ void g2_pu(const DagArgs& A, G2Smem& S, int k, int r, int c, int s, int g) {
+    const Layout& L = A.L;
+    const int nb = L.nb, s0 = s * 32, r0 = r * 32, q0 = c * 32;
+    double* T = dp_tile(L, k, k);
+    double* Ar = S.pot.D;
+    double* Bc = S.pot.X;
+    for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
+        const int a = idx % 32, t = idx / 32;
+        const bool tv = s0 + t < nb;
+        Ar[a * 33 + t] = (tv && r0 + a < nb) ? T[(size_t)(s0 + t) * nb + r0 + a] : 0.0;
+        Bc[a * 33 + t] = (tv && q0 + a < nb) ? T[(size_t)(s0 + t) * nb + q0 + a] : 0.0;
+    }
+    g2_sync();
+    const int lane = g & 31, wp = g >> 5, gi = lane >> 2, tq = lane & 3;
+    const int wr = (wp >> 1) * 16, wc = (wp & 1) * 16;
+    double acc[2][2][2] = {{{0.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 0.0}}};
+#pragma unroll
+    for (int kk = 0; kk < 32; kk += 4) {
+        double af[2], bf[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) af[a] = Ar[(wr + a * 8 + gi) * 33 + kk + tq];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) bf[b] = Bc[(wc + b * 8 + gi) * 33 + kk + tq];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) dmma884(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int rr = r0 + wr + a * 8 + gi, cc = q0 + wc + b * 8 + 2 * tq + e;
+                if (rr < nb && cc < nb && (r != c || rr >= cc)) T[(size_t)cc * nb + rr] -= acc[a][b][e];
+            }
+}
+
+// TRSM rows [r0, r0 + nrows) of panel tile (i,k) against L_kk (T = double for a
+// band tile, float against FP32(L_kk) otherwise); thread g owns row r0 + g.
+// Left-looking over super-blocks of SB columns held in registers: each earlier
+// solved value of the row is read once per super-block and feeds SB FMAs, 16
+// reads in flight at a time; the earlier columns' contributions are summed 16
+// terms at a time before entering the accumulator.  L is staged through shared
+// memory 16 x SB (and SB x SB for the diagonal block).  Returns max |x| of the row.
+template <typename T, int SB>
+__device__ float g2_trsm_rows(const double* __restrict__ Lkk, T* __restrict__ X, int nb, int r0, int nrows, int g,
+                              G2Smem& S) {
+    const int r = r0 + g;
+    const bool valid = g < nrows && r < nb;
+    T* Lst = reinterpret_cast<T*>(S.tr.Lb);            // [16][SB]
+    T* Ld = reinterpret_cast<T*>(S.tr.Lb) + 16 * SB;   // [SB][SB + 1]
+    float rowmax = 0.0f;
+    for (int sb0 = 0; sb0 < nb; sb0 += SB) {
+        const int w = min(SB, nb - sb0);
+        T acc[SB];
+#pragma unroll
+        for (int jj = 0; jj < SB; ++jj) acc[jj] = (valid && jj < w) ? X[(size_t)(sb0 + jj) * nb + r] : (T)0;
+        // software pipeline over the stages of 16 earlier columns: the loads of
+        // stage t0 + 16 are issued before the FMAs of stage t0
+        constexpr int LPT = 16 * SB / G2_THREADS;   // staged L values per thread
+        T lreg[LPT], xs[16];
+        auto load_stage = [&](int t0) {
+#pragma unroll
+            for (int u = 0; u < LPT; ++u) {
+                const int idx = g + u * G2_THREADS, tt = idx / SB, jj = idx % SB;
+                lreg[u] = (jj < w) ? (T)Lkk[(size_t)(t0 + tt) * nb + sb0 + jj] : (T)0;
+            }
+            if (valid) {
+#pragma unroll
+                for (int tt = 0; tt < 16; ++tt) xs[tt] = X[(size_t)(t0 + tt) * nb + r];
+            }
+        };
+        if (sb0 > 0) load_stage(0);
+        for (int t0 = 0; t0 < sb0; t0 += 16) {
+#pragma unroll
+            for (int u = 0; u < LPT; ++u) Lst[g + u * G2_THREADS] = lreg[u];
+            T xcur[16];
+#pragma unroll
+            for (int tt = 0; tt < 16; ++tt) xcur[tt] = xs[tt];
+            g2_sync();
+            if (t0 + 16 < sb0) load_stage(t0 + 16);
+            if (valid) {
+                T part[SB];
+#pragma unroll
+                for (int jj = 0; jj < SB; ++jj) part[jj] = (T)0;
+#pragma unroll
+                for (int tt = 0; tt < 16; ++tt)
+#pragma unroll
+                    for (int jj = 0; jj < SB; ++jj) part[jj] = fma(xcur[tt], Lst[tt * SB + jj], part[jj]);
+#pragma unroll
+                for (int jj = 0; jj < SB; ++jj) acc[jj] -= part[jj];
+            }
+            g2_sync();
+        }
+        // diagonal block: Ld[jj][ii] = L[sb0 + jj][sb0 + ii]
+        for (int idx = g; idx < SB * SB; idx += G2_THREADS) {
+            const int jj = idx / SB, ii = idx % SB;
+            Ld[jj * (SB + 1) + ii] = (jj < w && ii <= jj) ? (T)Lkk[(size_t)(sb0 + ii) * nb + sb0 + jj] : (T)0;
+        }
+        g2_sync();
+        if (valid) {
+#pragma unroll
+            for (int jj = 0; jj < SB; ++jj) {
+                if (jj < w) {
+                    const T xv = acc[jj] / Ld[jj * (SB + 1) + jj];
+                    acc[jj] = xv;
+#pragma unroll
+                    for (int j2 = jj + 1; j2 < SB; ++j2) acc[j2] -= xv * Ld[j2 * (SB + 1) + jj];
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < SB; ++jj)
+                if (jj < w) {
+                    X[(size_t)(sb0 + jj) * nb + r] = acc[jj];
+                    rowmax = fmaxf(rowmax, fabsf((float)acc[jj]));
+                }
+        }
+        g2_sync();
+    }
+    return rowmax;
+}
+
+// Fixed-point slicing of one solved row (see lp_gemm.cuh): row exponent and
+// four BF16 planes of the whole padded row.
+template <typename T>
+__device__ void g2_slice_row(const Layout& L, const T* __restrict__ X, int i, int k, int r, float m) {
+    const int nb = L.nb, pp = L.pp;
+    int e = 0;
+    if (m > 0.0f) {
+        frexpf(m, &e);
+        e += 1;
+    }
+    const int slot = L.slot[i * L.p + k];
+    L.rexp[(size_t)slot * pp + r] = e;
+    __nv_bfloat16* P0 = plane(L, i, k, 0) + (size_t)r * pp;
+    __nv_bfloat16* P1 = plane(L, i, k, 1) + (size_t)r * pp;
+    __nv_bfloat16* P2 = plane(L, i, k, 2) + (size_t)r * pp;
+    __nv_bfloat16* P3 = plane(L, i, k, 3) + (size_t)r * pp;
+    for (int c0 = 0; c0 < pp; c0 += 8) {
+        __align__(16) __nv_bfloat16 s0[8], s1[8], s2[8], s3[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = c0 + q;
+            const float v = (c < nb) ? (float)X[(size_t)c * nb + r] : 0.0f;
+            const float t0 = ldexpf(v, 8 - e);
+            const float a0 = rintf(t0);
+            const float t1 = (t0 - a0) * 256.0f;
+            const float a1 = rintf(t1);
+            const float t2 = (t1 - a1) * 256.0f;
+            const float a2 = rintf(t2);
+            const float a3 = rintf((t2 - a2) * 256.0f);
+            s0[q] = __float2bfloat16_rn(a0);
+            s1[q] = __float2bfloat16_rn(a1 * (1.0f / 256.0f));
+            s2[q] = __float2bfloat16_rn(a2 * (1.0f / 65536.0f));
+            s3[q] = __float2bfloat16_rn(a3 * (1.0f / 16777216.0f));
+        }
+        *reinterpret_cast<uint4*>(P0 + c0) = *reinterpret_cast<const uint4*>(s0);
+        *reinterpret_cast<uint4*>(P1 + c0) = *reinterpret_cast<const uint4*>(s1);
+        *reinterpret_cast<uint4*>(P2 + c0) = *reinterpret_cast<const uint4*>(s2);
+        *reinterpret_cast<uint4*>(P3 + c0) = *reinterpret_cast<const uint4*>(s3);
+    }
+}
+
+// UPD(k,i,j,q): 64 x 64 sub-block q of target (i,j) -= A(i,k) A(j,k)' in FP64.
+__device__ void g2_upd(const DagArgs& A, G2Smem& S, int k, int i, int j, int q, int g) {
+    const Layout& L = A.L;
+    const int nb = L.nb, nsb = A.g.nsb64;
+    const int sbr = q / nsb, sbc = q % nsb;
+    const bool syrk = (i == j);
+    if (syrk && sbr < sbc) return;
+    const int R0 = sbr * 64, C0 = sbc * 64;
+    const int lane = g & 31, wp = g >> 5, gi = lane >> 2, tq = lane & 3;
+    const int wr = (wp >> 1) * 32, wc = (wp & 1) * 32;
+    double acc[4][4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+    const bool a_dp = is_dp(i, k, L.band), b_dp = is_dp(j, k, L.band);
+    // on a diagonal sub-block of a dsyrk, the warp owning the upper-right 32 x 32
+    // quadrant has nothing below the diagonal: it only helps with the loads
+    const bool idle = syrk && sbr == sbc && wr == 0 && wc == 32;
+    const double* Ad = a_dp ? dp_tile(L, i, k) : nullptr;
+    const float* Af = a_dp ? nullptr : sp_tile(L, i, k);
+    const double* Bd = b_dp ? dp_tile(L, j, k) : nullptr;
+    const float* Bf = b_dp ? nullptr : sp_tile(L, j, k);
+    double va[4], vb[4];   // 64 x 8 chunk / 128 threads
+    auto fetch = [&](int kc) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = g + u * G2_THREADS, rr = idx % 64, tt = idx / 64, t = kc + tt;
+            va[u] = (R0 + rr < nb && t < nb) ? (a_dp ? Ad[(size_t)t * nb + R0 + rr] : (double)Af[(size_t)t * nb + R0 + rr]) : 0.0;
+            vb[u] = (C0 + rr < nb && t < nb) ? (b_dp ? Bd[(size_t)t * nb + C0 + rr] : (double)Bf[(size_t)t * nb + C0 + rr]) : 0.0;
+        }
+    };
+    auto store = [&](int b) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = g + u * G2_THREADS;
+            S.upd.As[b][(idx % 64) * 12 + idx / 64] = va[u];
+            S.upd.Bs[b][(idx % 64) * 12 + idx / 64] = vb[u];
+        }
+    };
+    fetch(0);
+    store(0);
+    g2_sync();
+    int buf = 0;
+    for (int kc = 0; kc < nb; kc += 8, buf ^= 1) {
+        const bool more = kc + 8 < nb;
+        if (more) fetch(kc + 8);
+#pragma unroll
+        for (int kk = 0; kk < 8; kk += 4) {
+            if (idle) break;
+            double af[4], bf[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) af[a] = S.upd.As[buf][(wr + a * 8 + gi) * 12 + kk + tq];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bf[b] = S.upd.Bs[buf][(wc + b * 8 + gi) * 12 + kk + tq];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) dmma884(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
+        }
+        if (more) store(buf ^ 1);
+        g2_sync();
+    }
+    double* C = dp_tile(L, i, j);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int rr = R0 + wr + a * 8 + gi, cc = C0 + wc + b * 8 + 2 * tq + e;
+                if (rr < nb && cc < nb && (!syrk || rr >= cc)) C[(size_t)cc * nb + rr] -= acc[a][b][e];
+            }
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
+
+__device__ void g2_worker(const DagArgs& A, G2Smem& S) {
+    const Layout& L = A.L;
+    const int g = threadIdx.x - TC_THREADS;
+    const int nb = L.nb, ns = A.g.ns;
+    int* prio_head = A.ctr + 0;
+    int* bulk_head = A.ctr + 2;
+    int* inflight = A.ctr + 3;
+    __shared__ long long t_claim, t_ready;
+    for (;;) {
+        // ---- claim: priority queue while fewer than PRIO_LIMIT workers are in it,
+        // otherwise the bulk queue once the priority head has passed the solves
+        // its next items need; sleep when neither is available.
+        if (g == 0) {
+            int kind = -1, idx = -1;
+            const long long dl = gtimer() + DAG_WAIT_NS;
+            for (unsigned spin = 0; kind < 0; ++spin) {
+                if (failed(L)) break;
+                const int ph = ld_volatile(prio_head);
+                if (ph < A.n_prio) {
+                    if (atomicAdd(inflight, 1) < PRIO_LIMIT) {
+                        idx = atomicAdd(prio_head, 1);
+                        if (idx < A.n_prio) {
+                            kind = 0;
+                            break;
+                        }
+                    }
+                    atomicSub(inflight, 1);
+                }
+                const int bh = ld_volatile(bulk_head);
+                if (bh < A.n_bulk) {
+                    const int kb = A.bulk[bh].k;
+                    if (ld_volatile(prio_head) >= A.trsm_end[kb]) {
+                        idx = atomicAdd(bulk_head, 1);
+                        if (idx < A.n_bulk) {
+                            kind = 1;
+                            break;
+                        }
+                    }
+                } else if (ph >= A.n_prio) {
+                    break;   // both queues exhausted
+                }
+                __nanosleep(256);
+                if ((spin & 63u) == 63u && gtimer() > dl) {
+                    set_timeout(L, 10);
+                    break;
+                }
+            }
+            S.task = kind < 0 ? -1 : (kind << 30) | idx;
+            t_claim = gtimer();
+        }
+        g2_sync();
+        if (S.task < 0) return;
+        const int kind = S.task >> 30, tix = S.task & ((1 << 30) - 1);
+        const G2Task t = kind == 0 ? A.prio[tix] : A.bulk[tix];
+        // ---- dependencies (thread 0 waits, the group follows)
+        if (g == 0) {
+            bool ok = true;
+            const int k = t.k;
+            if (kind == 1 && ld_volatile(prio_head) < A.trsm_end[k])
+                ok = wait_ge(L, prio_head, A.trsm_end[k], 25);
+            switch (t.type) {
+                case T_PF:
+                    if (t.a == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * A.g.items64, 11);
+                    ok = ok && wait_ge(L, pot_at(A, k, t.a, t.a), t.a, 12);
+                    break;
+                case T_PT:
+                    if (t.b == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * A.g.items64, 13);
+                    ok = ok && wait_ge(L, pot_at(A, k, t.b, t.b), t.b + 1, 14) &&
+                         wait_ge(L, pot_at(A, k, t.a, t.b), t.b, 15);
+                    break;
+                case T_PU:
+                    if (t.c == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * A.g.items64, 16);
+                    ok = ok && wait_ge(L, pot_at(A, k, t.a, t.c), t.c + 1, 17) &&
+                         wait_ge(L, pot_at(A, k, t.b, t.c), t.c + 1, 18) &&
+                         wait_ge(L, pot_at(A, k, t.a, t.b), t.c, 19);
+                    break;
+                case T_TRSM:
+                    ok = wait_ge(L, pot_at(A, k, ns - 1, ns - 1), ns, 20) &&
+                         wait_ge(L, A.upd + t.a * L.p + k, k * items_of(A, t.a, k), 21);
+                    break;
+                default:   // T_UPD: own sub-block's previous step only
+                    ok = wait_ge(L, A.tcnt + t.a * L.p + k, chunks_of(A, t.a, k), 22) &&
+                         wait_ge(L, A.tcnt + t.b * L.p + k, chunks_of(A, t.b, k), 23) &&
+                         wait_ge(L, sub_at(A, t.a, t.b, t.c), k, 24);
+                    break;
+            }
+            S.ok = ok ? 1 : 0;
+            t_ready = gtimer();
+        }
+        g2_sync();
+        if (!S.ok) return;
+        // ---- the task
+        int* done = nullptr;
+        switch (t.type) {
+            case T_PF:
+                if (!g2_pf(A, S, t.k, t.a, g)) return;
+                done = pot_at(A, t.k, t.a, t.a);
+                break;
+            case T_PT:
+                g2_pt(A, S, t.k, t.a, t.b, g);
+                done = pot_at(A, t.k, t.a, t.b);
+                break;
+            case T_PU:
+                g2_pu(A, S, t.k, t.a, t.b, t.c, g);
+                done = pot_at(A, t.k, t.a, t.b);
+                break;
+            case T_TRSM: {
+                const int i = t.a, k = t.k, q = t.b;
+                const double* Lkk = dp_tile(L, k, k);
+                if (is_dp(i, k, L.band)) {
+                    double* X = dp_tile(L, i, k);
+                    const float m = g2_trsm_rows<double, 16>(Lkk, X, nb, q * 32, 32, g, S);
+                    if (L.planes && g < 32 && q * 32 + g < nb) g2_slice_row<double>(L, X, i, k, q * 32 + g, m);
+                } else {
+                    float* X = sp_tile(L, i, k);
+                    const float m = g2_trsm_rows<float, 32>(Lkk, X, nb, q * 128, 128, g, S);
+                    if (L.planes && q * 128 + g < nb) g2_slice_row<float>(L, X, i, k, q * 128 + g, m);
+                }
+                fence_proxy_async_global();   // the planes are read by TMA
+                done = A.tcnt + i * L.p + k;
+                break;
+            }
+            default:
+                g2_upd(A, S, t.k, t.a, t.b, t.c, g);
+                done = A.upd + t.a * L.p + t.b;
+                break;
+        }
+        __threadfence();
+        g2_sync();
+        if (g == 0) {
+            if (t.type == T_UPD) red_release_add(sub_at(A, t.a, t.b, t.c), 1);
+            red_release_add(done, 1);
+            if (kind == 0) atomicSub(inflight, 1);
+            trace_put(A, t.type, t.k, t.a, t.b, t.c, t_claim, t_ready, gtimer());
+        }
+    }
+}
+
+// ---- tensor group: the split-BF16 update with dynamic items and dependencies
+// bounded mbarrier wait for the scheduler: gives up on a recorded failure, an
+// abort of this CTA, or after DAG_WAIT_NS
+__device__ bool dwait(const Layout& L, uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const long long dl = gtimer() + DAG_WAIT_NS;
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*abort_flag || failed(L)) return false;
+            if (gtimer() > dl) return false;
+        }
+    }
+}
+
+__device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUtensorMap* tmap_b, uint8_t* smem,
+                          uint64_t* bars, uint32_t tmem_base, volatile int* abort_flag, volatile int* ring) {
+    const Layout& L = A.L;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto FULL = [&](int s) { return bar0 + 8u * s; };
+    auto EMPTY = [&](int s) { return bar0 + 8u * (TC_STAGES + s); };
+    auto TFULL = [&](int a) { return bar0 + 8u * (2 * TC_STAGES + a); };
+    auto TEMPTY = [&](int a) { return bar0 + 8u * (2 * TC_STAGES + 2 + a); };
+    auto RFULL = [&](int q) { return bar0 + 8u * (2 * TC_STAGES + 4 + q); };
+    const int nb = L.nb, pp = L.pp, p = L.p;
+    const int nnc = (pp + TC_BN - 1) / TC_BN;
+    const int per = A.g.items_tc;
+    const int nk = pp / TC_BK;
+    if (warp == 0) {
+        if (lane != 0) return;
+        int it = 0;
+        for (int t = 0;; ++t) {
+            long long w = failed(L) || *abort_flag ? -1 : atomicAdd(A.ctr + 1, 1);
+            if (w >= A.n_tc_items) w = -1;
+            int i = 0, j = 0, k = 0, mb = 0, nc = 0;
+            if (w >= 0) {
+                const int4 tg = A.tct[w / per];
+                i = tg.x;
+                j = tg.y;
+                k = tg.z;
+                const int rem = (int)(w % per);
+                mb = rem / nnc;
+                nc = rem % nnc;
+                const bool ok = wait_ge(L, A.tcnt + i * p + k, A.g.chunks_sp, 31) &&
+                                wait_ge(L, A.tcnt + j * p + k, chunks_of(A, j, k), 32);
+                if (!ok) w = -1;
+                else fence_proxy_async_global();
+            }
+            ring[t % RING] = (int)w;
+            mbar_arrive(RFULL(t % RING));
+            const int st0 = it % TC_STAGES;
+            if (w < 0) {
+                // hand the end marker to the MMA thread through the next stage
+                if (dwait(L, EMPTY(st0), ((it / TC_STAGES) & 1) ^ 1, abort_flag)) mbar_arrive(FULL(st0));
+                ++it;
+                break;
+            }
+            const int sa = L.slot[i * p + k] * TC_NS, sb = L.slot[j * p + k] * TC_NS;
+            bool ok = true;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int st = it % TC_STAGES;
+                const uint32_t ph = (it / TC_STAGES) & 1;
+                if (!dwait(L, EMPTY(st), ph ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(FULL(st), TC_STAGE_BYTES);
+                uint8_t* sbase = smem + st * TC_STAGE_BYTES;
+#pragma unroll
+                for (int s = 0; s < TC_NS; ++s)
+                    tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), tmap_a, kc * TC_BK, mb * TC_BM, sa + s, FULL(st));
+#pragma unroll
+                for (int s = 0; s < TC_NS; ++s)
+                    tma_load_3d(smem_u32(sbase + TC_NS * TC_A_BYTES + s * TC_B_BYTES), tmap_b, kc * TC_BK,
+                                nc * TC_BN, sb + s, FULL(st));
+            }
+            if (!ok) {
+                if (!failed(L)) set_timeout(L, 33);
+                *abort_flag = 1;
+                break;
+            }
+        }
+        for (int q = max(0, it - TC_STAGES); q < it; ++q)
+            mbar_wait(FULL(q % TC_STAGES), (q / TC_STAGES) & 1, gtimer() + TC_WAIT_NS);
+    } else if (warp == 1) {
+        if (lane != 0) return;
+        int it = 0;
+        for (int tc = 0;; ++tc) {
+            const int acc = tc & 1;
+            const uint32_t aph = (tc >> 1) & 1;
+            // the first stage of the item carries the item id (or the end marker)
+            const int st0 = it % TC_STAGES;
+            if (!dwait(L, FULL(st0), (it / TC_STAGES) & 1, abort_flag)) {
+                if (!failed(L)) set_timeout(L, 34);
+                *abort_flag = 1;
+                mbar_arrive(TFULL(acc));
+                break;
+            }
+            const int w = ring[tc % RING];
+            if (w < 0) {
+                mbar_arrive(TFULL(acc));   // end marker for the epilogue
+                break;
+            }
+            if (!dwait(L, TEMPTY(acc), aph ^ 1, abort_flag)) {
+                if (!failed(L)) set_timeout(L, 35);
+                *abort_flag = 1;
+                mbar_arrive(TFULL(acc));
+                break;
+            }
+            tc_fence_after();
+            const uint32_t dst0 = tmem_base + acc * (2 * TC_BN), dst1 = dst0 + TC_BN;
+            bool ok = true;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int st = it % TC_STAGES;
+                const uint32_t ph = (it / TC_STAGES) & 1;
+                if (kc > 0 && !dwait(L, FULL(st), ph, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sbase = smem_u32(smem + st * TC_STAGE_BYTES);
+#pragma unroll
+                for (int q = 0; q < TC_NPAIRS; ++q) {
+                    const uint32_t a_addr = sbase + c_pair_a[q] * TC_A_BYTES;
+                    const uint32_t b_addr = sbase + TC_NS * TC_A_BYTES + c_pair_b[q] * TC_B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        if (q == 0)
+                            umma_bf16(dst0, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32), (kc | kk) != 0);
+                        else
+                            umma_bf16(dst1, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
+                                      (kc | (q - 1) | kk) != 0);
+                    }
+                }
+                umma_commit(EMPTY(st));
+            }
+            if (!ok) {
+                if (!failed(L)) set_timeout(L, 36);
+                *abort_flag = 1;
+                mbar_arrive(TFULL(acc));
+                break;
+            }
+            umma_commit(TFULL(acc));
+        }
+        if (it > 0) {
+            const int q = it - 1;
+            mbar_wait(EMPTY(q % TC_STAGES), (q / TC_STAGES) & 1, gtimer() + TC_WAIT_NS);
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lane quadrant warp % 4
+        const int quad = warp & 3;
+        const int row_in = quad * 32 + lane;
+        for (int tc = 0;; ++tc) {
+            const int acc = tc & 1;
+            const uint32_t aph = (tc >> 1) & 1;
+            if (!dwait(L, RFULL(tc % RING), (tc / RING) & 1, abort_flag)) {
+                if (!failed(L)) set_timeout(L, 37);
+                *abort_flag = 1;
+                break;
+            }
+            const int w = ring[tc % RING];
+            if (w < 0) break;
+            const int4 tg = A.tct[w / per];
+            const int i = tg.x, j = tg.y, k = tg.z;
+            const int rem = w % per, mb = rem / nnc, nc = rem % nnc;
+            // read-modify-write of C(i,j) only after the previous step's items on it
+            const long long te0 = gtimer();
+            if (threadIdx.x == 64) {
+                if (!wait_ge(L, sub_at(A, i, j, rem), k, 38)) *abort_flag = 1;
+            }
+            epi_sync();
+            if (*abort_flag) break;
+            float* C = sp_tile(L, i, j);
+            const int r = mb * TC_BM + row_in;
+            const bool rv = r < nb;
+            const int c_begin = nc * TC_BN;
+            const int ncol = rv ? max(0, min(TC_BN, nb - c_begin)) : 0;
+            float* Crow = C + (size_t)c_begin * nb + (rv ? r : 0);
+            constexpr int BATCH = 32;
+            float cpre[BATCH];
+#pragma unroll
+            for (int e = 0; e < BATCH; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0f;
+            if (!dwait(L, TFULL(acc), aph, abort_flag) || *abort_flag) {
+                if (!failed(L)) set_timeout(L, 39);
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (2 * TC_BN);
+            const int* eb = L.rexp + (size_t)L.slot[j * p + k] * pp;
+            const int er = (r < pp) ? L.rexp[(size_t)L.slot[i * p + k] * pp + r] : 0;
+#pragma unroll 1
+            for (int h = 0; h < TC_BN / BATCH; ++h) {
+                if (h > 0) {
+#pragma unroll
+                    for (int e = 0; e < BATCH; ++e)
+                        cpre[e] = (h * BATCH + e < ncol) ? Crow[(size_t)(h * BATCH + e) * nb] : 0.0f;
+                }
+#pragma unroll
+                for (int cc = 0; cc < BATCH; cc += 16) {
+                    float v0[16], v1[16];
+                    tmem_ld16(taddr + h * BATCH + cc, v0);
+                    tmem_ld16(taddr + TC_BN + h * BATCH + cc, v1);
+                    int ec[16];
+                    const int cl0 = c_begin + h * BATCH + cc;
+                    if (cl0 + 16 <= pp) {
+                        const int4* e4 = reinterpret_cast<const int4*>(eb + cl0);
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) {
+                            const int4 w4 = e4[qq];
+                            ec[4 * qq] = w4.x;
+                            ec[4 * qq + 1] = w4.y;
+                            ec[4 * qq + 2] = w4.z;
+                            ec[4 * qq + 3] = w4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) ec[e] = 0;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) cpre[cc + e] -= (v0[e] + v1[e]) * pow2f(er + ec[e] - 16);
+                }
+#pragma unroll
+                for (int e = 0; e < BATCH; ++e)
+                    if (h * BATCH + e < ncol) Crow[(size_t)(h * BATCH + e) * nb] = cpre[e];
+            }
+            tc_fence_before();
+            mbar_arrive(TEMPTY(acc));
+            __threadfence();
+            epi_sync();
+            if (threadIdx.x == 64) {
+                red_release_add(sub_at(A, i, j, rem), 1);
+                red_release_add(A.upd + i * p + j, 1);
+                trace_put(A, 10, k, i, j, rem, te0, te0, gtimer());
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(DAG_THREADS, 1)
+    dag_kernel(DagArgs A, const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b) {
+    extern __shared__ uint8_t dag_smem_raw[];
+    __shared__ G2Smem g2s;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)dag_smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);
+    // bars: FULL[S], EMPTY[S], TFULL[2], TEMPTY[2], RFULL[RING]; then tmem slot, abort flag, ring
+    volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * TC_STAGES + 4 + RING);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* ring = abort_flag + 1;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        const uint32_t b0 = smem_u32(bars);
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(b0 + 8u * s, 1);
+            mbar_init(b0 + 8u * (TC_STAGES + s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(b0 + 8u * (2 * TC_STAGES + a), 1);
+            mbar_init(b0 + 8u * (2 * TC_STAGES + 2 + a), 128);
+        }
+        for (int q = 0; q < RING; ++q) mbar_init(b0 + 8u * (2 * TC_STAGES + 4 + q), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void*)tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    if (threadIdx.x < TC_THREADS) tc_worker(A, &tmap_a, &tmap_b, smem, bars, tmem_base, abort_flag, ring);
+    else g2_worker(A, g2s);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, cudaStream_t s) {
+    static int attr_done = 0, nsm = 0;
+    cudaError_t e;
+    if (!attr_done) {
+        if ((e = cudaFuncSetAttribute(dag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DAG_DYN_SMEM)))
+            return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        attr_done = 1;
+    }
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dag_kernel, DAG_THREADS, DAG_DYN_SMEM))) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    if ((e = cudaMemsetAsync(sv.counters, 0, sizeof(int) * (size_t)sv.geom.n_counters, s))) return e;
+    DagArgs A;
+    A.L = L;
+    A.prio = sv.prio;
+    A.bulk = sv.bulk;
+    A.trsm_end = sv.trsm_end;
+    A.n_prio = sv.geom.n_prio;
+    A.n_bulk = sv.geom.n_bulk;
+    A.tct = sv.tct;
+    A.n_tc_items = sv.geom.n_tct * (long long)sv.geom.items_tc;
+    A.ctr = sv.counters;
+    A.upd = sv.counters + 16;
+    A.tcnt = A.upd + (size_t)L.p * L.p;
+    A.pot = A.tcnt + (size_t)L.p * L.p;
+    A.sub = A.pot + (size_t)L.p * sv.geom.ns * sv.geom.ns;
+    A.g = sv.geom;
+    A.trace_ctr = (unsigned long long*)t->trace;
+    A.trace = t->trace ? (geo_trace_rec*)((char*)t->trace + 64) : nullptr;
+    A.trace_cap = t->trace_cap;
+    CUtensorMap maps[2];
+    memcpy(maps, t->tmap, sizeof(maps));
+    void* args[] = {&A, &maps[0], &maps[1]};
+    prof_begin(0, s);
+    e = cudaLaunchCooperativeKernel((const void*)dag_kernel, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
+    prof_end(0, s);
+    count_launch();
+    return e;
+}
+
+}  // namespace geo

@@ -1,0 +1,38 @@
+// Persistent tile-DAG scheduler of Algorithm 1 (see dag.cu): task records,
+// queue geometry and the host entry point.
+#pragma once
+#include <vector>
+
+#include "geo_internal.cuh"
+
+namespace geo {
+
+enum TaskType : int { T_PF = 0, T_PT = 1, T_PU = 2, T_TRSM = 3, T_UPD = 4 };
+
+// One CUDA-core task: PF(k; a = s), PT(k; a = r, b = s), PU(k; a = r, b = c, c = s),
+// TRSM(k; a = i, b = row chunk), UPD(k; a = i, b = j, c = 64 x 64 sub-block).
+struct G2Task {
+    int type, k, a, b, c;
+};
+
+struct SchedGeom {
+    int p, ns, nsb64, items64, items_tc, max_items, chunks_dp, chunks_sp;
+    long long n_counters, n_g2, n_prio, n_bulk, n_tct;
+};
+
+// Device view of the scheduler's tables inside the meta buffer.
+struct SchedView {
+    SchedGeom geom;
+    int* counters;       // zeroed before each factorization
+    const G2Task* prio;  // CUDA-core priority queue, in order
+    const G2Task* bulk;  // CUDA-core bulk queue, in order
+    const int* trsm_end; // [p] priority index past A(k)'s solves
+    const int4* tct;     // tensor queue targets (i, j, k), in order
+};
+
+SchedGeom sched_geom(int p, int nb, int band, int pp);
+void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
+                 std::vector<int>& trsm_end, std::vector<int4>& tct);
+cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, cudaStream_t s);
+
+}  // namespace geo

@@ -30,6 +30,7 @@ GEO_NOALLOC_MAX_P = 4096
 GEO_LP_SPLIT_BF16 = 0
 GEO_LP_FP32 = 1
 GEO_FLAG_FP64_OFFBAND_GEN = 1
+GEO_FLAG_STEPWISE = 2
 
 
 class GeoError(RuntimeError):
@@ -61,7 +62,8 @@ class geo_tiles(ctypes.Structure):
     _fields_ = [("lay", geo_layout), ("d_dp", ctypes.c_void_p), ("d_sp", ctypes.c_void_p),
                 ("d_planes", ctypes.c_void_p), ("d_meta", ctypes.c_void_p),
                 ("aux_stream", ctypes.c_void_p), ("ev_fork", ctypes.c_void_p), ("ev_join", ctypes.c_void_p),
-                ("tmap", ctypes.c_uint64 * 32), ("flags", ctypes.c_int)]
+                ("tmap", ctypes.c_uint64 * 32), ("flags", ctypes.c_int),
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_longlong)]
 
 
 def _load():
@@ -75,6 +77,7 @@ def _load():
         "geo_tiles_bind": [ctypes.POINTER(geo_tiles), ctypes.POINTER(geo_layout), P, P, P, P, P],
         "geo_tiles_release": [ctypes.POINTER(geo_tiles)],
         "geo_tiles_set_flags": [ctypes.POINTER(geo_tiles), I],
+        "geo_tiles_set_trace": [ctypes.POINTER(geo_tiles), P, ctypes.c_longlong],
         "geo_matern_tiles": [ctypes.POINTER(geo_tiles), P, P, geo_theta, P],
         "geo_tiles_load_dense": [ctypes.POINTER(geo_tiles), P, P],
         "geo_tiles_to_dense": [ctypes.POINTER(geo_tiles), P, P],
@@ -169,6 +172,24 @@ class TileStore:
 
     def set_flags(self, flags: int):
         _check(lib.geo_tiles_set_flags(ctypes.byref(self.t), int(flags)), "geo_tiles_set_flags")
+
+    def enable_trace(self, capacity: int = 1 << 20):
+        """Record the scheduler's tasks of the following factorizations."""
+        import torch
+        self._trace = torch.zeros(64 + 48 * int(capacity), dtype=torch.uint8, device=self._dp.device)
+        _check(lib.geo_tiles_set_trace(ctypes.byref(self.t), _ptr(self._trace), int(capacity)), "geo_tiles_set_trace")
+
+    def read_trace(self, reset: bool = True):
+        """Records (structured numpy array) of the traced tasks, in completion order."""
+        raw = self._trace.cpu().numpy()
+        n = int(raw[:8].view(np.uint64)[0])
+        cap = (raw.size - 64) // 48
+        dt = np.dtype([("type", "i4"), ("sm", "i4"), ("k", "i4"), ("a", "i4"), ("b", "i4"), ("c", "i4"),
+                       ("t_claim", "i8"), ("t_ready", "i8"), ("t_end", "i8")])
+        recs = raw[64:64 + 48 * min(n, cap)].view(dt).copy()
+        if reset:
+            self._trace[:8].zero_()
+        return recs
 
     def __del__(self):
         try:

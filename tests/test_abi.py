@@ -28,9 +28,9 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_sizes_match_header():
-    # geo_theta: 4 doubles; geo_tiles = layout + 7 pointers + 32 u64 + int flags (padded)
+    # geo_theta: 4 doubles; geo_tiles = layout + 7 pointers + 32 u64 + int flags (padded) + trace ptr/cap
     assert ctypes.sizeof(geo.geo_theta) == 32
-    assert ctypes.sizeof(geo.geo_tiles) == ctypes.sizeof(geo.geo_layout) + 7 * 8 + 256 + 8  # int + pad
+    assert ctypes.sizeof(geo.geo_tiles) == ctypes.sizeof(geo.geo_layout) + 7 * 8 + 256 + 8 + 16  # int+pad, trace
 
 
 @pytest.mark.parametrize("n,nb,band", [(1600, 200, 8), (40000, 500, 1), (1000, 96, 2), (50, 64, 1), (1, 16, 1),
