@@ -32,7 +32,6 @@ sys.path.insert(0, ROOT)
 M_GRID = 200          # 200 x 200 = 40,000 locations
 NB = 500
 THETA = (1.0, 0.1, 0.5, 0.0)
-FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 (profiling recipe); our probe measured 0.97 (DMMA)
 CPU_SAMPLE_M = 80            # oracle sample: 80 x 80 = 6,400 locations, tile 400, band 1
 
 
@@ -172,6 +171,89 @@ def run_reference(args):
     }), flush=True)
 
 
+FP64_MEASURED_TFLOPS = 0.97  # DMMA, measured by csrc/tools/fp64_peak_probe.cu on a B300
+FP32_MEASURED_TFLOPS = 68.9  # FFMA, same probe
+TC_PAIRS = 10                # BF16 slice products per off-band split update
+
+
+def algorithmic_flops(p, nb, band):
+    """Algorithmic work of one factorization by arithmetic unit (Algorithm 1's
+    tasks with their textbook counts): FP64 (potrf, in-band trsm, dsyrk,
+    in-band dgemm), FP32 (off-band trsm) and off-band sgemm (2 nb^3 each)."""
+    f64 = p * nb ** 3 / 3.0
+    f32 = 0.0
+    lp = 0.0
+    for k in range(p):
+        for i in range(k + 1, p):
+            if i - k < band:
+                f64 += nb ** 3
+            else:
+                f32 += nb ** 3
+        for j in range(k + 1, p):
+            f64 += nb ** 3                       # dsyrk on (j, j), lower triangle
+            for i in range(j + 1, p):
+                if i - j < band:
+                    f64 += 2.0 * nb ** 3
+                else:
+                    lp += 2.0 * nb ** 3
+    return f64, f32, lp
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+        return pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")), "measured (sustained, MEASURED_PEAKS.json)"
+    return 1400.0, "fallback (sustained 1.4 PFLOP/s of the profiling recipe)"
+
+
+def kernel_rows(ts, args, kern):
+    """Roofline rows for the factorization kernels timed live in the region.
+    The persistent DAG kernel runs every unit at once, so its bound is the
+    largest of the per-unit lower bounds F_unit / P_unit; achieved = that
+    unit's algorithmic flops / the kernel's measured time."""
+    steps = args.steps
+    f64, f32, lp = algorithmic_flops(ts.p, NB, ts.band)
+    bf16_peak, bf16_src = measured_peaks()
+    tc = lp * TC_PAIRS if args.lp == "bf16" else 0.0
+    units = [("FP64 pipe (potrf, in-band trsm, dsyrk, in-band dgemm)", f64, FP64_MEASURED_TFLOPS, "alu",
+              "FP64 DMMA measured by fp64_peak_probe (0.97 TFLOP/s)"),
+             ("FP32 pipe (off-band trsm)", f32 + (lp if args.lp != "bf16" else 0.0), FP32_MEASURED_TFLOPS, "alu",
+              "FP32 FFMA measured by fp64_peak_probe (68.9 TFLOP/s)")]
+    if tc:
+        units.append(("tensor cores (off-band split-BF16, %d products)" % TC_PAIRS, tc, bf16_peak, "tensor",
+                      "bf16 " + bf16_src))
+    rows = []
+    dag_ms, dag_n = kern[4]
+    if dag_n:
+        t = dag_ms / 1000.0 / steps
+        lb = [(f / (pk * 1e12), name, f, pk, bound, src) for name, f, pk, bound, src in units]
+        tstar, name, f, pk, bound, src = max(lb)
+        ach = f / t / 1e12
+        rows.append({"kernel": "dag_kernel (persistent tile DAG: potrf, trsm, dsyrk/dgemm, tcgen05 sgemm)",
+                     "bound": bound, "binding_unit": name, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                     "frac": ach / pk, "lower_bound_ms": tstar * 1e3, "avg_ms": dag_ms / dag_n,
+                     "launches": dag_n, "total_ms": dag_ms, "peak_source": src,
+                     "unit_lower_bounds_ms": {u[1]: u[0] * 1e3 for u in lb}})
+    names = {0: ("fp64_update (dsyrk+dgemm, DMMA)", f64 - ts.p * NB ** 3 / 3.0, FP64_MEASURED_TFLOPS, "alu",
+                 "FP64 DMMA measured by fp64_peak_probe"),
+             1: ("offband_update (split-BF16 tcgen05)", tc, bf16_peak, "tensor", "bf16 " + bf16_src)}
+    for kind, (name, f, pk, bound, src) in names.items():
+        kms, kn = kern[kind]
+        if kn and f:
+            ach = f * steps / (kms / 1000.0) / 1e12
+            rows.append({"kernel": name, "bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                         "frac": ach / pk, "avg_ms": kms / kn, "launches": kn, "total_ms": kms,
+                         "peak_source": src})
+    dominant = max(rows, key=lambda r: r["total_ms"]) if rows else None
+    roofline = None
+    if dominant:
+        roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+        roofline["kernel"] = dominant["kernel"]
+        roofline["traffic"] = None
+    return rows, roofline
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -250,53 +332,8 @@ def main():
     tflops = world * flops * args.steps / (ms / 1000.0) / 1e12
 
     # per-kernel live timings (CUDA events on each kernel's own stream)
-    kern = {}
-    names = {0: "fp64_update (dsyrk+dgemm, DMMA)", 1: "offband_update (split-BF16 tcgen05)" if args.lp == "bf16"
-             else "offband_update (FP32 FMA)", 2: "potrf (FP64, cooperative)", 3: "trsm (panel)"}
-    for kind in range(4):
-        kms, kn = geo.profile_read(kind)
-        kern[kind] = (kms, kn)
-
-    # algorithmic work per kernel kind over the timed steps
-    p, b = ts.p, ts.band
-    f64_upd = 0.0
-    lp_upd = 0.0
-    for k in range(p):
-        for j in range(k + 1, p):
-            f64_upd += NB ** 3                      # dsyrk on (j,j): lower triangle n^3 (2n^3/2)
-            for i in range(j + 1, p):
-                if i - j < b:
-                    f64_upd += 2.0 * NB ** 3
-                else:
-                    lp_upd += 6 * 2.0 * NB ** 3        # six BF16 products per split update
-    f64_upd *= args.steps
-    lp_upd *= args.steps
-    sustained = None
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    bf16_peak = 1800.0
-    peak_src = "fallback"
-    if os.path.exists(peaks_path):
-        pk = json.load(open(peaks_path))
-        bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", bf16_peak))
-        peak_src = "measured (sustained)"
-    rows = []
-    if kern[0][1]:
-        ach = f64_upd / (kern[0][0] / 1000.0) / 1e12
-        rows.append({"kernel": names[0], "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "avg_ms": kern[0][0] / kern[0][1],
-                     "launches": kern[0][1], "total_ms": kern[0][0],
-                     "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s); probe measured 0.97"})
-    if kern[1][1] and args.lp == "bf16":
-        ach = lp_upd / (kern[1][0] / 1000.0) / 1e12
-        rows.append({"kernel": names[1], "bound": "tensor", "achieved": ach, "peak": bf16_peak,
-                     "unit": "TFLOP/s", "frac": ach / bf16_peak, "avg_ms": kern[1][0] / kern[1][1],
-                     "launches": kern[1][1], "total_ms": kern[1][0], "peak_source": f"bf16 {peak_src}"})
-    dominant = max(rows, key=lambda r: r["total_ms"]) if rows else None
-    roofline = None
-    if dominant:
-        roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
-        roofline["kernel"] = dominant["kernel"]
-        roofline["traffic"] = None
+    kern = {kind: geo.profile_read(kind) for kind in range(5)}
+    rows, roofline = kernel_rows(ts, args, kern)
 
     # all-FP64 GPU path: accuracy reference and throughput comparison (one eval)
     fp64 = None

@@ -210,12 +210,14 @@ int geo_krige(const geo_tiles* t, const double* d_x, const double* d_y, const do
 
 /* Instrumentation.  geo_kernel_launches returns the number of kernel launches
  * this library has issued in the process (all entry points, all devices).
- * geo_profile_enable(1) makes geo_potrf_mp bracket each launch of the two
- * trailing-update kernels with CUDA events on the stream it launches them on;
+ * geo_profile_enable(1) makes geo_potrf_mp bracket each launch of its
+ * factorization kernels with CUDA events on the stream it launches them on;
  * geo_profile_read (blocking: synchronizes those events) returns, for
  * kind 0 = FP64 update (dsyrk/dgemm), 1 = off-band update (tensor-core or
- * FP32), 2 = diagonal-tile potrf, 3 = panel trsm, the summed event time in ms
- * and the launch count since the last geo_profile_reset. */
+ * FP32), 2 = diagonal-tile potrf, 3 = panel trsm (kinds 0-3: the step-by-step
+ * driver), 4 = the persistent tile-DAG kernel (the whole factorization in one
+ * launch), the summed event time in ms and the launch count since the last
+ * geo_profile_reset.  An unknown kind returns -1. */
 unsigned long long geo_kernel_launches(void);
 int geo_profile_enable(int on);
 int geo_profile_reset(void);

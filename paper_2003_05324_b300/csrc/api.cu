@@ -66,7 +66,7 @@ struct ProfSlot {
     double ms = 0.0;
     long long launches = 0;
 };
-static ProfSlot g_slots[4];
+static ProfSlot g_slots[5];
 static std::mutex g_prof_mu;
 
 void count_launch(int n) { g_launches += (unsigned long long)n; }
@@ -456,7 +456,7 @@ int geo_profile_reset(void) {
 }
 
 int geo_profile_read(int kind, double* h_ms, long long* h_launches) {
-    if (kind < 0 || kind > 3) return -1;
+    if (kind < 0 || kind > 4) return -1;
     if (!h_ms) return -2;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     prof_collect(g_slots[kind]);

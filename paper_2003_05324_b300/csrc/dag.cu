@@ -1009,9 +1009,9 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
     CUtensorMap maps[2];
     memcpy(maps, t->tmap, sizeof(maps));
     void* args[] = {&A, &maps[0], &maps[1]};
-    prof_begin(0, s);
+    prof_begin(4, s);
     e = cudaLaunchCooperativeKernel((const void*)dag_kernel, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
-    prof_end(0, s);
+    prof_end(4, s);
     count_launch();
     return e;
 }
