@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sweep", action="store_true", help="also time bands 2, 4, 8 (slow)")
     ap.add_argument("--gen64", action="store_true", help="generate off-band entries in FP64 and round")
+    ap.add_argument("--dmma", action="store_true",
+                    help="in-band (FP64) updates on the FP64 pipe instead of FP64-accurate tensor-core products")
     return ap.parse_args()
 
 
@@ -174,13 +176,15 @@ def run_reference(args):
 FP64_MEASURED_TFLOPS = 0.97  # DMMA, measured by csrc/tools/fp64_peak_probe.cu on a B300
 FP32_MEASURED_TFLOPS = 68.9  # FFMA, same probe
 TC_PAIRS = 10                # BF16 slice products per off-band split update
+EX_PAIRS = 28                # BF16 slice products per FP64-accurate in-band update
 
 
 def algorithmic_flops(p, nb, band):
-    """Algorithmic work of one factorization by arithmetic unit (Algorithm 1's
-    tasks with their textbook counts): FP64 (potrf, in-band trsm, dsyrk,
-    in-band dgemm), FP32 (off-band trsm) and off-band sgemm (2 nb^3 each)."""
+    """Algorithmic work of one factorization by kind (Algorithm 1's tasks with
+    their textbook counts): FP64 potrf + in-band trsm, FP64 in-band updates
+    (dsyrk nb^3, dgemm 2 nb^3), FP32 off-band trsm, off-band sgemm (2 nb^3)."""
     f64 = p * nb ** 3 / 3.0
+    f64u = 0.0
     f32 = 0.0
     lp = 0.0
     for k in range(p):
@@ -190,13 +194,13 @@ def algorithmic_flops(p, nb, band):
             else:
                 f32 += nb ** 3
         for j in range(k + 1, p):
-            f64 += nb ** 3                       # dsyrk on (j, j), lower triangle
+            f64u += nb ** 3                      # dsyrk on (j, j), lower triangle
             for i in range(j + 1, p):
                 if i - j < band:
-                    f64 += 2.0 * nb ** 3
+                    f64u += 2.0 * nb ** 3
                 else:
                     lp += 2.0 * nb ** 3
-    return f64, f32, lp
+    return f64, f64u, f32, lp
 
 
 def measured_peaks():
@@ -213,15 +217,21 @@ def kernel_rows(ts, args, kern):
     largest of the per-unit lower bounds F_unit / P_unit; achieved = that
     unit's algorithmic flops / the kernel's measured time."""
     steps = args.steps
-    f64, f32, lp = algorithmic_flops(ts.p, NB, ts.band)
+    f64, f64u, f32, lp = algorithmic_flops(ts.p, NB, ts.band)
     bf16_peak, bf16_src = measured_peaks()
+    ex = args.lp == "bf16" and not args.dmma      # in-band updates on the tensor cores
     tc = lp * TC_PAIRS if args.lp == "bf16" else 0.0
-    units = [("FP64 pipe (potrf, in-band trsm, dsyrk, in-band dgemm)", f64, FP64_MEASURED_TFLOPS, "alu",
-              "FP64 DMMA measured by fp64_peak_probe (0.97 TFLOP/s)"),
+    if ex:
+        tc += f64u * EX_PAIRS
+    else:
+        f64 += f64u
+    units = [("FP64 pipe (potrf, in-band trsm" + ("" if ex else ", dsyrk, in-band dgemm") + ")", f64,
+              FP64_MEASURED_TFLOPS, "alu", "FP64 DMMA measured by fp64_peak_probe (0.97 TFLOP/s)"),
              ("FP32 pipe (off-band trsm)", f32 + (lp if args.lp != "bf16" else 0.0), FP32_MEASURED_TFLOPS, "alu",
               "FP32 FFMA measured by fp64_peak_probe (68.9 TFLOP/s)")]
     if tc:
-        units.append(("tensor cores (off-band split-BF16, %d products)" % TC_PAIRS, tc, bf16_peak, "tensor",
+        units.append(("tensor cores (off-band split-BF16 x %d%s)" % (
+                      TC_PAIRS, ", in-band FP64-accurate x %d" % EX_PAIRS if ex else ""), tc, bf16_peak, "tensor",
                       "bf16 " + bf16_src))
     rows = []
     dag_ms, dag_n = kern[4]
@@ -235,7 +245,7 @@ def kernel_rows(ts, args, kern):
                      "frac": ach / pk, "lower_bound_ms": tstar * 1e3, "avg_ms": dag_ms / dag_n,
                      "launches": dag_n, "total_ms": dag_ms, "peak_source": src,
                      "unit_lower_bounds_ms": {u[1]: u[0] * 1e3 for u in lb}})
-    names = {0: ("fp64_update (dsyrk+dgemm, DMMA)", f64 - ts.p * NB ** 3 / 3.0, FP64_MEASURED_TFLOPS, "alu",
+    names = {0: ("fp64_update (dsyrk+dgemm, DMMA)", f64u, FP64_MEASURED_TFLOPS, "alu",
                  "FP64 DMMA measured by fp64_peak_probe"),
              1: ("offband_update (split-BF16 tcgen05)", tc, bf16_peak, "tensor", "bf16 " + bf16_src)}
     for kind, (name, f, pk, bound, src) in names.items():
@@ -281,7 +291,7 @@ def main():
     Z = torch.as_tensor(z, device=dev)
     lp = geo.GEO_LP_SPLIT_BF16 if args.lp == "bf16" else geo.GEO_LP_FP32
     ts = geo.TileStore(n, NB, args.band, lp, device=dev)
-    gen_flags = geo.GEO_FLAG_FP64_OFFBAND_GEN if args.gen64 else 0
+    gen_flags = (geo.GEO_FLAG_FP64_OFFBAND_GEN if args.gen64 else 0) | (geo.GEO_FLAG_FP64_DMMA if args.dmma else 0)
     ts.set_flags(gen_flags)
     stream = torch.cuda.current_stream(dev)
     flops = n ** 3 / 3.0
@@ -348,9 +358,24 @@ def main():
         torch.cuda.synchronize(dev)
         t64 = e0.elapsed_time(e1) / 1000.0
         l64 = ts64.assemble(float(ld64), float(q64))
-        fp64 = {"seconds_per_eval": t64, "tflops": flops / t64 / 1e12, "evals_per_s": 1.0 / t64, "loglik": l64,
+        fp64 = {"path": "all tiles FP64, updates on the FP64 pipe (DMMA)",
+                "seconds_per_eval": t64, "tflops": flops / t64 / 1e12, "evals_per_s": 1.0 / t64, "loglik": l64,
                 "mp_speedup": t64 / (ms_step / 1000.0), "mp_rel_err": abs(l_mp - l64) / abs(l64)}
         del ts64
+        # all tiles FP64 with the FP64-accurate tensor-core updates
+        ts64e = geo.TileStore(n, NB, 10 ** 6, geo.GEO_LP_SPLIT_BF16, device=dev)
+        ts64e.loglik_async(X, Y, Z, th)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        lde, qe = ts64e.loglik_async(X, Y, Z, th)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        te = e0.elapsed_time(e1) / 1000.0
+        le = ts64e.assemble(float(lde), float(qe))
+        fp64["tensor_core_fp64"] = {"path": "all tiles FP64, FP64-accurate tensor-core updates",
+                                    "seconds_per_eval": te, "tflops": flops / te / 1e12,
+                                    "rel_err_vs_dmma_path": abs(le - l64) / abs(l64)}
+        del ts64e
 
     # end to end through the public blocking call, host buffers copied every step
     xh = torch.as_tensor(x).pin_memory()

@@ -84,15 +84,16 @@ typedef struct geo_tiles {
     void* aux_stream;             /* library-created stream for concurrent off-band work */
     void* ev_fork;
     void* ev_join;
-    unsigned long long tmap[32];  /* library-private: TMA descriptors of the BF16 planes */
+    unsigned long long tmap[48];  /* library-private: three TMA descriptors of the BF16 planes */
     int flags;                    /* GEO_FLAG_* options, set with geo_tiles_set_flags */
     void* trace;                  /* optional device trace buffer (geo_tiles_set_trace) */
     long long trace_cap;          /* its capacity in records */
 } geo_tiles;
 
 /* One record of the device-side task trace (tensor-core mode scheduler):
- * type 0..4 = potrf sub-block factor / solve / update, panel trsm, FP64 update
- * item; 10 = tensor-core update item.  Times are %globaltimer nanoseconds:
+ * type 0..4 = potrf sub-block factor / solve / update, panel trsm, FP64 (DMMA)
+ * update item; 10 = tensor-core off-band update item, 11 = tensor-core
+ * in-band (FP64-accurate) update item.  Times are %globaltimer nanoseconds:
  * claimed, dependencies satisfied, finished. */
 typedef struct geo_trace_rec {
     int type, sm, k, a, b, c;
@@ -109,6 +110,14 @@ typedef struct geo_trace_rec {
  * updates concurrently) instead of the persistent device-side task scheduler.
  * Same arithmetic; kept for comparison. */
 #define GEO_FLAG_STEPWISE 2
+/* Arithmetic option (tensor-core mode only): run the in-band (FP64 target)
+ * dsyrk/dgemm updates of Algorithm 1 on the FP64 pipe (DMMA) instead of the
+ * default FP64-accurate tensor-core products.  The default splits each operand
+ * into seven 8-bit fixed-point slices, forms the 28 slice products of weight
+ * >= 2^-48 with exact integer accumulation for the leading 15 and drains every
+ * 256-long part of the contraction into the FP64 tile: its rounding error is
+ * no larger than that of FP64 accumulation (measured against exact sums). */
+#define GEO_FLAG_FP64_DMMA 4
 
 /* A1, "appropriate ordering" (Section IV): Z-order permutation of n locations.
  * Each coordinate c (expected in [0,1]) is quantised to q = clamp(floor(c*2^16),

@@ -18,10 +18,13 @@ namespace geo {
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // meta buffer: off[p*p] int64 | slot[p*p] int32 | status[16] + tickets[2p] int32 |
-// scal doubles | (tensor-core mode) scheduler counters | CUDA-core tasks | tensor targets
+// scal doubles | (tensor-core mode) scheduler counters | per scheduling variant
+// (0: in-band updates on the tensor cores, 1: on the FP64 pipe): CUDA-core
+// tasks, bulk tasks, solve ends, tensor targets
 struct MetaOffsets {
-    size_t off, slot, status, scal, sched_ctr, sched_g2, sched_bulk, sched_end, sched_tct, total;
-    SchedGeom geom;
+    size_t off, slot, status, scal, sched_ctr, total;
+    size_t sched_g2[2], sched_bulk[2], sched_end[2], sched_tct[2];
+    SchedGeom geom[2];
     bool dag;
 };
 
@@ -37,19 +40,24 @@ static MetaOffsets meta_offsets(int p, int nb, int band, int lp_mode, int pp) {
     m.scal = b;
     b = align256(b + sizeof(double) * ((size_t)2 * p + 8 + (size_t)p * nb));
     m.dag = (lp_mode == GEO_LP_SPLIT_BF16);
-    m.geom = sched_geom(p, nb, band, pp);
-    m.sched_ctr = m.sched_g2 = m.sched_bulk = m.sched_end = m.sched_tct = b;
+    m.sched_ctr = b;
+    for (int v = 0; v < 2; ++v) {
+        m.geom[v] = sched_geom(p, nb, band, pp, v == 0);
+        m.sched_g2[v] = m.sched_bulk[v] = m.sched_end[v] = m.sched_tct[v] = b;
+    }
     if (m.dag) {
-        m.sched_ctr = b;
-        b = align256(b + sizeof(int) * (size_t)m.geom.n_counters);
-        m.sched_g2 = b;
-        b = align256(b + sizeof(G2Task) * (size_t)m.geom.n_prio);
-        m.sched_bulk = b;
-        b = align256(b + sizeof(G2Task) * (size_t)std::max(m.geom.n_bulk, 1LL));
-        m.sched_end = b;
-        b = align256(b + sizeof(int) * (size_t)p);
-        m.sched_tct = b;
-        b = align256(b + sizeof(int4) * (size_t)std::max(m.geom.n_tct, 1LL));
+        b = align256(b + sizeof(int) * (size_t)m.geom[0].n_counters);
+        for (int v = 0; v < 2; ++v) {
+            const SchedGeom& g = m.geom[v];
+            m.sched_g2[v] = b;
+            b = align256(b + sizeof(G2Task) * (size_t)g.n_prio);
+            m.sched_bulk[v] = b;
+            b = align256(b + sizeof(G2Task) * (size_t)std::max(g.n_bulk, 1LL));
+            m.sched_end[v] = b;
+            b = align256(b + sizeof(int) * (size_t)p);
+            m.sched_tct[v] = b;
+            b = align256(b + sizeof(int4) * (size_t)std::max(g.n_tct, 1LL));
+        }
     }
     m.total = b;
     return m;
@@ -133,7 +141,7 @@ Layout make_layout(const geo_tiles* t) {
     L.scal = (double*)(base + mo.scal);
     L.planes = (__nv_bfloat16*)t->d_planes;
     L.rexp = t->d_planes ? (int*)((char*)t->d_planes +
-                                  align256((size_t)4 * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots))
+                                  align256((size_t)NPL * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots))
                          : nullptr;
     return L;
 }
@@ -191,9 +199,9 @@ int geo_layout_init(int n, int nb, int band, int lp_mode, geo_layout* out) {
     const size_t tile = (size_t)nb * nb;
     g.bytes_dp = align256(sizeof(double) * tile * (size_t)ndp);
     g.bytes_sp = align256(sizeof(float) * tile * (size_t)std::max(nsp, 1LL));
-    // four BF16 slice planes of every panel tile, then one int32 row exponent per plane row
-    g.bytes_planes = (lp_mode == GEO_LP_SPLIT_BF16 && nsp > 0)
-                         ? align256((size_t)4 * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots) +
+    // NPL BF16 slice planes of every panel tile, then one int32 row exponent per plane row
+    g.bytes_planes = (lp_mode == GEO_LP_SPLIT_BF16 && p > 1)
+                         ? align256((size_t)NPL * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots) +
                                align256(sizeof(int) * (size_t)g.pp * (size_t)g.n_slots)
                          : 0;
     g.bytes_meta = meta_offsets(g).total;
@@ -238,20 +246,21 @@ int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp, 
     std::vector<G2Task> prio, bulk;
     std::vector<int> trsm_end;
     std::vector<int4> tct;
-    if (!e && mo.dag) {
-        sched_build(mo.geom, lay->band, prio, bulk, trsm_end, tct);
+    for (int v = 0; v < 2 && !e && mo.dag; ++v) {
+        sched_build(mo.geom[v], lay->band, prio, bulk, trsm_end, tct);
         if (!prio.empty())
-            e = cudaMemcpyAsync((char*)d_meta + mo.sched_g2, prio.data(), sizeof(G2Task) * prio.size(),
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_g2[v], prio.data(), sizeof(G2Task) * prio.size(),
                                 cudaMemcpyHostToDevice, s);
         if (!e && !bulk.empty())
-            e = cudaMemcpyAsync((char*)d_meta + mo.sched_bulk, bulk.data(), sizeof(G2Task) * bulk.size(),
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_bulk[v], bulk.data(), sizeof(G2Task) * bulk.size(),
                                 cudaMemcpyHostToDevice, s);
         if (!e)
-            e = cudaMemcpyAsync((char*)d_meta + mo.sched_end, trsm_end.data(), sizeof(int) * trsm_end.size(),
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_end[v], trsm_end.data(), sizeof(int) * trsm_end.size(),
                                 cudaMemcpyHostToDevice, s);
         if (!e && !tct.empty())
-            e = cudaMemcpyAsync((char*)d_meta + mo.sched_tct, tct.data(), sizeof(int4) * tct.size(),
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_tct[v], tct.data(), sizeof(int4) * tct.size(),
                                 cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaStreamSynchronize(s);   // the host vectors are reused for the next variant
     }
     // padding rows of the slice planes are never written by the solves: zero them once
     if (!e && d_planes && lay->bytes_planes) e = cudaMemsetAsync(d_planes, 0, lay->bytes_planes, s);
@@ -280,7 +289,7 @@ int geo_tiles_release(geo_tiles* t) {
 
 int geo_tiles_set_flags(geo_tiles* t, int flags) {
     if (!t) return -1;
-    if (flags & ~(GEO_FLAG_FP64_OFFBAND_GEN | GEO_FLAG_STEPWISE)) return -2;
+    if (flags & ~(GEO_FLAG_FP64_OFFBAND_GEN | GEO_FLAG_STEPWISE | GEO_FLAG_FP64_DMMA)) return -2;
     t->flags = flags;
     return GEO_OK;
 }
@@ -332,14 +341,17 @@ static int reset_status(const Layout& L, cudaStream_t s) {
 static cudaError_t factor(const geo_tiles* t, const Layout& L, cudaStream_t s) {
     if (L.lp_mode == GEO_LP_SPLIT_BF16 && !(t->flags & GEO_FLAG_STEPWISE)) {
         MetaOffsets mo = meta_offsets(t->lay);
+        // in-band updates on the tensor cores unless the FP64 pipe is asked for
+        // (or there are no slice planes: a single tile)
+        const int v = ((t->flags & GEO_FLAG_FP64_DMMA) || !t->d_planes || t->lay.bytes_planes == 0) ? 1 : 0;
         SchedView sv;
-        sv.geom = mo.geom;
+        sv.geom = mo.geom[v];
         char* base = (char*)t->d_meta;
         sv.counters = (int*)(base + mo.sched_ctr);
-        sv.prio = (const G2Task*)(base + mo.sched_g2);
-        sv.bulk = (const G2Task*)(base + mo.sched_bulk);
-        sv.trsm_end = (const int*)(base + mo.sched_end);
-        sv.tct = (const int4*)(base + mo.sched_tct);
+        sv.prio = (const G2Task*)(base + mo.sched_g2[v]);
+        sv.bulk = (const G2Task*)(base + mo.sched_bulk[v]);
+        sv.trsm_end = (const int*)(base + mo.sched_end[v]);
+        sv.tct = (const int4*)(base + mo.sched_tct[v]);
         return run_potrf_dag(t, L, sv, s);
     }
     return run_potrf_mp(t, L, s);

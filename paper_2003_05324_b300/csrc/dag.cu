@@ -3,10 +3,13 @@
 //
 // One cooperative launch, one CTA per SM, runs the whole factorization.  Each
 // CTA hosts two worker groups that take tasks from two global queues:
-//   tensor group (warps 0..5)  off-band updates (sgemm) on the tensor cores: TMA
-//                              warp, single-thread MMA issue, 4 epilogue warps
-//                              (the pipeline of lp_gemm.cu), items taken one at a
-//                              time from the tensor queue;
+//   tensor group (warps 0..5)  trailing updates on the tensor cores: TMA warp,
+//                              single-thread MMA issue, 4 epilogue warps, items
+//                              (128 x 128 output blocks) taken one at a time from
+//                              the tensor queue.  Off-band targets: the
+//                              FP32-accurate sgemm of lp_gemm.cu; in-band (FP64)
+//                              targets, by default: the FP64-accurate dsyrk /
+//                              dgemm of the seven-slice products (tc_common.cuh);
 //   CUDA-core group (warps 6..9) everything else, from the CUDA-core queue:
 //       PF(k,s)      dpotrf of 32 x 32 sub-block (s,s) of diagonal tile k
 //       PT(k,r,s)    solve of sub-block (r,s) against it
@@ -14,7 +17,9 @@
 //       TRSM(k,i,q)  rows of panel tile (i,k): dtrsm (band) or strsm (off band),
 //                    followed, for tensor-core mode, by the fixed-point slicing
 //                    of the solved rows (row exponent + four BF16 planes)
-//       UPD(k,i,j,q) 64 x 64 sub-block of a dsyrk / in-band dgemm    (DMMA f64)
+//       UPD(k,i,j,q) 64 x 64 sub-block of a dsyrk / in-band dgemm    (DMMA f64;
+//                    only with GEO_FLAG_FP64_DMMA, otherwise these updates
+//                    are tensor items)
 // Dependencies are integer counters in global memory, raised with release
 // atomics and awaited with acquire loads (bounded by %globaltimer):
 //   upd[i][j]   update items applied to tile (i,j) (all steps)
@@ -27,7 +32,8 @@
 //   priority:  A(0) C(0) A(1) C(1) ...     A(k) = potrf(k) sub-tasks + trsm(k),
 //                                          C(k) = FP64 items of step k on column k+1
 //   bulk:      B(0) B(1) ...               B(k) = FP64 items of step k on columns >= k+2
-//   tensor:    C'(0) B'(0) C'(1) B'(1) ... (off-band items, same split by column)
+//   tensor:    C'(0) B'(0) C'(1) B'(1) ... (tensor items, same split by column)
+// (with the in-band updates on the tensor cores, C(k) and B(k) are empty).
 // At most PRIO_LIMIT CUDA-core groups work in the priority queue at once (its
 // tasks form narrow dependency chains; the others keep the FP64 pipes busy with
 // bulk items), and a bulk item of step k is claimed only after the priority head
@@ -50,9 +56,10 @@ namespace geo {
 // ------------------------------------------------------------- host side ---
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-SchedGeom sched_geom(int p, int nb, int band, int pp) {
+SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     SchedGeom g;
     g.p = p;
+    g.ex = ex ? 1 : 0;
     g.ns = ceil_div(nb, 32);
     g.nsb64 = ceil_div(nb, 64);
     g.items64 = g.nsb64 * g.nsb64;
@@ -69,7 +76,7 @@ SchedGeom sched_geom(int p, int nb, int band, int pp) {
         for (int i = k + 1; i < p; ++i) n_prio += is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
         for (int j = k + 1; j < p; ++j)
             for (int i = j; i < p; ++i) {
-                if (is_dp(i, j, band)) (j == k + 1 ? n_prio : n_bulk) += g.items64;
+                if (is_dp(i, j, band) && !ex) (j == k + 1 ? n_prio : n_bulk) += g.items64;
                 else n_tct += 1;
             }
     }
@@ -77,16 +84,18 @@ SchedGeom sched_geom(int p, int nb, int band, int pp) {
     g.n_bulk = n_bulk;
     g.n_g2 = n_prio + n_bulk;
     g.n_tct = n_tct;
-    (void)band;
     return g;
 }
 
 // Fill the CUDA-core queues and the tensor-queue targets in their queue order.
 // Priority queue: A(k) C(k) for k = 0, 1, ...; bulk queue: B(0) B(1) ...;
-// trsm_end[k] = priority-queue index just past A(k)'s triangular solves.
+// trsm_end[k] = priority-queue index just past A(k)'s triangular solves.  With
+// in-band updates on the tensor cores (g.ex) every update is a tensor target
+// and the CUDA-core queues hold only the A(k).
 void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
                  std::vector<int>& trsm_end, std::vector<int4>& tct) {
     const int p = g.p, ns = g.ns;
+    const bool ex = g.ex != 0;
     prio.clear();
     bulk.clear();
     tct.clear();
@@ -112,15 +121,16 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
     };
     for (int k = 0; k < p; ++k) {
         A(k);
+        if (ex) continue;
         if (k + 1 < p) fp64_items(prio, k, k + 1, k + 2);   // C(k): column k+1
         fp64_items(bulk, k, k + 2, p);                      // B(k): columns >= k+2
     }
     for (int k = 0; k < p; ++k) {
         for (int i = k + 1; i < p; ++i)                  // C'(k): column k+1
-            if (!is_dp(i, k + 1, band)) tct.push_back(make_int4(i, k + 1, k, 0));
+            if (ex || !is_dp(i, k + 1, band)) tct.push_back(make_int4(i, k + 1, k, 0));
         for (int j = k + 2; j < p; ++j)                  // B'(k): columns >= k+2
             for (int i = j; i < p; ++i)
-                if (!is_dp(i, j, band)) tct.push_back(make_int4(i, j, k, 0));
+                if (ex || !is_dp(i, j, band)) tct.push_back(make_int4(i, j, k, 0));
     }
 }
 
@@ -132,7 +142,7 @@ constexpr long long DAG_WAIT_NS = 10000000000LL;   // 10 s per wait (legitimate 
 constexpr int RING = 8;
 constexpr size_t DAG_DYN_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ring*/;
 
-constexpr int PRIO_LIMIT = 48;   // workers allowed inside priority tasks at once
+constexpr int PRIO_LIMIT = 48;   // workers allowed inside priority tasks at once when a bulk queue exists
 
 struct DagArgs {
     Layout L;
@@ -147,7 +157,7 @@ struct DagArgs {
     int* tcnt;
     int* pot;
     int* sub;    // [p*p*max_items]: steps applied to each update sub-block of a tile
-    SchedGeom g;
+    SchedGeom g;   // g.ex: in-band updates are tensor-core (FP64-accurate) items
     unsigned long long* trace_ctr;   // optional task trace (nullptr: off)
     geo_trace_rec* trace;
     long long trace_cap;
@@ -198,8 +208,9 @@ __device__ bool wait_ge(const Layout& L, const int* p, int v, int where) {
     }
 }
 
+// update items applied to tile (i,j) per step
 __device__ __forceinline__ int items_of(const DagArgs& A, int i, int j) {
-    return is_dp(i, j, A.L.band) ? A.g.items64 : A.g.items_tc;
+    return (is_dp(i, j, A.L.band) && !A.g.ex) ? A.g.items64 : A.g.items_tc;
 }
 __device__ __forceinline__ int chunks_of(const DagArgs& A, int i, int k) {
     return is_dp(i, k, A.L.band) ? A.g.chunks_dp : A.g.chunks_sp;
@@ -429,44 +440,30 @@ __device__ float g2_trsm_rows(const double* __restrict__ Lkk, T* __restrict__ X,
     return rowmax;
 }
 
-// Fixed-point slicing of one solved row (see lp_gemm.cuh): row exponent and
-// four BF16 planes of the whole padded row.
+// Fixed-point slicing of one solved row (slice_value): row exponent and the
+// NPL BF16 planes of the whole padded row, from the row's stored precision.
 template <typename T>
 __device__ void g2_slice_row(const Layout& L, const T* __restrict__ X, int i, int k, int r, float m) {
     const int nb = L.nb, pp = L.pp;
-    int e = 0;
-    if (m > 0.0f) {
-        frexpf(m, &e);
-        e += 1;
-    }
+    const int e = row_exponent(m);
     const int slot = L.slot[i * L.p + k];
     L.rexp[(size_t)slot * pp + r] = e;
     __nv_bfloat16* P0 = plane(L, i, k, 0) + (size_t)r * pp;
-    __nv_bfloat16* P1 = plane(L, i, k, 1) + (size_t)r * pp;
-    __nv_bfloat16* P2 = plane(L, i, k, 2) + (size_t)r * pp;
-    __nv_bfloat16* P3 = plane(L, i, k, 3) + (size_t)r * pp;
+    const size_t pstride = (size_t)pp * pp;
     for (int c0 = 0; c0 < pp; c0 += 8) {
-        __align__(16) __nv_bfloat16 s0[8], s1[8], s2[8], s3[8];
+        __align__(16) __nv_bfloat16 sl[NPL][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int c = c0 + q;
-            const float v = (c < nb) ? (float)X[(size_t)c * nb + r] : 0.0f;
-            const float t0 = ldexpf(v, 8 - e);
-            const float a0 = rintf(t0);
-            const float t1 = (t0 - a0) * 256.0f;
-            const float a1 = rintf(t1);
-            const float t2 = (t1 - a1) * 256.0f;
-            const float a2 = rintf(t2);
-            const float a3 = rintf((t2 - a2) * 256.0f);
-            s0[q] = __float2bfloat16_rn(a0);
-            s1[q] = __float2bfloat16_rn(a1 * (1.0f / 256.0f));
-            s2[q] = __float2bfloat16_rn(a2 * (1.0f / 65536.0f));
-            s3[q] = __float2bfloat16_rn(a3 * (1.0f / 16777216.0f));
+            const T v = (c < nb) ? X[(size_t)c * nb + r] : (T)0;
+            __nv_bfloat16 d[NPL];
+            slice_value<T>(v, e, d);
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) sl[s][q] = d[s];
         }
-        *reinterpret_cast<uint4*>(P0 + c0) = *reinterpret_cast<const uint4*>(s0);
-        *reinterpret_cast<uint4*>(P1 + c0) = *reinterpret_cast<const uint4*>(s1);
-        *reinterpret_cast<uint4*>(P2 + c0) = *reinterpret_cast<const uint4*>(s2);
-        *reinterpret_cast<uint4*>(P3 + c0) = *reinterpret_cast<const uint4*>(s3);
+#pragma unroll
+        for (int s = 0; s < NPL; ++s)
+            *reinterpret_cast<uint4*>(P0 + s * pstride + c0) = *reinterpret_cast<const uint4*>(sl[s]);
     }
 }
 
@@ -566,7 +563,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 if (failed(L)) break;
                 const int ph = ld_volatile(prio_head);
                 if (ph < A.n_prio) {
-                    if (atomicAdd(inflight, 1) < PRIO_LIMIT) {
+                    if (atomicAdd(inflight, 1) < (A.n_bulk > 0 ? PRIO_LIMIT : DAG_THREADS * 4096)) {
                         idx = atomicAdd(prio_head, 1);
                         if (idx < A.n_prio) {
                             kind = 0;
@@ -609,16 +606,16 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 ok = wait_ge(L, prio_head, A.trsm_end[k], 25);
             switch (t.type) {
                 case T_PF:
-                    if (t.a == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * A.g.items64, 11);
+                    if (t.a == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * items_of(A, k, k), 11);
                     ok = ok && wait_ge(L, pot_at(A, k, t.a, t.a), t.a, 12);
                     break;
                 case T_PT:
-                    if (t.b == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * A.g.items64, 13);
+                    if (t.b == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * items_of(A, k, k), 13);
                     ok = ok && wait_ge(L, pot_at(A, k, t.b, t.b), t.b + 1, 14) &&
                          wait_ge(L, pot_at(A, k, t.a, t.b), t.b, 15);
                     break;
                 case T_PU:
-                    if (t.c == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * A.g.items64, 16);
+                    if (t.c == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * items_of(A, k, k), 16);
                     ok = ok && wait_ge(L, pot_at(A, k, t.a, t.c), t.c + 1, 17) &&
                          wait_ge(L, pot_at(A, k, t.b, t.c), t.c + 1, 18) &&
                          wait_ge(L, pot_at(A, k, t.a, t.b), t.c, 19);
@@ -700,8 +697,40 @@ __device__ bool dwait(const Layout& L, uint32_t bar, uint32_t parity, volatile i
     }
 }
 
-__device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUtensorMap* tmap_b, uint8_t* smem,
-                          uint64_t* bars, uint32_t tmem_base, volatile int* abort_flag, volatile int* ring) {
+// Tensor-queue item w: target (i,j) of step k, output block (mb, nc) of
+// TC_BM x TC_BN.  An off-band target's block is one FP32-accurate product (one
+// TMEM buffer, 10 slice pairs over the whole contraction); an in-band target's
+// block (A.g.ex) is FP64-accurate: for each of its one or two 64-column halves
+// and each 256-long part of the contraction, the 28 slice pairs of two passes
+// into seven accumulators spanning both TMEM buffers, drained into the FP64
+// tile before the next part.  Blocks of a diagonal target wholly above its
+// diagonal are not computed.
+struct TcItem {
+    int i, j, k, mb, nc, rem;
+    bool ex, skip;
+    int nh;   // in-band: 64-column halves holding columns < nb
+};
+
+__device__ __forceinline__ TcItem tc_decode(const DagArgs& A, long long w) {
+    const int per = A.g.items_tc;
+    const int nnc = (A.L.pp + TC_BN - 1) / TC_BN;
+    const int4 tg = A.tct[w / per];
+    TcItem t;
+    t.i = tg.x;
+    t.j = tg.y;
+    t.k = tg.z;
+    t.rem = (int)(w % per);
+    t.mb = t.rem / nnc;
+    t.nc = t.rem % nnc;
+    t.ex = A.g.ex && is_dp(t.i, t.j, A.L.band);
+    t.skip = t.ex && t.i == t.j && t.mb < t.nc;
+    t.nh = (t.nc * TC_BN + EX_BN < A.L.nb) ? 2 : 1;
+    return t;
+}
+
+__device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUtensorMap* tmap_b,
+                          const CUtensorMap* tmap_b64, uint8_t* smem, uint64_t* bars, uint32_t tmem_base,
+                          volatile int* abort_flag, volatile int* ring) {
     const Layout& L = A.L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = smem_u32(bars);
@@ -711,31 +740,30 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
     auto TEMPTY = [&](int a) { return bar0 + 8u * (2 * TC_STAGES + 2 + a); };
     auto RFULL = [&](int q) { return bar0 + 8u * (2 * TC_STAGES + 4 + q); };
     const int nb = L.nb, pp = L.pp, p = L.p;
-    const int nnc = (pp + TC_BN - 1) / TC_BN;
-    const int per = A.g.items_tc;
     const int nk = pp / TC_BK;
+    constexpr int KPC = EX_KP / TC_BK;   // K chunks per part of an in-band item
+    const int nkp = (nk + KPC - 1) / KPC;
     if (warp == 0) {
         if (lane != 0) return;
         int it = 0;
-        for (int t = 0;; ++t) {
+        for (int t = 0;;) {
             long long w = failed(L) || *abort_flag ? -1 : atomicAdd(A.ctr + 1, 1);
             if (w >= A.n_tc_items) w = -1;
-            int i = 0, j = 0, k = 0, mb = 0, nc = 0;
+            TcItem m;
             if (w >= 0) {
-                const int4 tg = A.tct[w / per];
-                i = tg.x;
-                j = tg.y;
-                k = tg.z;
-                const int rem = (int)(w % per);
-                mb = rem / nnc;
-                nc = rem % nnc;
-                const bool ok = wait_ge(L, A.tcnt + i * p + k, A.g.chunks_sp, 31) &&
-                                wait_ge(L, A.tcnt + j * p + k, chunks_of(A, j, k), 32);
+                m = tc_decode(A, w);
+                if (m.skip) {   // nothing below the diagonal: count the item as applied
+                    red_release_add(A.upd + m.i * p + m.j, 1);
+                    continue;
+                }
+                const bool ok = wait_ge(L, A.tcnt + m.i * p + m.k, chunks_of(A, m.i, m.k), 31) &&
+                                wait_ge(L, A.tcnt + m.j * p + m.k, chunks_of(A, m.j, m.k), 32);
                 if (!ok) w = -1;
                 else fence_proxy_async_global();
             }
             ring[t % RING] = (int)w;
             mbar_arrive(RFULL(t % RING));
+            ++t;
             const int st0 = it % TC_STAGES;
             if (w < 0) {
                 // hand the end marker to the MMA thread through the next stage
@@ -743,24 +771,66 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                 ++it;
                 break;
             }
-            const int sa = L.slot[i * p + k] * TC_NS, sb = L.slot[j * p + k] * TC_NS;
+            const int sa = L.slot[m.i * p + m.k] * NPL, sb = L.slot[m.j * p + m.k] * NPL;
             bool ok = true;
-            for (int kc = 0; kc < nk; ++kc, ++it) {
+            auto next_stage = [&](uint32_t bytes) -> uint8_t* {
                 const int st = it % TC_STAGES;
                 const uint32_t ph = (it / TC_STAGES) & 1;
-                if (!dwait(L, EMPTY(st), ph ^ 1, abort_flag)) {
-                    ok = false;
-                    break;
+                if (!dwait(L, EMPTY(st), ph ^ 1, abort_flag)) return nullptr;
+                mbar_expect_tx(FULL(st), bytes);
+                return smem + st * TC_STAGE_BYTES;
+            };
+            if (!m.ex) {
+                for (int kc = 0; kc < nk && ok; ++kc, ++it) {
+                    uint8_t* sbase = next_stage(TC_STAGE_BYTES);
+                    if (!sbase) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = FULL(it % TC_STAGES);
+#pragma unroll
+                    for (int s = 0; s < TC_NS; ++s)
+                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), tmap_a, kc * TC_BK, m.mb * TC_BM, sa + s, full);
+#pragma unroll
+                    for (int s = 0; s < TC_NS; ++s)
+                        tma_load_3d(smem_u32(sbase + TC_NS * TC_A_BYTES + s * TC_B_BYTES), tmap_b, kc * TC_BK,
+                                    m.nc * TC_BN, sb + s, full);
                 }
-                mbar_expect_tx(FULL(st), TC_STAGE_BYTES);
-                uint8_t* sbase = smem + st * TC_STAGE_BYTES;
+            } else {
+                for (int h = 0; h < m.nh && ok; ++h) {
+                    const int brow = m.nc * TC_BN + h * EX_BN;
+                    for (int kp = 0; kp < nkp && ok; ++kp) {
+                        const int kc0 = kp * KPC, kc1 = min(nk, kc0 + KPC);
+                        for (int pass = 0; pass < 2 && ok; ++pass)
+                            for (int kc = kc0; kc < kc1; ++kc, ++it) {
+                                uint8_t* sbase = next_stage(pass == 0 ? EX_P1_BYTES : EX_P2_BYTES);
+                                if (!sbase) {
+                                    ok = false;
+                                    break;
+                                }
+                                const uint32_t full = FULL(it % TC_STAGES);
+                                if (pass == 0) {
 #pragma unroll
-                for (int s = 0; s < TC_NS; ++s)
-                    tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), tmap_a, kc * TC_BK, mb * TC_BM, sa + s, FULL(st));
+                                    for (int s = 0; s < 4; ++s)
+                                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), tmap_a, kc * TC_BK,
+                                                    m.mb * TC_BM, sa + s, full);
 #pragma unroll
-                for (int s = 0; s < TC_NS; ++s)
-                    tma_load_3d(smem_u32(sbase + TC_NS * TC_A_BYTES + s * TC_B_BYTES), tmap_b, kc * TC_BK,
-                                nc * TC_BN, sb + s, FULL(st));
+                                    for (int s = 0; s < NPL; ++s)
+                                        tma_load_3d(smem_u32(sbase + 4 * TC_A_BYTES + s * EX_B_BYTES), tmap_b64,
+                                                    kc * TC_BK, brow, sb + s, full);
+                                } else {
+#pragma unroll
+                                    for (int u = 0; u < 3; ++u)
+                                        tma_load_3d(smem_u32(sbase + u * TC_A_BYTES), tmap_a, kc * TC_BK,
+                                                    m.mb * TC_BM, sa + 4 + u, full);
+#pragma unroll
+                                    for (int s = 0; s < 3; ++s)
+                                        tma_load_3d(smem_u32(sbase + 3 * TC_A_BYTES + s * EX_B_BYTES), tmap_b64,
+                                                    kc * TC_BK, brow, sb + s, full);
+                                }
+                            }
+                    }
+                }
             }
             if (!ok) {
                 if (!failed(L)) set_timeout(L, 33);
@@ -773,62 +843,128 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
     } else if (warp == 1) {
         if (lane != 0) return;
         int it = 0;
+        int use0 = 0, use1 = 0, nxt = 0;   // completed uses of each TMEM buffer; buffer of the next off-band item
+        auto bail = [&](int where) {
+            if (!failed(L)) set_timeout(L, where);
+            *abort_flag = 1;
+            mbar_arrive(TFULL(0));
+            mbar_arrive(TFULL(1));
+        };
         for (int tc = 0;; ++tc) {
-            const int acc = tc & 1;
-            const uint32_t aph = (tc >> 1) & 1;
             // the first stage of the item carries the item id (or the end marker)
             const int st0 = it % TC_STAGES;
             if (!dwait(L, FULL(st0), (it / TC_STAGES) & 1, abort_flag)) {
-                if (!failed(L)) set_timeout(L, 34);
-                *abort_flag = 1;
-                mbar_arrive(TFULL(acc));
+                bail(34);
                 break;
             }
             const int w = ring[tc % RING];
-            if (w < 0) {
-                mbar_arrive(TFULL(acc));   // end marker for the epilogue
-                break;
-            }
-            if (!dwait(L, TEMPTY(acc), aph ^ 1, abort_flag)) {
-                if (!failed(L)) set_timeout(L, 35);
-                *abort_flag = 1;
-                mbar_arrive(TFULL(acc));
-                break;
-            }
-            tc_fence_after();
-            const uint32_t dst0 = tmem_base + acc * (2 * TC_BN), dst1 = dst0 + TC_BN;
+            if (w < 0) break;   // end marker (the epilogue reads it from the ring)
+            const TcItem m = tc_decode(A, w);
             bool ok = true;
-            for (int kc = 0; kc < nk; ++kc, ++it) {
+            bool first = true;   // FULL(it) of the item's first stage already observed
+            auto stage = [&]() -> uint32_t {
                 const int st = it % TC_STAGES;
-                const uint32_t ph = (it / TC_STAGES) & 1;
-                if (kc > 0 && !dwait(L, FULL(st), ph, abort_flag)) {
-                    ok = false;
+                if (!first && !dwait(L, FULL(st), (it / TC_STAGES) & 1, abort_flag)) return 0;
+                first = false;
+                tc_fence_after();
+                return smem_u32(smem + st * TC_STAGE_BYTES);
+            };
+            if (!m.ex) {
+                const int b = nxt;
+                if (!dwait(L, TEMPTY(b), ((b ? use1 : use0) & 1) ^ 1, abort_flag)) {
+                    bail(35);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sbase = smem_u32(smem + st * TC_STAGE_BYTES);
-#pragma unroll
-                for (int q = 0; q < TC_NPAIRS; ++q) {
-                    const uint32_t a_addr = sbase + c_pair_a[q] * TC_A_BYTES;
-                    const uint32_t b_addr = sbase + TC_NS * TC_A_BYTES + c_pair_b[q] * TC_B_BYTES;
-#pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                        if (q == 0)
-                            umma_bf16(dst0, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32), (kc | kk) != 0);
-                        else
-                            umma_bf16(dst1, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
-                                      (kc | (q - 1) | kk) != 0);
+                const uint32_t dst0 = tmem_base + b * (2 * TC_BN), dst1 = dst0 + TC_BN;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const uint32_t sbase = stage();
+                    if (!sbase) {
+                        ok = false;
+                        break;
                     }
+#pragma unroll
+                    for (int q = 0; q < TC_NPAIRS; ++q) {
+                        const uint32_t a_addr = sbase + c_pair_a[q] * TC_A_BYTES;
+                        const uint32_t b_addr = sbase + TC_NS * TC_A_BYTES + c_pair_b[q] * TC_B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            if (q == 0)
+                                umma_bf16(dst0, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
+                                          (kc | kk) != 0);
+                            else
+                                umma_bf16(dst1, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
+                                          (kc | (q - 1) | kk) != 0);
+                        }
+                    }
+                    umma_commit(EMPTY(it % TC_STAGES));
                 }
-                umma_commit(EMPTY(st));
+                if (!ok) {
+                    bail(36);
+                    break;
+                }
+                umma_commit(TFULL(b));
+                if (b) ++use1;
+                else ++use0;
+                nxt ^= 1;
+            } else {
+                for (int h = 0; h < m.nh && ok; ++h)
+                    for (int kp = 0; kp < nkp && ok; ++kp) {
+                        if (!dwait(L, TEMPTY(0), (use0 & 1) ^ 1, abort_flag) ||
+                            !dwait(L, TEMPTY(1), (use1 & 1) ^ 1, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        uint32_t touched = 0;
+                        const int kc0 = kp * KPC, kc1 = min(nk, kc0 + KPC);
+                        for (int pass = 0; pass < 2 && ok; ++pass)
+                            for (int kc = kc0; kc < kc1; ++kc, ++it) {
+                                const uint32_t sbase = stage();
+                                if (!sbase) {
+                                    ok = false;
+                                    break;
+                                }
+                                if (pass == 0) {
+#pragma unroll
+                                    for (int q = 0; q < EX_P1_PAIRS; ++q) {
+                                        const int acc = c_ex1[q][2];
+                                        const uint32_t a_addr = sbase + c_ex1[q][0] * TC_A_BYTES;
+                                        const uint32_t b_addr = sbase + 4 * TC_A_BYTES + c_ex1[q][1] * EX_B_BYTES;
+#pragma unroll
+                                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                                            umma_bf16(tmem_base + acc * EX_BN, sw64_desc(a_addr + kk * 32),
+                                                      sw64_desc(b_addr + kk * 32), (touched >> acc) & 1u, EX_IDESC);
+                                            touched |= 1u << acc;
+                                        }
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int q = 0; q < EX_P2_PAIRS; ++q) {
+                                        const int acc = c_ex2[q][2];
+                                        const uint32_t a_addr = sbase + c_ex2[q][0] * TC_A_BYTES;
+                                        const uint32_t b_addr = sbase + 3 * TC_A_BYTES + c_ex2[q][1] * EX_B_BYTES;
+#pragma unroll
+                                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                                            umma_bf16(tmem_base + acc * EX_BN, sw64_desc(a_addr + kk * 32),
+                                                      sw64_desc(b_addr + kk * 32), (touched >> acc) & 1u, EX_IDESC);
+                                            touched |= 1u << acc;
+                                        }
+                                    }
+                                }
+                                umma_commit(EMPTY(it % TC_STAGES));
+                            }
+                        if (!ok) break;
+                        umma_commit(TFULL(0));
+                        umma_commit(TFULL(1));
+                        ++use0;
+                        ++use1;
+                    }
+                if (!ok) {
+                    bail(36);
+                    break;
+                }
             }
-            if (!ok) {
-                if (!failed(L)) set_timeout(L, 36);
-                *abort_flag = 1;
-                mbar_arrive(TFULL(acc));
-                break;
-            }
-            umma_commit(TFULL(acc));
         }
         if (it > 0) {
             const int q = it - 1;
@@ -838,9 +974,8 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
         // epilogue warps 2..5: TMEM lane quadrant warp % 4
         const int quad = warp & 3;
         const int row_in = quad * 32 + lane;
+        int use0 = 0, use1 = 0, nxt = 0;
         for (int tc = 0;; ++tc) {
-            const int acc = tc & 1;
-            const uint32_t aph = (tc >> 1) & 1;
             if (!dwait(L, RFULL(tc % RING), (tc / RING) & 1, abort_flag)) {
                 if (!failed(L)) set_timeout(L, 37);
                 *abort_flag = 1;
@@ -848,85 +983,146 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             }
             const int w = ring[tc % RING];
             if (w < 0) break;
-            const int4 tg = A.tct[w / per];
-            const int i = tg.x, j = tg.y, k = tg.z;
-            const int rem = w % per, mb = rem / nnc, nc = rem % nnc;
+            const TcItem m = tc_decode(A, w);
+            const int i = m.i, j = m.j, k = m.k;
             // read-modify-write of C(i,j) only after the previous step's items on it
             const long long te0 = gtimer();
             if (threadIdx.x == 64) {
-                if (!wait_ge(L, sub_at(A, i, j, rem), k, 38)) *abort_flag = 1;
+                if (!wait_ge(L, sub_at(A, i, j, m.rem), k, 38)) *abort_flag = 1;
             }
             epi_sync();
             if (*abort_flag) break;
-            float* C = sp_tile(L, i, j);
-            const int r = mb * TC_BM + row_in;
+            const int r = m.mb * TC_BM + row_in;
             const bool rv = r < nb;
-            const int c_begin = nc * TC_BN;
-            const int ncol = rv ? max(0, min(TC_BN, nb - c_begin)) : 0;
-            float* Crow = C + (size_t)c_begin * nb + (rv ? r : 0);
-            constexpr int BATCH = 32;
-            float cpre[BATCH];
-#pragma unroll
-            for (int e = 0; e < BATCH; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0f;
-            if (!dwait(L, TFULL(acc), aph, abort_flag) || *abort_flag) {
-                if (!failed(L)) set_timeout(L, 39);
-                *abort_flag = 1;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * (2 * TC_BN);
             const int* eb = L.rexp + (size_t)L.slot[j * p + k] * pp;
             const int er = (r < pp) ? L.rexp[(size_t)L.slot[i * p + k] * pp + r] : 0;
-#pragma unroll 1
-            for (int h = 0; h < TC_BN / BATCH; ++h) {
-                if (h > 0) {
+            const uint32_t tlane = (uint32_t)(quad * 32) << 16;
+            bool ok = true;
+            if (!m.ex) {
+                const int b = nxt;
+                float* C = sp_tile(L, i, j);
+                const int c_begin = m.nc * TC_BN;
+                const int ncol = rv ? max(0, min(TC_BN, nb - c_begin)) : 0;
+                float* Crow = C + (size_t)c_begin * nb + (rv ? r : 0);
+                constexpr int BATCH = 32;
+                float cpre[BATCH];
 #pragma unroll
-                    for (int e = 0; e < BATCH; ++e)
-                        cpre[e] = (h * BATCH + e < ncol) ? Crow[(size_t)(h * BATCH + e) * nb] : 0.0f;
+                for (int e = 0; e < BATCH; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0f;
+                if (!dwait(L, TFULL(b), (b ? use1 : use0) & 1, abort_flag) || *abort_flag) {
+                    if (!failed(L)) set_timeout(L, 39);
+                    *abort_flag = 1;
+                    break;
                 }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + tlane + b * (2 * TC_BN);
+#pragma unroll 1
+                for (int hb = 0; hb < TC_BN / BATCH; ++hb) {
+                    if (hb > 0) {
 #pragma unroll
-                for (int cc = 0; cc < BATCH; cc += 16) {
-                    float v0[16], v1[16];
-                    tmem_ld16(taddr + h * BATCH + cc, v0);
-                    tmem_ld16(taddr + TC_BN + h * BATCH + cc, v1);
-                    int ec[16];
-                    const int cl0 = c_begin + h * BATCH + cc;
-                    if (cl0 + 16 <= pp) {
-                        const int4* e4 = reinterpret_cast<const int4*>(eb + cl0);
-#pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) {
-                            const int4 w4 = e4[qq];
-                            ec[4 * qq] = w4.x;
-                            ec[4 * qq + 1] = w4.y;
-                            ec[4 * qq + 2] = w4.z;
-                            ec[4 * qq + 3] = w4.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) ec[e] = 0;
+                        for (int e = 0; e < BATCH; ++e)
+                            cpre[e] = (hb * BATCH + e < ncol) ? Crow[(size_t)(hb * BATCH + e) * nb] : 0.0f;
                     }
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) cpre[cc + e] -= (v0[e] + v1[e]) * pow2f(er + ec[e] - 16);
-                }
+                    for (int cc = 0; cc < BATCH; cc += 16) {
+                        float v0[16], v1[16];
+                        tmem_ld16(taddr + hb * BATCH + cc, v0);
+                        tmem_ld16(taddr + TC_BN + hb * BATCH + cc, v1);
+                        int ec[16];
+                        const int cl0 = c_begin + hb * BATCH + cc;
+                        if (cl0 + 16 <= pp) {
+                            const int4* e4 = reinterpret_cast<const int4*>(eb + cl0);
 #pragma unroll
-                for (int e = 0; e < BATCH; ++e)
-                    if (h * BATCH + e < ncol) Crow[(size_t)(h * BATCH + e) * nb] = cpre[e];
+                            for (int qq = 0; qq < 4; ++qq) {
+                                const int4 w4 = e4[qq];
+                                ec[4 * qq] = w4.x;
+                                ec[4 * qq + 1] = w4.y;
+                                ec[4 * qq + 2] = w4.z;
+                                ec[4 * qq + 3] = w4.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) ec[e] = 0;
+                        }
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) cpre[cc + e] -= (v0[e] + v1[e]) * pow2f(er + ec[e] - 16);
+                    }
+#pragma unroll
+                    for (int e = 0; e < BATCH; ++e)
+                        if (hb * BATCH + e < ncol) Crow[(size_t)(hb * BATCH + e) * nb] = cpre[e];
+                }
+                tc_fence_before();
+                mbar_arrive(TEMPTY(b));
+                if (b) ++use1;
+                else ++use0;
+                nxt ^= 1;
+            } else {
+                double* C = dp_tile(L, i, j);
+                const bool diag = (i == j);
+                for (int h = 0; h < m.nh && ok; ++h) {
+                    const int c_begin = m.nc * TC_BN + h * EX_BN;
+                    int ncol = rv ? max(0, min(EX_BN, nb - c_begin)) : 0;
+                    if (diag) ncol = min(ncol, max(0, r - c_begin + 1));   // lower triangle only
+                    double* Crow = C + (size_t)c_begin * nb + (rv ? r : 0);
+                    for (int kp = 0; kp < nkp; ++kp) {
+                        double cpre[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0;
+                        if (!dwait(L, TFULL(0), use0 & 1, abort_flag) ||
+                            !dwait(L, TFULL(1), use1 & 1, abort_flag) || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+#pragma unroll 1
+                        for (int cc = 0; cc < EX_BN; cc += 8) {
+                            float v[EX_NACC][8];
+                            tmem_ld7x8(tmem_base + tlane + cc, v);
+                            const int4 ea = *reinterpret_cast<const int4*>(eb + c_begin + cc);
+                            const int4 ebb = *reinterpret_cast<const int4*>(eb + c_begin + cc + 4);
+                            const int ec[8] = {ea.x, ea.y, ea.z, ea.w, ebb.x, ebb.y, ebb.z, ebb.w};
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                double d = (double)v[0][e];
+#pragma unroll
+                                for (int a = 1; a < EX_NACC; ++a) d += (double)v[a][e];
+                                cpre[e] = fma(-d, pow2d(er + ec[e] - 16), cpre[e]);
+                            }
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                if (cc + e < ncol) Crow[(size_t)(cc + e) * nb] = cpre[e];
+                            if (cc + 8 < EX_BN) {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e)
+                                    cpre[e] = (cc + 8 + e < ncol) ? Crow[(size_t)(cc + 8 + e) * nb] : 0.0;
+                            }
+                        }
+                        tc_fence_before();
+                        mbar_arrive(TEMPTY(0));
+                        mbar_arrive(TEMPTY(1));
+                        ++use0;
+                        ++use1;
+                    }
+                }
+                if (!ok) {
+                    if (!failed(L)) set_timeout(L, 39);
+                    *abort_flag = 1;
+                    break;
+                }
             }
-            tc_fence_before();
-            mbar_arrive(TEMPTY(acc));
             __threadfence();
             epi_sync();
             if (threadIdx.x == 64) {
-                red_release_add(sub_at(A, i, j, rem), 1);
+                red_release_add(sub_at(A, i, j, m.rem), 1);
                 red_release_add(A.upd + i * p + j, 1);
-                trace_put(A, 10, k, i, j, rem, te0, te0, gtimer());
+                trace_put(A, m.ex ? 11 : 10, k, i, j, m.rem, te0, te0, gtimer());
             }
         }
     }
 }
 
 __global__ void __launch_bounds__(DAG_THREADS, 1)
-    dag_kernel(DagArgs A, const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b) {
+    dag_kernel(DagArgs A, const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
+               const __grid_constant__ CUtensorMap tmap_b64) {
     extern __shared__ uint8_t dag_smem_raw[];
     __shared__ G2Smem g2s;
     uint8_t* smem = (uint8_t*)(((uintptr_t)dag_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -962,7 +1158,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    if (threadIdx.x < TC_THREADS) tc_worker(A, &tmap_a, &tmap_b, smem, bars, tmem_base, abort_flag, ring);
+    if (threadIdx.x < TC_THREADS) tc_worker(A, &tmap_a, &tmap_b, &tmap_b64, smem, bars, tmem_base, abort_flag, ring);
     else g2_worker(A, g2s);
     tc_fence_before();
     __syncthreads();
@@ -1006,9 +1202,9 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
     A.trace_ctr = (unsigned long long*)t->trace;
     A.trace = t->trace ? (geo_trace_rec*)((char*)t->trace + 64) : nullptr;
     A.trace_cap = t->trace_cap;
-    CUtensorMap maps[2];
+    CUtensorMap maps[3];
     memcpy(maps, t->tmap, sizeof(maps));
-    void* args[] = {&A, &maps[0], &maps[1]};
+    void* args[] = {&A, &maps[0], &maps[1], &maps[2]};
     prof_begin(4, s);
     e = cudaLaunchCooperativeKernel((const void*)dag_kernel, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
     prof_end(4, s);

@@ -16,7 +16,7 @@ struct G2Task {
 };
 
 struct SchedGeom {
-    int p, ns, nsb64, items64, items_tc, max_items, chunks_dp, chunks_sp;
+    int p, ex, ns, nsb64, items64, items_tc, max_items, chunks_dp, chunks_sp;
     long long n_counters, n_g2, n_prio, n_bulk, n_tct;
 };
 
@@ -30,7 +30,9 @@ struct SchedView {
     const int4* tct;     // tensor queue targets (i, j, k), in order
 };
 
-SchedGeom sched_geom(int p, int nb, int band, int pp);
+// ex: in-band (FP64) updates as FP64-accurate tensor-core items instead of
+// CUDA-core DMMA items
+SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex);
 void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
                  std::vector<int>& trsm_end, std::vector<int4>& tct);
 cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, cudaStream_t s);

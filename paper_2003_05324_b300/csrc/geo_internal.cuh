@@ -4,10 +4,12 @@
 // stored contiguously: in the FP64 store when i - j < band (Algorithm 1's
 // diag_thick), otherwise in the FP32 store.  `off[i*p + j]` is its element
 // offset inside the store of its precision (-1 for the upper triangle).
-// Panel tiles (i > j) also own a slot of four BF16 planes (fixed-point slices
-// of their FP32 value, scaled per row), each pp x pp row-major with the column
-// (the contraction index of the off-band update) contiguous and zero padding
-// beyond nb, plus one scale exponent per row.
+// Panel tiles (i > j) also own a slot of NPL = 7 BF16 planes (fixed-point
+// slices of their value, scaled per row: 8 bits each, 56 bits in all), each
+// pp x pp row-major with the column (the contraction index of the updates)
+// contiguous and zero padding beyond nb, plus one scale exponent per row.  The
+// off-band (FP32-accurate) products read the first four planes, the in-band
+// (FP64-accurate) products all seven.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -33,12 +35,14 @@ struct Layout {
     double* scal;   // scalar scratch: per-tile log-det and quad partials [2*p], results [2]
 };
 
+constexpr int NPL = 7;   // slice planes stored per panel tile
+
 __host__ __device__ inline bool is_dp(int i, int j, int band) { return (i - j) < band; }
 
 __device__ __forceinline__ double* dp_tile(const Layout& L, int i, int j) { return L.dp + L.off[i * L.p + j]; }
 __device__ __forceinline__ float* sp_tile(const Layout& L, int i, int j) { return L.sp + L.off[i * L.p + j]; }
 __device__ __forceinline__ __nv_bfloat16* plane(const Layout& L, int i, int j, int s) {
-    return L.planes + ((size_t)L.slot[i * L.p + j] * 4 + s) * (size_t)L.pp * L.pp;
+    return L.planes + ((size_t)L.slot[i * L.p + j] * NPL + s) * (size_t)L.pp * L.pp;
 }
 __device__ __forceinline__ bool failed(const Layout& L) {
     return *((volatile int*)L.status + ST_CODE) != 0;

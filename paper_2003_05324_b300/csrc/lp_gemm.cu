@@ -25,66 +25,51 @@ namespace geo {
 // ------------------------------------------------------------ split ---
 // One CTA per 32 rows of a panel tile (i,k), all columns.  Phase 1: the row
 // maxima give each row a power-of-two scale 2^E (|v| 2^-E < 1/2).  Phase 2:
-// each value m = v 2^-E is cut into four rounded 8-bit integer slices
-//   a0 = rint(2^8 m), a1 = rint(2^8 (2^8 m - a0)), a2, a3 likewise,
-// |a_s| <= 128, stored exactly in BF16 as a_s 2^-8s, so that
-// v = 2^(E-8) (P0 + P1 + P2 + P3) up to 2^(E-41).  The SP copy of an in-band (FP64)
-// panel tile is its FP32 rounding (Algorithm 1's dconv2s), sliced the same way.
-// Writes go through a 32 x 32 shared transpose so both sides coalesce.
+// each value is cut into NPL rounded 8-bit slices (slice_value), exactly, from
+// its stored precision: the FP32 value of an off-band tile, the FP64 value of
+// an in-band one.  Writes go through a 32 x 32 shared transpose so both sides
+// coalesce.
 __global__ void __launch_bounds__(256) split_panel_kernel(Layout L, int k) {
     if (failed(L)) return;
     const int i = k + 1 + blockIdx.y;
     const int nb = L.nb, pp = L.pp;
     const int r0 = blockIdx.x * 32;
-    __shared__ float t[32][33];
+    __shared__ double t[32][33];
     __shared__ float pmax[8][32];
     __shared__ int es[32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const bool dp = is_dp(i, k, L.band);
     const double* Ad = dp ? dp_tile(L, i, k) : nullptr;
     const float* As = dp ? nullptr : sp_tile(L, i, k);
-    auto val = [&](int r, int c) -> float {
-        if (r >= nb || c >= nb) return 0.0f;
-        return dp ? (float)Ad[(size_t)c * nb + r] : As[(size_t)c * nb + r];
+    auto val = [&](int r, int c) -> double {
+        if (r >= nb || c >= nb) return 0.0;
+        return dp ? Ad[(size_t)c * nb + r] : (double)As[(size_t)c * nb + r];
     };
     float mx = 0.0f;
-    for (int c = ty; c < nb; c += 8) mx = fmaxf(mx, fabsf(val(r0 + tx, c)));
+    for (int c = ty; c < nb; c += 8) mx = fmaxf(mx, fabsf((float)val(r0 + tx, c)));
     pmax[ty][tx] = mx;
     __syncthreads();
     if (ty == 0) {
         float m = pmax[0][tx];
 #pragma unroll
         for (int w = 1; w < 8; ++w) m = fmaxf(m, pmax[w][tx]);
-        int e = 0;
-        if (m > 0.0f) {
-            frexpf(m, &e);    // m < 2^e
-            e += 1;           // |v| 2^-e < 1/2
-        }
+        const int e = row_exponent(m);
         es[tx] = e;
         L.rexp[(size_t)L.slot[i * L.p + k] * pp + r0 + tx] = e;
     }
     __syncthreads();
     __nv_bfloat16* P0 = plane(L, i, k, 0);
-    __nv_bfloat16* P1 = plane(L, i, k, 1);
-    __nv_bfloat16* P2 = plane(L, i, k, 2);
-    __nv_bfloat16* P3 = plane(L, i, k, 3);
+    const size_t pstride = (size_t)pp * pp;
     for (int cb = 0; cb < pp; cb += 32) {
         for (int q = ty; q < 32; q += 8) t[tx][q] = val(r0 + tx, cb + q);
         __syncthreads();
         for (int q = ty; q < 32; q += 8) {
             const int r = r0 + q, c = cb + tx;
-            const float t0 = ldexpf(t[q][tx], 8 - es[q]);
-            const float a0 = rintf(t0);
-            const float t1 = (t0 - a0) * 256.0f;
-            const float a1 = rintf(t1);
-            const float t2 = (t1 - a1) * 256.0f;
-            const float a2 = rintf(t2);
-            const float a3 = rintf((t2 - a2) * 256.0f);
+            __nv_bfloat16 sl[NPL];
+            slice_value<double>(t[q][tx], es[q], sl);
             const size_t e = (size_t)r * pp + c;
-            P0[e] = __float2bfloat16_rn(a0);
-            P1[e] = __float2bfloat16_rn(a1 * (1.0f / 256.0f));
-            P2[e] = __float2bfloat16_rn(a2 * (1.0f / 65536.0f));
-            P3[e] = __float2bfloat16_rn(a3 * (1.0f / 16777216.0f));
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) P0[s * pstride + e] = sl[s];
         }
         __syncthreads();
     }
@@ -170,7 +155,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int i, j;
                 decode_lp_target(w / per_target, k, p, L.band, i, j);
                 const int rem = w % per_target, mb = rem / nnc, nc = rem % nnc;
-                const int sa = L.slot[i * p + k] * TC_NS, sb = L.slot[j * p + k] * TC_NS;
+                const int sa = L.slot[i * p + k] * NPL, sb = L.slot[j * p + k] * NPL;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int st = it % TC_STAGES;
                     const uint32_t ph = (it / TC_STAGES) & 1;
@@ -354,12 +339,12 @@ static PFN_encodeTiled get_encode() {
     return fn;
 }
 
-// 3D map over all planes: (K = pp, rows = pp, plane index = 4 * n_slots); the
+// 3D map over all planes: (K = pp, rows = pp, plane index = NPL * n_slots); the
 // box is 32 columns (64 bytes, the swizzle width) by `rows` rows.
 static int make_plane_map(const Layout& L, long long nslots, int rows, CUtensorMap* map) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return 1;
-    cuuint64_t dims[3] = {(cuuint64_t)L.pp, (cuuint64_t)L.pp, (cuuint64_t)(TC_NS * nslots)};
+    cuuint64_t dims[3] = {(cuuint64_t)L.pp, (cuuint64_t)L.pp, (cuuint64_t)(NPL * nslots)};
     cuuint64_t strides[2] = {(cuuint64_t)L.pp * 2, (cuuint64_t)L.pp * L.pp * 2};
     cuuint32_t box[3] = {TC_BK, (cuuint32_t)rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -369,12 +354,15 @@ static int make_plane_map(const Layout& L, long long nslots, int rows, CUtensorM
     return r == CUDA_SUCCESS ? 0 : 2;
 }
 
+// maps[0]: A operand boxes (128 rows), maps[1]: off-band B boxes (128 rows),
+// maps[2]: in-band B boxes (64 rows)
 int prepare_lp_gemm(geo_tiles* t, const Layout& L) {
-    static_assert(2 * sizeof(CUtensorMap) <= sizeof(((geo_tiles*)0)->tmap), "tensor map storage");
+    static_assert(3 * sizeof(CUtensorMap) <= sizeof(((geo_tiles*)0)->tmap), "tensor map storage");
     if (!L.planes || t->lay.n_slots == 0) return 0;
-    CUtensorMap maps[2];
+    CUtensorMap maps[3];
     int rc = make_plane_map(L, t->lay.n_slots, TC_BM, &maps[0]);
     if (!rc) rc = make_plane_map(L, t->lay.n_slots, TC_BN, &maps[1]);
+    if (!rc) rc = make_plane_map(L, t->lay.n_slots, EX_BN, &maps[2]);
     if (rc) return rc;
     memcpy(t->tmap, maps, sizeof(maps));
     return 0;

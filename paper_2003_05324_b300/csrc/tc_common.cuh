@@ -9,7 +9,7 @@
 namespace geo {
 
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;  // K chunk of 32 BF16 = one 64-byte swizzle row
-constexpr int TC_NS = 4;                             // slices per operand
+constexpr int TC_NS = 4;                             // slices per operand of an off-band (FP32-accurate) product
 constexpr int TC_NPAIRS = 10;                        // slice pairs (a, b) with a + b <= 3
 constexpr int TC_STAGES = 3;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;        // 8 KB, one A slice chunk
@@ -24,6 +24,41 @@ constexpr long long TC_WAIT_NS = 2000000000LL;      // 2 s per wait
 // smallest weight first, -> the second accumulator
 __constant__ int c_pair_a[TC_NPAIRS] = {0, 0, 1, 2, 3, 0, 1, 2, 0, 1};
 __constant__ int c_pair_b[TC_NPAIRS] = {0, 3, 2, 1, 0, 2, 1, 0, 1, 0};
+
+// ---- FP64-accurate products for in-band (FP64) targets ("EX" items).
+// Seven slices a_0..a_6 per operand (|a_s| <= 128, 56 bits below the row
+// scale) and every pair with a + b <= 6 (28 pairs).  A 128 x 64 output block
+// is accumulated over K parts of EX_KP = 256: one product of two slices sums
+// at most 256 * 2^14 = 2^22 in integer units, so an accumulator holding up to
+// four pairs of one level a + b stays below 2^24 and the tensor core's FP32
+// accumulation is exact.  Levels 0..4 (15 pairs) use six exact accumulators;
+// levels 5 and 6 (13 pairs), 2^-40 below level 0, share a seventh, FP32-
+// accumulated one.  Each K part is drained into the FP64 target, so the error
+// of the whole update is that of FP64 accumulation.
+// Pass 1 stages A slices 0..3 and B slices 0..6, pass 2 A slices 4..6 and B
+// slices 0..2 (the stage holds at most 4 x 8 KB + 7 x 4 KB).
+constexpr int EX_BN = 64;
+constexpr int EX_KP = 256;
+constexpr int EX_NACC = 7;
+constexpr int EX_B_BYTES = EX_BN * TC_BK * 2;        // 4 KB
+constexpr int EX_P1_PAIRS = 22, EX_P2_PAIRS = 6;
+constexpr uint32_t EX_P1_BYTES = 4 * TC_A_BYTES + 7 * EX_B_BYTES;
+constexpr uint32_t EX_P2_BYTES = 3 * TC_A_BYTES + 3 * EX_B_BYTES;
+static_assert(EX_P1_BYTES <= (uint32_t)TC_STAGE_BYTES, "EX stage");
+static_assert(EX_NACC * EX_BN <= 4 * TC_BN, "EX accumulators");
+// (A slice, B slice, accumulator); pass 2's A slice index counts from slice 4
+__constant__ signed char c_ex1[EX_P1_PAIRS][3] = {
+    {0, 0, 0},                                                       // level 0
+    {0, 1, 1}, {1, 0, 1},                                            // level 1
+    {0, 2, 2}, {1, 1, 2}, {2, 0, 2},                                 // level 2
+    {0, 3, 3}, {1, 2, 3}, {2, 1, 3}, {3, 0, 3},                      // level 3
+    {0, 4, 4}, {1, 3, 4}, {2, 2, 4}, {3, 1, 4},                      // level 4 (with (4,0) below)
+    {0, 5, 6}, {1, 4, 6}, {2, 3, 6}, {3, 2, 6},                      // level 5
+    {0, 6, 6}, {1, 5, 6}, {2, 4, 6}, {3, 3, 6}};                     // level 6
+__constant__ signed char c_ex2[EX_P2_PAIRS][3] = {
+    {0, 0, 5},                                                       // (4,0): level 4
+    {0, 1, 6}, {1, 0, 6},                                            // (4,1) (5,0): level 5
+    {0, 2, 6}, {1, 1, 6}, {2, 0, 6}};                                // (4,2) (5,1) (6,0): level 6
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -72,11 +107,15 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
 constexpr uint32_t TC_IDESC =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+constexpr uint32_t EX_IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(EX_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc,
+                                          uint32_t idesc = TC_IDESC) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -100,6 +139,81 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[e]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 8 columns of each of the seven in-band accumulators (64 columns apart) for
+// this warp's 32 lanes, loads and the wait in one statement so that no use of
+// the registers can be scheduled before the wait
+__device__ __forceinline__ void tmem_ld7x8(uint32_t taddr, float (&v)[EX_NACC][8]) {
+    uint32_t r[EX_NACC][8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%56];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%57];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%58];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%59];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32,%33,%34,%35,%36,%37,%38,%39}, [%60];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40,%41,%42,%43,%44,%45,%46,%47}, [%61];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48,%49,%50,%51,%52,%53,%54,%55}, [%62];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]),
+          "=r"(r[0][6]), "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]),
+          "=r"(r[1][4]), "=r"(r[1][5]), "=r"(r[1][6]), "=r"(r[1][7]), "=r"(r[2][0]), "=r"(r[2][1]),
+          "=r"(r[2][2]), "=r"(r[2][3]), "=r"(r[2][4]), "=r"(r[2][5]), "=r"(r[2][6]), "=r"(r[2][7]),
+          "=r"(r[3][0]), "=r"(r[3][1]), "=r"(r[3][2]), "=r"(r[3][3]), "=r"(r[3][4]), "=r"(r[3][5]),
+          "=r"(r[3][6]), "=r"(r[3][7]), "=r"(r[4][0]), "=r"(r[4][1]), "=r"(r[4][2]), "=r"(r[4][3]),
+          "=r"(r[4][4]), "=r"(r[4][5]), "=r"(r[4][6]), "=r"(r[4][7]), "=r"(r[5][0]), "=r"(r[5][1]),
+          "=r"(r[5][2]), "=r"(r[5][3]), "=r"(r[5][4]), "=r"(r[5][5]), "=r"(r[5][6]), "=r"(r[5][7]),
+          "=r"(r[6][0]), "=r"(r[6][1]), "=r"(r[6][2]), "=r"(r[6][3]), "=r"(r[6][4]), "=r"(r[6][5]),
+          "=r"(r[6][6]), "=r"(r[6][7])
+        : "r"(taddr), "r"(taddr + EX_BN), "r"(taddr + 2 * EX_BN), "r"(taddr + 3 * EX_BN), "r"(taddr + 4 * EX_BN),
+          "r"(taddr + 5 * EX_BN), "r"(taddr + 6 * EX_BN)
+        : "memory");
+#pragma unroll
+    for (int a = 0; a < EX_NACC; ++a)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[a][e] = __uint_as_float(r[a][e]);
+}
+
+// Fixed-point slicing of one value v of a row with scale exponent e
+// (|v| 2^-e < 1/2): t = v 2^(8-e), a_s = rint(t), t = 256 (t - a_s), s = 0..NPL-1,
+// so |a_s| <= 128 and v = 2^(e-8) sum_s a_s 2^-8s + O(2^(e-65)).  Every step is
+// exact in T (float for an FP32 value, double for an FP64 one); slice s is
+// stored as the BF16 a_s 2^-8s (exact: |a_s| has at most 8 significant bits).
+template <typename T>
+__device__ __forceinline__ void slice_value(T v, int e, __nv_bfloat16* out) {
+    T t = (sizeof(T) == 8) ? (T)ldexp((double)v, 8 - e) : (T)ldexpf((float)v, 8 - e);
+    float w = 1.0f;
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+        const T a = rint(t);
+        out[s] = __float2bfloat16_rn((float)a * w);
+        t = (t - a) * (T)256;
+        w *= (1.0f / 256.0f);
+    }
+}
+
+// row scale exponent of a row whose largest magnitude (rounded to float) is m
+__device__ __forceinline__ int row_exponent(float m) {
+    int e = 0;
+    if (m > 0.0f) {
+        frexpf(m, &e);   // m < 2^e
+        e += 1;          // |v| 2^-e < 1/2
+    }
+    return e;
+}
+
+// 2^e as a double, exact for -1022 <= e <= 1023 (the range of two row scales)
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
 // 2^e as a float for e >= -126 (exact), 0 below: contributions that small are
 // beneath the FP32 resolution of any covariance entry they update.

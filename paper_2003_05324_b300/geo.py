@@ -31,6 +31,7 @@ GEO_LP_SPLIT_BF16 = 0
 GEO_LP_FP32 = 1
 GEO_FLAG_FP64_OFFBAND_GEN = 1
 GEO_FLAG_STEPWISE = 2
+GEO_FLAG_FP64_DMMA = 4
 
 
 class GeoError(RuntimeError):
@@ -62,7 +63,7 @@ class geo_tiles(ctypes.Structure):
     _fields_ = [("lay", geo_layout), ("d_dp", ctypes.c_void_p), ("d_sp", ctypes.c_void_p),
                 ("d_planes", ctypes.c_void_p), ("d_meta", ctypes.c_void_p),
                 ("aux_stream", ctypes.c_void_p), ("ev_fork", ctypes.c_void_p), ("ev_join", ctypes.c_void_p),
-                ("tmap", ctypes.c_uint64 * 32), ("flags", ctypes.c_int),
+                ("tmap", ctypes.c_uint64 * 48), ("flags", ctypes.c_int),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_longlong)]
 
 

@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_sizes_match_header():
     # geo_theta: 4 doubles; geo_tiles = layout + 7 pointers + 32 u64 + int flags (padded) + trace ptr/cap
     assert ctypes.sizeof(geo.geo_theta) == 32
-    assert ctypes.sizeof(geo.geo_tiles) == ctypes.sizeof(geo.geo_layout) + 7 * 8 + 256 + 8 + 16  # int+pad, trace
+    assert ctypes.sizeof(geo.geo_tiles) == ctypes.sizeof(geo.geo_layout) + 7 * 8 + 384 + 8 + 16  # int+pad, trace
 
 
 @pytest.mark.parametrize("n,nb,band", [(1600, 200, 8), (40000, 500, 1), (1000, 96, 2), (50, 64, 1), (1, 16, 1),
@@ -45,8 +45,8 @@ def test_layout_counts(n, nb, band):
     assert lay.bytes_dp >= ndp * nb * nb * 8
     assert lay.bytes_sp >= lay.n_sp_tiles * nb * nb * 4
     assert lay.pp % 64 == 0 and lay.pp >= nb
-    if lay.n_sp_tiles:
-        assert lay.bytes_planes >= 4 * lay.pp ** 2 * 2 * p * (p - 1) // 2
+    if p > 1:
+        assert lay.bytes_planes >= 7 * lay.pp ** 2 * 2 * p * (p - 1) // 2
     assert geo.layout(n, nb, band, geo.GEO_LP_FP32).bytes_planes == 0
 
 

@@ -95,17 +95,49 @@ def spd_matrix(n, seed, nu=0.5, beta=0.1, nugget=1e-3):
     return O.covariance(x, y, theta=O.Theta(1.0, beta, nu, nugget))
 
 
-@pytest.mark.parametrize("n,nb", [(640, 128), (700, 96), (500, 500), (37, 64)])
-def test_fp64_factor_matches_oracle(G, n, nb):
+@pytest.mark.parametrize("n,nb", [(640, 128), (700, 96), (500, 500), (37, 64), (1536, 512), (1500, 720)])
+@pytest.mark.parametrize("updates", ["fp64-pipe", "tensor"])
+def test_fp64_factor_matches_oracle(G, n, nb, updates):
+    # band = p: all tiles FP64.  "fp64-pipe": every update in FP64 FMA/DMMA;
+    # "tensor": the in-band updates as FP64-accurate slice products on the
+    # tensor cores (tile 512 and 720 take two and three 256-long parts).
     S = spd_matrix(n, seed=n)
     p = -(-n // nb)
-    ts = G.TileStore(n, nb, p, G.GEO_LP_FP32)   # band = p: all FP64
+    ts = G.TileStore(n, nb, p, G.GEO_LP_FP32 if updates == "fp64-pipe" else G.GEO_LP_SPLIT_BF16)
     ts.load_dense(dev(S.T))                      # column-major upload
     ts.potrf()
     got = ts.to_dense().cpu().numpy()
     Lo, info = O.dense_factor(S)
     assert info == 0
     assert np.max(np.abs(got - Lo)) <= 1e-12 * np.max(np.abs(Lo))
+
+
+@pytest.mark.parametrize("band", [1, 3])
+def test_tensor_fp64_updates_match_fp64_pipe(G, band):
+    # the same mixed-precision factorization with the in-band updates on the
+    # FP64 pipe and on the tensor cores: FP64-level agreement on every tile
+    n, nb = 1536, 256
+    S = spd_matrix(n, seed=9)
+    out = []
+    for flags in (G.GEO_FLAG_FP64_DMMA, 0):
+        ts = G.TileStore(n, nb, band, G.GEO_LP_SPLIT_BF16)
+        ts.set_flags(flags)
+        ts.load_dense(dev(S.T))
+        ts.potrf()
+        out.append(ts.to_dense().cpu().numpy())
+    Lmp, _ = O.mp_tile_cholesky(S, nb, band)
+    Ldp, _ = O.dense_factor(S)
+    mp_err = np.max(np.abs(Lmp - Ldp))
+    for got in out:
+        assert np.max(np.abs(got - Ldp)) <= 2.0 * mp_err
+    # the variants differ by FP64-level rounding in the in-band tiles (which
+    # can move an FP32 rounding of an off-band tile by one unit)
+    assert np.max(np.abs(out[0] - out[1])) <= 0.25 * mp_err
+    if band >= 3:
+        # tiles (1,1) and (2,1) are updated from FP64 panels (1,0), (2,0) only:
+        # FP64 parity through one tensor-core dsyrk / dgemm
+        sl = np.s_[nb:3 * nb, nb:2 * nb]
+        assert np.max(np.abs(out[1][sl] - Ldp[sl])) <= 1e-12 * np.max(np.abs(Ldp))
 
 
 @pytest.mark.parametrize("band,lp", [(1, "fp32"), (2, "fp32"), (1, "bf16"), (3, "bf16")])
@@ -271,12 +303,13 @@ def markov(x, z, s2, beta):
     return -0.5 * len(z) * math.log(2 * math.pi) - 0.5 * logdet - 0.5 * quad
 
 
-def test_loglik_markov_closed_form_fp64(G):
+@pytest.mark.parametrize("mode", ["fp64-pipe", "tensor"])
+def test_loglik_markov_closed_form_fp64(G, mode):
     n = 6000
     x, y = inputs.line_points(n, seed=7, min_gap=0.2)
     z = inputs.white_noise(n, seed=8)
     want = markov(x, z, 1.1, 0.002)
-    ts = G.TileStore(n, 500, 100, G.GEO_LP_FP32)
+    ts = G.TileStore(n, 500, 100, G.GEO_LP_FP32 if mode == "fp64-pipe" else G.GEO_LP_SPLIT_BF16)
     l, _, _ = ts.loglik(dev(x), dev(y), dev(z), G.Theta(1.1, 0.002, 0.5))
     assert abs(l - want) <= 1e-10 * abs(want)
 
