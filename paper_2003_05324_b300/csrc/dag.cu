@@ -64,7 +64,7 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     g.nsb64 = ceil_div(nb, 64);
     g.items64 = g.nsb64 * g.nsb64;
     g.items_tc = ceil_div(pp, TC_BM) * ceil_div(pp, TC_BN);
-    g.chunks_dp = ceil_div(nb, 32);
+    g.chunks_dp = ceil_div(nb, 128);
     g.chunks_sp = ceil_div(nb, 128);
     // counters: grab counters, upd[p*p], tcnt[p*p], pot[p*ns*ns], sub[p*p*maxitems]
     g.max_items = std::max(g.items64, g.items_tc);
@@ -136,7 +136,6 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
 
 // ----------------------------------------------------------- device side ---
 constexpr int G2_THREADS = 128;
-constexpr int G2_WARP0 = TC_THREADS / 32;   // 6
 constexpr int DAG_THREADS = TC_THREADS + G2_THREADS;
 constexpr long long DAG_WAIT_NS = 10000000000LL;   // 10 s per wait (legitimate waits are ms)
 constexpr int RING = 8;
@@ -238,10 +237,17 @@ struct G2Smem {
     int task, ok;
 };
 
-// PF(k,s): FP64 Cholesky of the 32 x 32 sub-block (s,s); warp 0 of the group.
+// PF(k,s): FP64 Cholesky of the 32 x 32 sub-block (s,s), right-looking in
+// shared memory with the whole group: per column c, every thread takes
+// r = 1/sqrt(d_cc); lane i scales row c+i of column c; then the trailing lower
+// triangle is updated with lanes over rows and the four warps over columns
+// (column j handled by warp j mod 4).  FP64 throughput per SM sub-partition is
+// tiny on this part, so spreading the updates over the four warps (and
+// replacing divisions by one reciprocal square root) shortens this task, which
+// is on the factorization's critical path.
 __device__ bool g2_pf(const DagArgs& A, G2Smem& S, int k, int s, int g) {
     const Layout& L = A.L;
-    const int nb = L.nb, c0 = s * 32, w = min(32, nb - c0), lane = g & 31;
+    const int nb = L.nb, c0 = s * 32, w = min(32, nb - c0), lane = g & 31, wp = g >> 5;
     double* T = dp_tile(L, k, k);
     double* D = S.pot.D;
     for (int idx = g; idx < w * w; idx += G2_THREADS) {
@@ -249,32 +255,28 @@ __device__ bool g2_pf(const DagArgs& A, G2Smem& S, int k, int s, int g) {
         D[r * 33 + c] = T[(size_t)(c0 + c) * nb + c0 + r];
     }
     g2_sync();
-    if (g == 0) S.ok = 1;
-    g2_sync();
-    if (g < 32) {
-        for (int c = 0; c < w; ++c) {
-            double d = D[c * 33 + c];
-            if (!(d > 0.0)) {
-                if (lane == 0) {
-                    S.ok = 0;
-                    if (atomicCAS(L.status + ST_CODE, 0, GEO_ERR_NOT_SPD) == 0) L.status[ST_INFO] = k * nb + c0 + c + 1;
-                }
-                break;
-            }
-            d = sqrt(d);
-            __syncwarp();
-            if (lane == c) D[c * 33 + c] = d;
-            if (lane > c && lane < w) D[lane * 33 + c] /= d;
-            __syncwarp();
-            if (lane > c && lane < w) {
-                const double lc = D[lane * 33 + c];
-                for (int j = c + 1; j <= lane; ++j) D[lane * 33 + j] -= lc * D[j * 33 + c];
-            }
-            __syncwarp();
+    bool ok = true;
+    for (int c = 0; c < w; ++c) {
+        const double d = D[c * 33 + c];
+        if (!(d > 0.0)) {   // the same d in every thread: all leave together
+            if (g == 0 && atomicCAS(L.status + ST_CODE, 0, GEO_ERR_NOT_SPD) == 0)
+                L.status[ST_INFO] = k * nb + c0 + c + 1;
+            ok = false;
+            break;
         }
+        const double rs = rsqrt(d);
+        g2_sync();   // everyone has read d before it is overwritten
+        if (g < w - c) D[(c + g) * 33 + c] = (g == 0) ? d * rs : D[(c + g) * 33 + c] * rs;
+        g2_sync();
+        const int i = c + 1 + lane;
+        if (i < w) {
+            const double li = D[i * 33 + c];
+            int j = c + 1 + ((wp - (c + 1)) & 3);
+            for (; j <= i; j += 4) D[i * 33 + j] = fma(-li, D[j * 33 + c], D[i * 33 + j]);
+        }
+        g2_sync();
     }
-    g2_sync();
-    if (!S.ok) return false;
+    if (!ok) return false;
     for (int idx = g; idx < w * w; idx += G2_THREADS) {
         const int r = idx % w, c = idx / w;
         if (r >= c) T[(size_t)(c0 + c) * nb + c0 + r] = D[r * 33 + c];
@@ -282,10 +284,13 @@ __device__ bool g2_pf(const DagArgs& A, G2Smem& S, int k, int s, int g) {
     return true;
 }
 
-// PT(k,r,s): X(r,s) <- X(r,s) L(s,s)^-T; thread per row (32 rows).
+// PT(k,r,s): X(r,s) <- X(r,s) L(s,s)^-T, right-looking over the 32 columns:
+// lane i scales row i of column c by 1/L_cc, then row i of the later columns
+// j > c is updated, the four warps taking the columns j = c+1.. in turn.
 __device__ void g2_pt(const DagArgs& A, G2Smem& S, int k, int r, int s, int g) {
     const Layout& L = A.L;
     const int nb = L.nb, c0 = s * 32, r0 = r * 32, w = min(32, nb - c0), h = min(32, nb - r0);
+    const int lane = g & 31, wp = g >> 5;
     double* T = dp_tile(L, k, k);
     double* D = S.pot.D;
     double* X = S.pot.X;
@@ -295,14 +300,19 @@ __device__ void g2_pt(const DagArgs& A, G2Smem& S, int k, int r, int s, int g) {
         X[a * 33 + b] = (a < h && b < w) ? T[(size_t)(c0 + b) * nb + r0 + a] : 0.0;
     }
     g2_sync();
-    if (g < h) {
-        for (int c = 0; c < w; ++c) {
-            double acc = X[g * 33 + c];
-            for (int t = 0; t < c; ++t) acc = fma(-X[g * 33 + t], D[c * 33 + t], acc);
-            X[g * 33 + c] = acc / D[c * 33 + c];
-        }
-    }
+    // reciprocal pivots in the (unused) upper triangle's first row slot: D[c*33 + 32]
+    if (g < w) D[g * 33 + 32] = 1.0 / D[g * 33 + g];
     g2_sync();
+    for (int c = 0; c < w; ++c) {
+        if (g < h) X[g * 33 + c] *= D[c * 33 + 32];
+        g2_sync();
+        if (lane < h) {
+            const double xc = X[lane * 33 + c];
+            for (int j = c + 1 + ((wp - (c + 1)) & 3); j < w; j += 4)
+                X[lane * 33 + j] = fma(-xc, D[j * 33 + c], X[lane * 33 + j]);
+        }
+        g2_sync();
+    }
     for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
         const int a = idx % 32, b = idx / 32;
         if (a < h && b < w) T[(size_t)(c0 + b) * nb + r0 + a] = X[a * 33 + b];
@@ -653,14 +663,15 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
             case T_TRSM: {
                 const int i = t.a, k = t.k, q = t.b;
                 const double* Lkk = dp_tile(L, k, k);
+                const int r = q * 128 + g;
                 if (is_dp(i, k, L.band)) {
                     double* X = dp_tile(L, i, k);
-                    const float m = g2_trsm_rows<double, 16>(Lkk, X, nb, q * 32, 32, g, S);
-                    if (L.planes && g < 32 && q * 32 + g < nb) g2_slice_row<double>(L, X, i, k, q * 32 + g, m);
+                    const float m = g2_trsm_rows<double, 16>(Lkk, X, nb, q * 128, 128, g, S);
+                    if (L.planes && r < nb) g2_slice_row<double>(L, X, i, k, r, m);
                 } else {
                     float* X = sp_tile(L, i, k);
                     const float m = g2_trsm_rows<float, 32>(Lkk, X, nb, q * 128, 128, g, S);
-                    if (L.planes && q * 128 + g < nb) g2_slice_row<float>(L, X, i, k, q * 128 + g, m);
+                    if (L.planes && r < nb) g2_slice_row<float>(L, X, i, k, r, m);
                 }
                 fence_proxy_async_global();   // the planes are read by TMA
                 done = A.tcnt + i * L.p + k;
