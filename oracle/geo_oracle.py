@@ -38,6 +38,13 @@ Function -> paper passage -> what pins it (tests/test_oracle_pins.py):
                                kriging reading                          observed points
   profile_sigma2               Eq. 3 and theta1_opt = Z'S~^-1 Z / n     argmax of Eq. 2
                                                                         over theta1
+  nelder_mead                  the MLE's optimizer (Section III-A: the  convex quadratic,
+                               paper uses NLopt with tolerance 1e-3;    Rosenbrock, 1D
+                               reading: Nelder & Mead 1965 simplex)     Markov MLE vs a
+                                                                        grid search
+  mle                          the estimator theta-hat maximising Eq. 2 1D Markov MLE vs
+                               (all three parameters, or Eq. 3's two    a grid search of
+                               with theta1 profiled)                    the closed form
 """
 from __future__ import annotations
 
@@ -51,7 +58,7 @@ import scipy.special as sps
 __all__ = [
     "morton_keys", "morton_order", "matern", "covariance", "loglik_dense",
     "dense_factor", "mp_tile_cholesky", "loglik_mp", "factor_logdet_quad",
-    "krige", "profile_sigma2", "Theta", "tile_is_dp",
+    "krige", "profile_sigma2", "Theta", "tile_is_dp", "nelder_mead", "mle", "profile_loglik",
 ]
 
 LOG_2PI = math.log(2.0 * math.pi)
@@ -293,3 +300,154 @@ def profile_sigma2(x, y, z, beta, nu, nugget_ratio=0.0):
     s2 = quad / n
     prof = -0.5 * n * LOG_2PI - 0.5 * n - 0.5 * n * math.log(s2) - 0.5 * logdet
     return s2, prof
+
+
+# ------------------------------------------------------ MLE (Section III-A) ---
+# The estimator theta-hat maximises Eq. 2.  The paper drives it with NLopt at an
+# optimisation tolerance of 1e-3 without naming the method; the reading here is
+# the Nelder-Mead simplex (Nelder & Mead, 1965) over log-parameters with the
+# classic coefficients (reflection 1, expansion 2, contraction 1/2, shrink 1/2),
+# box bounds by clamping, a fixed budget of objective evaluations and a
+# simplex-size stopping rule at the tolerance.
+NM_LO = (1e-3, 1e-4, 0.05)   # sigma2, beta, nu
+NM_HI = (1e2, 2.0, 3.0)
+
+
+def nelder_mead(f, u0, step=0.1, max_evals=60, xtol=1e-3, lo=None, hi=None):
+    """Minimise f over R^d from u0.
+
+    Simplex u0, u0 + step e_i.  Each iteration orders the vertices by f (ties:
+    the earlier position first), stops when every vertex is within xtol (max
+    norm) of the best, and replaces the worst by the reflection, expansion,
+    outside or inside contraction, or shrinks towards the best.  Trial points
+    are clamped to [lo, hi] before evaluation.  An evaluation is made only while
+    fewer than max_evals have been made; the best point evaluated is returned as
+    (u, f(u), evaluations, iterations).
+    """
+    d = len(u0)
+    lo = np.full(d, -np.inf) if lo is None else np.asarray(lo, dtype=np.float64)
+    hi = np.full(d, np.inf) if hi is None else np.asarray(hi, dtype=np.float64)
+    state = {"evals": 0, "best_u": None, "best_f": math.inf}
+
+    def clamp(u):
+        return np.minimum(np.maximum(np.asarray(u, dtype=np.float64), lo), hi)
+
+    def ev(u):
+        if state["evals"] >= max_evals:
+            return None
+        state["evals"] += 1
+        v = f(u)
+        v = v if (v is not None and math.isfinite(v)) else math.inf
+        if v < state["best_f"]:
+            state["best_f"], state["best_u"] = v, u.copy()
+        return v
+
+    verts, fv = [], []
+    for i in range(d + 1):
+        u = np.array(u0, dtype=np.float64)
+        if i > 0:
+            u[i - 1] += step
+        u = clamp(u)
+        v = ev(u)
+        if v is None:
+            break
+        verts.append(u)
+        fv.append(v)
+    iters = 0   # completed iterations
+    while len(verts) == d + 1:
+        order = sorted(range(d + 1), key=lambda q: (fv[q], q))
+        verts = [verts[q] for q in order]
+        fv = [fv[q] for q in order]
+        if max(np.max(np.abs(verts[q] - verts[0])) for q in range(1, d + 1)) <= xtol:
+            break
+        c = np.mean(verts[:d], axis=0)
+        worst = verts[d]
+        r = clamp(c + (c - worst))
+        fr = ev(r)
+        if fr is None:
+            break
+        if fr < fv[0]:
+            e = clamp(c + 2.0 * (c - worst))
+            fe = ev(e)
+            if fe is None:
+                break
+            verts[d], fv[d] = (e, fe) if fe < fr else (r, fr)
+            iters += 1
+            continue
+        if fr < fv[d - 1]:
+            verts[d], fv[d] = r, fr
+            iters += 1
+            continue
+        if fr < fv[d]:
+            oc = clamp(c + 0.5 * (r - c))
+            fo = ev(oc)
+            if fo is None:
+                break
+            if fo <= fr:
+                verts[d], fv[d] = oc, fo
+                iters += 1
+                continue
+        else:
+            ic = clamp(c + 0.5 * (worst - c))
+            fi = ev(ic)
+            if fi is None:
+                break
+            if fi < fv[d]:
+                verts[d], fv[d] = ic, fi
+                iters += 1
+                continue
+        for q in range(1, d + 1):          # shrink towards the best vertex
+            verts[q] = clamp(verts[0] + 0.5 * (verts[q] - verts[0]))
+            v = ev(verts[q])
+            if v is None:
+                verts = verts[:q]          # out of budget mid-shrink
+                break
+            fv[q] = v
+        else:
+            iters += 1
+    return state["best_u"], state["best_f"], state["evals"], iters
+
+
+def profile_loglik(n, logdet, quad):
+    """Eq. 3 at theta1 = quad / n (reading R9): -n/2 log 2pi - n/2 - n/2 log(quad/n) - 1/2 logdet."""
+    return -0.5 * n * LOG_2PI - 0.5 * n - 0.5 * n * math.log(quad / n) - 0.5 * logdet
+
+
+def mle(x, y, z, theta0: Theta, max_evals=60, xtol=1e-3, profile=False, fix_nu=False, evaluate=None):
+    """theta-hat maximising Eq. 2 (profile=False: over log sigma2, log beta,
+    log nu) or Eq. 3 (profile=True: over log beta, log nu, with theta1 = Q/n and
+    the nugget taken relative to theta1).  fix_nu keeps nu at theta0.nu.
+    evaluate(theta) -> (logdet, quad) of Sigma(theta), or None when it is not
+    positive definite (default: the dense FP64 definition).  Returns
+    dict(theta, loglik, evals, iterations)."""
+    n = len(z)
+    if evaluate is None:
+        def evaluate(th):
+            L, info = dense_factor(covariance(x, y, theta=th))
+            return None if info != 0 else factor_logdet_quad(L, z)
+    names = ([] if profile else [0]) + [1] + ([] if fix_nu else [2])
+    base = [theta0.sigma2, theta0.beta, theta0.nu]
+    lo = [math.log(NM_LO[q]) for q in names]
+    hi = [math.log(NM_HI[q]) for q in names]
+
+    def unpack(u):
+        t = list(base)
+        for q, v in zip(names, u):
+            t[q] = math.exp(v)
+        return t
+
+    def objective(u):
+        t = unpack(u)
+        r = evaluate(Theta(1.0 if profile else t[0], t[1], t[2], theta0.nugget))
+        if r is None:
+            return math.inf
+        logdet, quad = r
+        return -(profile_loglik(n, logdet, quad) if profile else _assemble(n, logdet, quad))
+
+    u0 = [math.log(base[q]) for q in names]
+    ub, fb, evals, iters = nelder_mead(objective, u0, max_evals=max_evals, xtol=xtol, lo=lo, hi=hi)
+    t = unpack(ub)
+    if profile:
+        logdet, quad = evaluate(Theta(1.0, t[1], t[2], theta0.nugget))
+        t[0] = quad / n
+    return dict(theta=Theta(t[0], t[1], t[2], theta0.nugget), loglik=-fb, evals=evals, iterations=iters)

@@ -311,3 +311,115 @@ def test_krige_far_point_predicts_zero_mean():
     th = O.Theta(1.0, 0.01, 0.5, 0.0)
     zhat = O.krige(x, y, z, th, np.array([50.0]), np.array([50.0]))
     assert zhat[0] == 0.0
+
+
+# ------------------------------------------- MLE: the Nelder-Mead simplex ---
+def test_nelder_mead_convex_quadratic():
+    a = np.array([0.7, -1.3, 2.1])
+    w = np.array([1.0, 4.0, 0.25])
+    u, f, evals, iters = O.nelder_mead(lambda u: float(np.sum(w * (u - a) ** 2)), [0.0, 0.0, 0.0],
+                                       step=0.5, max_evals=2000, xtol=1e-10)
+    assert np.max(np.abs(u - a)) <= 1e-6 and f <= 1e-11 and evals <= 2000 and iters > 0
+
+
+def test_nelder_mead_rosenbrock():
+    def rosen(u):
+        return float(100.0 * (u[1] - u[0] ** 2) ** 2 + (1.0 - u[0]) ** 2)
+    u, f, evals, _ = O.nelder_mead(rosen, [-1.2, 1.0], step=0.5, max_evals=5000, xtol=1e-12)
+    assert np.max(np.abs(u - 1.0)) <= 1e-5 and f <= 1e-10
+
+
+def test_nelder_mead_bounds_and_budget():
+    # the unconstrained minimum (3, -3) lies outside the box: the result is its corner
+    calls = []
+    def f(u):
+        calls.append(u.copy())
+        return float((u[0] - 3.0) ** 2 + (u[1] + 3.0) ** 2)
+    u, _, evals, _ = O.nelder_mead(f, [0.0, 0.0], step=0.3, max_evals=400, xtol=1e-9, lo=[-1, -1], hi=[1, 1])
+    assert np.allclose(u, [1.0, -1.0], atol=1e-7)
+    assert all(np.all(c >= -1) and np.all(c <= 1) for c in calls)
+    # a budget is never exceeded, and the best point seen is returned
+    calls.clear()
+    u, fb, evals, _ = O.nelder_mead(f, [0.0, 0.0], step=0.3, max_evals=7)
+    assert evals == len(calls) == 7 and fb == min(f(c) for c in calls[:7])
+
+
+def _ar1_field(x, sigma2, beta, seed):
+    # exact simulation of the nu = 1/2 (exponential) process on sorted 1D points
+    w = inputs.white_noise(len(x), seed)
+    z = np.empty(len(x))
+    z[0] = math.sqrt(sigma2) * w[0]
+    rho = np.exp(-np.diff(x) / beta)
+    for i in range(1, len(x)):
+        z[i] = rho[i - 1] * z[i - 1] + math.sqrt(sigma2 * (1.0 - rho[i - 1] ** 2)) * w[i]
+    return z
+
+
+def _markov_argmax(x, z):
+    # theta-hat of the 1D Markov likelihood without any simplex: for fixed beta
+    # the maximising sigma2 is Q_1(beta)/n, and the profile in log beta is
+    # maximised by a grid search refined with bounded Brent.
+    from scipy.optimize import minimize_scalar
+    n = len(z)
+    def neg_profile(lb):
+        _, ld1, q1 = _markov_loglik(x, z, 1.0, math.exp(lb))
+        return -(-0.5 * n * math.log(2 * math.pi) - 0.5 * n - 0.5 * n * math.log(q1 / n) - 0.5 * ld1)
+    grid = np.linspace(math.log(1e-4), math.log(2.0), 400)
+    vals = [neg_profile(g) for g in grid]
+    j = int(np.argmin(vals))
+    res = minimize_scalar(neg_profile, bounds=(grid[max(j - 1, 0)], grid[min(j + 1, len(grid) - 1)]),
+                          method="bounded", options={"xatol": 1e-12})
+    beta = math.exp(res.x)
+    _, _, q1 = _markov_loglik(x, z, 1.0, beta)
+    return q1 / n, beta
+
+
+@pytest.mark.parametrize("profile", [False, True])
+def test_mle_markov_1d_matches_closed_form_argmax(profile):
+    n = 2000
+    x, y = inputs.line_points(n, seed=21, min_gap=0.02)
+    z = _ar1_field(x, 1.3, 0.08, seed=22)
+    s2_hat, b_hat = _markov_argmax(x, z)
+    def evaluate(th):
+        _, ld, q = _markov_loglik(x, z, th.sigma2, th.beta)
+        return ld, q
+    res = O.mle(x, y, z, O.Theta(0.5, 0.05, 0.5), max_evals=400, xtol=1e-9, profile=profile, fix_nu=True,
+                evaluate=evaluate)
+    assert abs(res["theta"].beta - b_hat) <= 1e-6 * b_hat
+    assert abs(res["theta"].sigma2 - s2_hat) <= 1e-6 * s2_hat
+
+
+def test_mle_dense_objective_follows_the_same_path():
+    # the dense definition of Eq. 2 and the Markov closed form agree to ~1e-12,
+    # so the simplex takes the same steps with either objective
+    n = 240
+    x, y = inputs.line_points(n, seed=23, min_gap=0.02)
+    z = _ar1_field(x, 0.9, 0.1, seed=24)
+    def markov(th):
+        _, ld, q = _markov_loglik(x, z, th.sigma2, th.beta)
+        return ld, q
+    th0 = O.Theta(0.5, 0.05, 0.5)
+    a = O.mle(x, y, z, th0, max_evals=60, fix_nu=True)
+    b = O.mle(x, y, z, th0, max_evals=60, fix_nu=True, evaluate=markov)
+    assert a["evals"] == b["evals"] and a["iterations"] == b["iterations"]
+    assert abs(a["theta"].beta - b["theta"].beta) <= 1e-9 * b["theta"].beta
+    assert abs(a["theta"].sigma2 - b["theta"].sigma2) <= 1e-9 * b["theta"].sigma2
+
+
+def test_nelder_mead_hand_traced_steps():
+    # f = u0^2 + 2 u1^2 from (1, 1), step 0.5 (worked by hand):
+    # simplex (1,1) 3, (1.5,1) 4.25, (1,1.5) 5.5; centroid (1.25,1);
+    # reflection (1.5,0.5) 2.75 beats the best, expansion (1.75,0) 3.0625 does
+    # not beat it -> keep the reflection.  Next: centroid of (1.5,.5),(1,1) is
+    # (1.25,.75), worst (1.5,1): reflection (1,.5) 1.5, expansion (.75,.25)
+    # 0.6875 -> keep the expansion.  Seven evaluations.
+    u, f, evals, iters = O.nelder_mead(lambda u: float(u[0] ** 2 + 2 * u[1] ** 2), [1.0, 1.0], step=0.5,
+                                       max_evals=7)
+    assert evals == 7 and iters == 2
+    assert np.allclose(u, [0.75, 0.25], rtol=0, atol=1e-15) and abs(f - 0.6875) <= 1e-15
+    # 1D, f = u^2 from 0.2, step 1: simplex 0.2 (.04), 1.2 (1.44); reflection
+    # -0.8 (.64) -> outside contraction -0.3 (.09), accepted; then reflection
+    # 0.7 (.49) is worse than the worst -> inside contraction -0.05 (.0025).
+    u, f, evals, iters = O.nelder_mead(lambda u: float(u[0] ** 2), [0.2], step=1.0, max_evals=6)
+    assert evals == 6 and iters == 2
+    assert abs(u[0] + 0.05) <= 1e-15 and abs(f - 0.0025) <= 1e-16
