@@ -103,7 +103,8 @@ typedef struct geo_trace_rec {
 /* Generation option: compute off-band (FP32-stored) covariance entries in FP64
  * and round them to FP32 (Algorithm 1's dlag2s of the FP64 value) instead of
  * computing them in compensated FP32 arithmetic (the default, ~8x fewer FP64
- * operations; entries within (4x+8) 2^-24 relative, x = r/theta2). */
+ * operations; entries within 8 2^-24 relative for nu in {1/2, 3/2, 5/2} and
+ * (16 + 4 nu |ln x|) 2^-24 otherwise, x = r/theta2). */
 #define GEO_FLAG_FP64_OFFBAND_GEN 1
 /* Scheduling option (tensor-core mode only): run Algorithm 1 as host-sequenced
  * outer steps (per step: potrf, trsm, slicing, then the FP64 and tensor-core
@@ -207,6 +208,46 @@ int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream);
  * Returns GEO_OK, GEO_ERR_NOT_SPD (with *h_info set, h_out undefined), or an error. */
 int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z,
                geo_theta theta, double* h_out, int* h_info, void* stream);
+
+/* Maximum likelihood estimation (Section III-A).  theta-hat maximises Eq. 2
+ * over (sigma2, beta, nu), or, with profile = 1, Eq. 3 over (beta, nu) with
+ * theta1 = Z' S~^-1 Z / n (S~ the covariance at unit variance, the nugget taken
+ * relative to theta1).  The paper drives this with NLopt at tolerance 1e-3
+ * without naming the method; the reading here is the Nelder-Mead simplex
+ * (Nelder & Mead 1965) over the logarithms of the free parameters:
+ * simplex theta0 and theta0 * e^step in each free parameter; each iteration
+ * orders the vertices by -l (ties: the earlier position first), stops when
+ * every vertex is within xtol of the best (max norm), and replaces the worst
+ * by the reflection (coefficient 1), expansion (2), outside or inside
+ * contraction (1/2) or shrinks towards the best (1/2); trial points are
+ * clamped to [lo, hi]; an evaluation that is not positive definite counts as
+ * l = -inf.  At most max_evals likelihood evaluations (each a full A2-A12
+ * pass on t, blocking), and the best point evaluated is returned. */
+typedef struct geo_mle_opts {
+    int max_evals;        /* evaluation budget (default 60) */
+    int profile;          /* 0: Eq. 2 over 3 parameters; 1: Eq. 3 over (beta, nu) */
+    int fix_nu;           /* 1: nu stays at theta0.nu */
+    double xtol;          /* simplex-size stop in log-parameter space (default 1e-3) */
+    double step;          /* initial simplex step in log space (default 0.1) */
+    double lo[3], hi[3];  /* box on (sigma2, beta, nu) (defaults [1e-3,1e2], [1e-4,2], [0.05,3]) */
+} geo_mle_opts;
+
+typedef struct geo_mle_result {
+    geo_theta theta;      /* theta-hat (nugget as given in theta0) */
+    double loglik;        /* l at theta-hat: Eq. 2, or Eq. 3 with profile = 1 */
+    int evals;            /* likelihood evaluations made */
+    int iterations;       /* completed simplex iterations */
+    int not_spd;          /* evaluations that were not positive definite */
+} geo_mle_result;
+
+/* Fill *o with the defaults above.  Returns 0, or -1 for NULL. */
+int geo_mle_default_opts(geo_mle_opts* o);
+/* Run the estimator on the bound store t (its layout fixes n, nb, band and
+ * the arithmetic).  Locations and Z are caller-owned device arrays.  Returns
+ * GEO_OK with *out filled, -k for a bad argument k, or the first error other
+ * than GEO_ERR_NOT_SPD that an evaluation returned. */
+int geo_mle(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta0,
+            const geo_mle_opts* opts, geo_mle_result* out, void* stream);
 
 /* A13, prediction (Section VI-B; simple kriging reading): with t holding the
  * factor of Sigma(theta) over the observed locations (d_x, d_y, n = t->lay.n)

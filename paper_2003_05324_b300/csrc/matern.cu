@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
     __syncthreads();
     const bool dp = is_dp(i, j, L.band);
     const float s2f = (float)mp.sigma2, nuf = (float)mp.nu, lcf = (float)mp.log_c;
+    const float lcl = (float)(mp.log_c - (double)lcf), s2l = (float)(mp.sigma2 - (double)s2f);
     for (int a = threadIdx.x; a < nb; a += GEN_THREADS) {
         const int ga = i * nb + a;
         const bool va = ga < L.n;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
                     if (xh == 0.0f) v = s2f;
                     else {
                         const float xl = (fmaf(-xh, xh, r2h) + r2l) / (2.0f * xh);
-                        v = matern_fp32(xh, xl, mp, s2f, nuf, lcf);
+                        v = matern_fp32(xh, xl, mp, s2f, s2l, nuf, lcf, lcl);
                     }
                 }
                 T[(size_t)(c0 + c) * nb + a] = v;

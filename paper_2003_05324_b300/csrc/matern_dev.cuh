@@ -69,22 +69,45 @@ __device__ __forceinline__ double matern_fp64(double x, const MaternP& m) {
     }
 }
 
+// Exact sum of two floats: s + e = a + b (Knuth's TwoSum).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+    const float s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+    return s;
+}
+
 // FP32 entry from x = xh + xl (xl the low part of r/beta): the closed forms use
 // e^{-x} = e^{-xh} (1 - xl), so the error of the argument does not grow with x.
-__device__ __forceinline__ float matern_fp32(float xh, float xl, const MaternP& m, float s2, float nu,
-                                             float log_c) {
-    const float e = expf(-xh) * (1.0f - xl);
+// The general-nu form sigma2 x^nu e^-x / (2^(nu-1) Gamma(nu)) * [e^x K_nu(x)]
+// takes its first factor as exp(A) (1 + dA): A = nu log xh - xh - log_c in
+// float, dA the exact rounding errors of that sum (two-product, TwoSum) plus
+// the first-order effect of xl and of log_c's low part, so the exponent's
+// rounding (~x u) does not enter the entry's error.  sigma2 enters as
+// s2 + s2_lo (its float rounding would otherwise scale every entry alike).
+__device__ __forceinline__ float matern_fp32(float xh, float xl, const MaternP& m, float s2, float s2_lo,
+                                             float nu, float log_c, float log_c_lo) {
+    float q;
     switch (m.kind) {
-        case 1: return s2 * e;
-        case 2: return s2 * ((1.0f + xh) + xl) * e;
+        case 1: q = expf(-xh) * (1.0f - xl); break;
+        case 2: q = ((1.0f + xh) + xl) * (expf(-xh) * (1.0f - xl)); break;
         case 3: {
             const float x = xh + xl;
-            return s2 * (1.0f + x + x * x * (1.0f / 3.0f)) * e;
+            q = (1.0f + x + x * x * (1.0f / 3.0f)) * (expf(-xh) * (1.0f - xl));
+            break;
         }
-        default:
+        default: {
             if (xh > 110.0f) return 0.0f;
-            return s2 * expf(nu * logf(xh) - xh - log_c) * (1.0f - xl + nu * xl / xh) * ekv_fp32(nu, xh);
+            const float lg = logf(xh);
+            const float pr = __fmul_rn(nu, lg), pe = fmaf(nu, lg, -pr);   // pr + pe = nu * lg exactly
+            float e1, e2;
+            const float a1 = two_sum(pr, -xh, e1);
+            const float a2 = two_sum(a1, -log_c, e2);
+            const float dA = ((pe + e1) + e2) - log_c_lo - xl + nu * xl / xh;
+            q = expf(a2) * (1.0f + dA) * ekv_fp32(nu, xh);
+        }
     }
+    return fmaf(s2, q, s2_lo * q);
 }
 
 }  // namespace geo

@@ -67,6 +67,17 @@ class geo_tiles(ctypes.Structure):
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_longlong)]
 
 
+class geo_mle_opts(ctypes.Structure):
+    _fields_ = [("max_evals", ctypes.c_int), ("profile", ctypes.c_int), ("fix_nu", ctypes.c_int),
+                ("xtol", ctypes.c_double), ("step", ctypes.c_double),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class geo_mle_result(ctypes.Structure):
+    _fields_ = [("theta", geo_theta), ("loglik", ctypes.c_double), ("evals", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("not_spd", ctypes.c_int)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libgeo.so not built at {LIB_PATH}; run paper_2003_05324_b300/build.py")
@@ -88,6 +99,9 @@ def _load():
         "geo_status": [ctypes.POINTER(geo_tiles), ctypes.POINTER(I), ctypes.POINTER(I), P],
         "geo_loglik": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, ctypes.POINTER(D), ctypes.POINTER(I), P],
         "geo_krige": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, P, P, I, P, P, P],
+        "geo_mle_default_opts": [ctypes.POINTER(geo_mle_opts)],
+        "geo_mle": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, ctypes.POINTER(geo_mle_opts),
+                    ctypes.POINTER(geo_mle_result), P],
     }
     sig.update({
         "geo_profile_enable": [I],
@@ -270,6 +284,27 @@ class TileStore:
         _check(rc, "geo_loglik", info.value)
         return out[0], out[1], out[2]
 
+    def mle(self, x, y, z, theta0: Theta, max_evals: int = 60, profile: bool = False, fix_nu: bool = False,
+            xtol: float = 1e-3, step: float = 0.1, lo=None, hi=None, stream=None) -> dict:
+        """Maximum likelihood estimate (Nelder-Mead over log-parameters, see geo_mle)
+        with every likelihood evaluation on this store.  Returns dict(theta,
+        loglik, evals, iterations, not_spd)."""
+        o = geo_mle_opts()
+        _check(lib.geo_mle_default_opts(ctypes.byref(o)), "geo_mle_default_opts")
+        o.max_evals, o.profile, o.fix_nu = int(max_evals), int(bool(profile)), int(bool(fix_nu))
+        o.xtol, o.step = float(xtol), float(step)
+        if lo is not None:
+            for a in range(3):
+                o.lo[a] = float(lo[a])
+        if hi is not None:
+            for a in range(3):
+                o.hi[a] = float(hi[a])
+        r = geo_mle_result()
+        _check(lib.geo_mle(ctypes.byref(self.t), _ptr(x), _ptr(y), _ptr(z), theta0.c(), ctypes.byref(o),
+                           ctypes.byref(r), _stream(stream)), "geo_mle")
+        th = Theta(r.theta.sigma2, r.theta.beta, r.theta.nu, r.theta.nugget)
+        return dict(theta=th, loglik=r.loglik, evals=r.evals, iterations=r.iterations, not_spd=r.not_spd)
+
     def krige(self, x, y, z, theta: Theta, xnew, ynew, stream=None):
         """Simple-kriging prediction at (xnew, ynew) from the factored store."""
         import torch
@@ -310,3 +345,12 @@ def loglik_flops(n: int) -> float:
     return n ** 3 / 3.0
 
 
+
+
+def mle(x, y, z, theta0: Theta, nb: int, band: int, lp_mode: int = GEO_LP_SPLIT_BF16, flags: int = 0, **kw):
+    """geo.mle(x, y, z, theta0, nb, band, ...): the estimator on a fresh tile store
+    (x, y, z: Morton-ordered device tensors; keywords as TileStore.mle)."""
+    ts = TileStore(int(z.shape[0]), nb, band, lp_mode, device=z.device)
+    if flags:
+        ts.set_flags(flags)
+    return ts.mle(x, y, z, theta0, **kw)

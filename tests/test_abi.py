@@ -72,6 +72,30 @@ def test_entry_points_reject_null_arguments_without_device_work():
     assert L.geo_krige(None, None, None, None, th, None, None, 0, None, None, None) == -1
     assert L.geo_tiles_bind(None, None, None, None, None, None, None) == -1
     assert L.geo_morton_order(None, None, 3, None) == -1
+    assert L.geo_mle(None, None, None, None, th, None, None, None) == -1
+    assert L.geo_mle_default_opts(None) == -1
+
+
+def test_mle_options_defaults_and_validation():
+    o = geo.geo_mle_opts()
+    assert geo.lib.geo_mle_default_opts(ctypes.byref(o)) == 0
+    assert (o.max_evals, o.profile, o.fix_nu) == (60, 0, 0)
+    assert o.xtol == 1e-3 and o.step == 0.1
+    assert list(o.lo) == [1e-3, 1e-4, 0.05] and list(o.hi) == [1e2, 2.0, 3.0]
+    assert ctypes.sizeof(geo.geo_mle_opts) == 80 and ctypes.sizeof(geo.geo_mle_result) == 56
+    t = geo.geo_tiles()
+    th = geo.Theta(1.0, 0.1, 0.5).c()
+    r = geo.geo_mle_result()
+    d = ctypes.c_void_p(8)   # never dereferenced: validation fails first
+    bad = geo.geo_mle_opts()
+    geo.lib.geo_mle_default_opts(ctypes.byref(bad))
+    bad.max_evals = 0
+    assert geo.lib.geo_mle(ctypes.byref(t), d, d, d, th, ctypes.byref(bad), ctypes.byref(r), None) == -6
+    bad.max_evals, bad.lo[1] = 60, 0.0
+    assert geo.lib.geo_mle(ctypes.byref(t), d, d, d, th, ctypes.byref(bad), ctypes.byref(r), None) == -6
+    assert geo.lib.geo_mle(ctypes.byref(t), d, d, d, geo.Theta(-1.0, 0.1, 0.5).c(), ctypes.byref(o),
+                           ctypes.byref(r), None) == -5
+    assert geo.lib.geo_mle(ctypes.byref(t), d, d, d, th, ctypes.byref(o), None, None) == -7
 
 
 @pytest.mark.parametrize("seed", [0, 1])
