@@ -249,6 +249,38 @@ int geo_mle_default_opts(geo_mle_opts* o);
 int geo_mle(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta0,
             const geo_mle_opts* opts, geo_mle_result* out, void* stream);
 
+/* Batched evaluation: many problems of their own n, tile size, band and theta
+ * through one persistent factorization launch (the tasks of all problems share
+ * the device-side queues, merged step by step, each problem keeping its own
+ * dependency order).  Each item is a bound store with its Morton-ordered
+ * locations and Z (device arrays).  Per problem the arithmetic is that of
+ * geo_loglik, operation for operation, so a problem's result is the same
+ * alone and in any batch.
+ *
+ * geo_batch_workspace: bytes of device workspace for these items (host only).
+ * geo_batch_bind: write the merged task queues, the per-problem views and
+ *   tensor maps into d_work (blocking).  The stores' flags are read here.
+ * geo_loglik_batch: enqueue one evaluation (asynchronous, nprob + 2 kernel
+ *   launches, no host synchronization, so it can be captured in a CUDA graph):
+ *   generation of every problem from d_theta[b] (device memory: a replay of a
+ *   captured graph may use new values), the batched factorization, and the
+ *   batched log-det / solve / assembly into d_out[3b .. 3b+2] = (l, log|Sigma|,
+ *   Z' Sigma^-1 Z); NaN for a problem that is not positive definite (its
+ *   store's status says which row).  A launch-wide timeout marks every problem
+ *   with GEO_ERR_TIMEOUT.
+ * All return 0, -k for a bad argument k, or GEO_ERR_CUDA. */
+typedef struct geo_batch_item {
+    geo_tiles* t;
+    const double* d_x;
+    const double* d_y;
+    const double* d_z;
+} geo_batch_item;
+
+int geo_batch_workspace(int nprob, const geo_batch_item* items, size_t* bytes);
+int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t bytes, void* stream);
+int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_theta, void* d_work,
+                     double* d_out, void* stream);
+
 /* A13, prediction (Section VI-B; simple kriging reading): with t holding the
  * factor of Sigma(theta) over the observed locations (d_x, d_y, n = t->lay.n)
  * and observations d_z, write d_zhat[m] = Sigma_new,obs Sigma^-1 Z for the m

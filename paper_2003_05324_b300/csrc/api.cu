@@ -317,7 +317,7 @@ int geo_matern_tiles(geo_tiles* t, const double* d_x, const double* d_y, geo_the
     if (!d_y) return -3;
     if (check_theta(theta)) return -4;
     Layout L = make_layout(t);
-    return launch_matern_tiles(L, d_x, d_y, make_matern(theta), (cudaStream_t)stream) ? GEO_ERR_CUDA : GEO_OK;
+    return launch_matern_tiles(L, d_x, d_y, theta, nullptr, 0, (cudaStream_t)stream) ? GEO_ERR_CUDA : GEO_OK;
 }
 
 int geo_tiles_load_dense(geo_tiles* t, const double* d_a, void* stream) {
@@ -414,7 +414,7 @@ int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double*
     cudaStream_t s = (cudaStream_t)stream;
     int rc = reset_status(L, s);
     if (rc) return rc;
-    if (launch_matern_tiles(L, d_x, d_y, make_matern(theta), s)) return GEO_ERR_CUDA;
+    if (launch_matern_tiles(L, d_x, d_y, theta, nullptr, 0, s)) return GEO_ERR_CUDA;
     if (factor(t, L, s)) return GEO_ERR_CUDA;
     double* res = L.scal + 2 * L.p;
     if (run_logdet_trsv(L, d_z, res, res + 1, nullptr, s)) return GEO_ERR_CUDA;
@@ -426,8 +426,7 @@ int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double*
     if (e) return GEO_ERR_CUDA;
     if (h_info) *h_info = st[1];
     if (st[0] != 0) return st[0];
-    const double n = (double)L.n;
-    h_out[0] = -0.5 * n * log(2.0 * M_PI) - 0.5 * hres[0] - 0.5 * hres[1];
+    h_out[0] = assemble_loglik(L.n, hres[0], hres[1]);
     h_out[1] = hres[0];
     h_out[2] = hres[1];
     return GEO_OK;
@@ -474,6 +473,179 @@ int geo_profile_read(int kind, double* h_ms, long long* h_launches) {
     prof_collect(g_slots[kind]);
     *h_ms = g_slots[kind].ms;
     if (h_launches) *h_launches = g_slots[kind].launches;
+    return GEO_OK;
+}
+
+}  // extern "C"
+
+// ---- batched evaluation ------------------------------------------------------
+namespace {
+struct BatchMeta {
+    int nprob;
+    size_t off_probs, off_jobs, off_maps, off_tend, off_prio, off_bulk, off_tct, off_ctr, total;
+    long long n_prio, n_bulk, n_tct;
+    int per;
+    size_t counter_bytes;
+};
+std::mutex g_batch_mu;
+std::vector<std::pair<const void*, BatchMeta>> g_batches;   // bound workspaces
+
+int batch_variant(const geo_tiles* t) {
+    return ((t->flags & GEO_FLAG_FP64_DMMA) || !t->d_planes || t->lay.bytes_planes == 0) ? 1 : 0;
+}
+
+int batch_meta(int nprob, const geo_batch_item* items, BatchMeta& m, std::vector<SchedGeom>* geoms) {
+    if (nprob < 1) return -1;
+    if (!items) return -2;
+    m = BatchMeta();
+    m.nprob = nprob;
+    long long ptot = 0, ctot = 16;
+    m.n_prio = m.n_bulk = m.n_tct = 0;
+    m.per = 1;
+    for (int b = 0; b < nprob; ++b) {
+        const geo_batch_item& it = items[b];
+        if (!it.t || !it.t->d_meta || !it.d_x || !it.d_y || !it.d_z) return -2;
+        if (it.t->lay.lp_mode != GEO_LP_SPLIT_BF16) return -2;   // the batch runs the tensor-core DAG path
+        const MetaOffsets mo = meta_offsets(it.t->lay);
+        const SchedGeom& g = mo.geom[batch_variant(it.t)];
+        if (geoms) geoms->push_back(g);
+        ptot += g.p;
+        ctot += g.n_counters - 16;
+        m.n_prio += g.n_prio;
+        m.n_bulk += g.n_bulk;
+        m.n_tct += g.n_tct;
+        m.per = std::max(m.per, g.items_tc);
+    }
+    size_t b = 0;
+    m.off_probs = b;
+    b = align256(b + sizeof(ProbDev) * (size_t)nprob);
+    m.off_jobs = b;
+    b = align256(b + sizeof(SolveJob) * (size_t)nprob);
+    m.off_maps = b;
+    b = align256(b + sizeof(CUtensorMap) * 3 * (size_t)nprob);
+    m.off_tend = b;
+    b = align256(b + sizeof(int) * (size_t)ptot);
+    m.off_prio = b;
+    b = align256(b + sizeof(G2Task) * (size_t)std::max(m.n_prio, 1LL));
+    m.off_bulk = b;
+    b = align256(b + sizeof(G2Task) * (size_t)std::max(m.n_bulk, 1LL));
+    m.off_tct = b;
+    b = align256(b + sizeof(int4) * (size_t)std::max(m.n_tct, 1LL));
+    m.off_ctr = b;
+    m.counter_bytes = sizeof(int) * (size_t)ctot;
+    b = align256(b + m.counter_bytes);
+    m.total = b;
+    return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int geo_batch_workspace(int nprob, const geo_batch_item* items, size_t* bytes) {
+    if (!bytes) return -3;
+    BatchMeta m;
+    const int rc = batch_meta(nprob, items, m, nullptr);
+    if (rc) return rc;
+    *bytes = m.total;
+    return GEO_OK;
+}
+
+int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t bytes, void* stream) {
+    BatchMeta m;
+    std::vector<SchedGeom> geoms;
+    int rc = batch_meta(nprob, items, m, &geoms);
+    if (rc) return rc;
+    if (!d_work) return -3;
+    if (bytes < m.total) return -4;
+    std::vector<int> bands((size_t)nprob);
+    for (int b = 0; b < nprob; ++b) bands[(size_t)b] = items[b].t->lay.band;
+    BatchPlan plan;
+    sched_merge(geoms, bands, plan);
+    if ((long long)plan.prio.size() != m.n_prio || (long long)plan.bulk.size() != m.n_bulk ||
+        (long long)plan.tct.size() != m.n_tct || plan.per != m.per)
+        return GEO_ERR_UNSUPPORTED;   // the merge must account for every task
+    char* base = (char*)d_work;
+    std::vector<ProbDev> probs((size_t)nprob);
+    std::vector<SolveJob> jobs((size_t)nprob);
+    std::vector<CUtensorMap> maps(3 * (size_t)nprob);
+    std::vector<int> tend;
+    int* ctr = (int*)(base + m.off_ctr) + 16;
+    for (int b = 0; b < nprob; ++b) {
+        const geo_tiles* t = items[b].t;
+        ProbDev& P = probs[(size_t)b];
+        memset(&P, 0, sizeof(P));
+        P.L = make_layout(t);
+        P.g = geoms[(size_t)b];
+        bind_counters(P, ctr);
+        ctr += P.g.n_counters - 16;
+        P.trsm_end = (const int*)(base + m.off_tend) + tend.size();
+        tend.insert(tend.end(), plan.trsm_end[(size_t)b].begin(), plan.trsm_end[(size_t)b].end());
+        P.tmap = (const CUtensorMap*)(base + m.off_maps) + 3 * (size_t)b;
+        memcpy(&maps[3 * (size_t)b], t->tmap, 3 * sizeof(CUtensorMap));
+        jobs[(size_t)b].L = P.L;
+        jobs[(size_t)b].z = items[b].d_z;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(base + m.off_probs, probs.data(), sizeof(ProbDev) * probs.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(base + m.off_jobs, jobs.data(), sizeof(SolveJob) * jobs.size(),
+                                cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(base + m.off_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                                cudaMemcpyHostToDevice, s);
+    if (!e && !tend.empty())
+        e = cudaMemcpyAsync(base + m.off_tend, tend.data(), sizeof(int) * tend.size(), cudaMemcpyHostToDevice, s);
+    if (!e && !plan.prio.empty())
+        e = cudaMemcpyAsync(base + m.off_prio, plan.prio.data(), sizeof(G2Task) * plan.prio.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (!e && !plan.bulk.empty())
+        e = cudaMemcpyAsync(base + m.off_bulk, plan.bulk.data(), sizeof(G2Task) * plan.bulk.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (!e && !plan.tct.empty())
+        e = cudaMemcpyAsync(base + m.off_tct, plan.tct.data(), sizeof(int4) * plan.tct.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return GEO_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto& kv : g_batches)
+        if (kv.first == d_work) {
+            kv.second = m;
+            return GEO_OK;
+        }
+    g_batches.push_back({d_work, m});
+    return GEO_OK;
+}
+
+int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_theta, void* d_work,
+                     double* d_out, void* stream) {
+    if (nprob < 1) return -1;
+    if (!items) return -2;
+    if (!d_theta) return -3;
+    if (!d_work) return -4;
+    if (!d_out) return -5;
+    BatchMeta m;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        bool found = false;
+        for (auto& kv : g_batches)
+            if (kv.first == d_work) {
+                m = kv.second;
+                found = true;
+            }
+        if (!found || m.nprob != nprob) return -4;   // not bound by geo_batch_bind for this batch
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)d_work;
+    const geo_theta dummy = {1.0, 1.0, 0.5, 0.0};
+    for (int b = 0; b < nprob; ++b) {
+        const Layout L = make_layout(items[b].t);
+        if (launch_matern_tiles(L, items[b].d_x, items[b].d_y, dummy, d_theta + b, 1, s)) return GEO_ERR_CUDA;
+    }
+    if (run_potrf_dag_batch((const ProbDev*)(base + m.off_probs), nprob, (const G2Task*)(base + m.off_prio),
+                            m.n_prio, (const G2Task*)(base + m.off_bulk), m.n_bulk,
+                            (const int4*)(base + m.off_tct), m.n_tct, m.per, (int*)(base + m.off_ctr),
+                            m.counter_bytes, s))
+        return GEO_ERR_CUDA;
+    if (launch_trsv_batch((const SolveJob*)(base + m.off_jobs), nprob, d_out, s)) return GEO_ERR_CUDA;
     return GEO_OK;
 }
 

@@ -144,23 +144,25 @@ constexpr size_t DAG_DYN_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /*alig
 constexpr int PRIO_LIMIT = 48;   // workers allowed inside priority tasks at once when a bulk queue exists
 
 struct DagArgs {
-    Layout L;
+    ProbDev one;             // the problem of a single-problem launch
+    const ProbDev* probs;    // batched launch: the problems' views in global memory (nullptr: single)
     const G2Task* prio;
     const G2Task* bulk;
-    const int* trsm_end;
     long long n_prio, n_bulk;
-    const int4* tct;
+    const int4* tct;         // tensor targets (i, j, k, problem)
     long long n_tc_items;
-    int* ctr;    // [0] priority head, [1] tensor head, [2] bulk head, [3] workers in priority tasks
-    int* upd;
-    int* tcnt;
-    int* pot;
-    int* sub;    // [p*p*max_items]: steps applied to each update sub-block of a tile
-    SchedGeom g;   // g.ex: in-band updates are tensor-core (FP64-accurate) items
+    int per;                 // tensor items per target
+    int* ctr;    // [0] priority head, [1] tensor head, [2] bulk head, [3] workers in priority tasks,
+                 // [4] abort: a wait timed out somewhere
     unsigned long long* trace_ctr;   // optional task trace (nullptr: off)
     geo_trace_rec* trace;
     long long trace_cap;
 };
+
+__device__ __forceinline__ const ProbDev& prob_of(const DagArgs& A, int pid) {
+    return A.probs ? A.probs[pid] : A.one;
+}
+__device__ __forceinline__ bool aborted(const DagArgs& A) { return *((volatile const int*)A.ctr + 4) != 0; }
 
 __device__ __forceinline__ int smid() {
     int s;
@@ -189,18 +191,21 @@ __device__ __forceinline__ void trace_put(const DagArgs& A, int type, int k, int
 __device__ __forceinline__ void g2_sync() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// Wait until *p >= v (acquire).  False once the status records a failure or the
-// wait exceeds its bound (then it records GEO_ERR_TIMEOUT with `where`).
-__device__ bool wait_ge(const Layout& L, const int* p, int v, int where) {
+// Wait until *p >= v (acquire).  False once the problem's status records a
+// failure, the launch is aborted, or the wait exceeds its bound (then it
+// records GEO_ERR_TIMEOUT with `where` in the problem's status and aborts the
+// launch: a timeout means the schedule itself went wrong).
+__device__ bool wait_ge(const DagArgs& A, const Layout& L, const int* p, int v, int where) {
     if (ld_acquire_s32(p) >= v) return true;
     const long long dl = gtimer() + DAG_WAIT_NS;
     for (unsigned it = 1;; ++it) {
         __nanosleep(64);
         if (ld_acquire_s32(p) >= v) return true;
         if ((it & 31u) == 0) {
-            if (failed(L)) return false;
+            if (failed(L) || aborted(A)) return false;
             if (gtimer() > dl) {
                 set_timeout(L, where);
+                atomicExch(A.ctr + 4, 1);
                 return false;
             }
         }
@@ -208,17 +213,17 @@ __device__ bool wait_ge(const Layout& L, const int* p, int v, int where) {
 }
 
 // update items applied to tile (i,j) per step
-__device__ __forceinline__ int items_of(const DagArgs& A, int i, int j) {
-    return (is_dp(i, j, A.L.band) && !A.g.ex) ? A.g.items64 : A.g.items_tc;
+__device__ __forceinline__ int items_of(const ProbDev& P, int i, int j) {
+    return (is_dp(i, j, P.L.band) && !P.g.ex) ? P.g.items64 : P.g.items_tc;
 }
-__device__ __forceinline__ int chunks_of(const DagArgs& A, int i, int k) {
-    return is_dp(i, k, A.L.band) ? A.g.chunks_dp : A.g.chunks_sp;
+__device__ __forceinline__ int chunks_of(const ProbDev& P, int i, int k) {
+    return is_dp(i, k, P.L.band) ? P.g.chunks_dp : P.g.chunks_sp;
 }
-__device__ __forceinline__ int* sub_at(const DagArgs& A, int i, int j, int q) {
-    return A.sub + ((size_t)i * A.L.p + j) * A.g.max_items + q;
+__device__ __forceinline__ int* sub_at(const ProbDev& P, int i, int j, int q) {
+    return P.sub + ((size_t)i * P.L.p + j) * P.g.max_items + q;
 }
-__device__ __forceinline__ int* pot_at(const DagArgs& A, int k, int r, int c) {
-    return A.pot + ((size_t)k * A.g.ns + r) * A.g.ns + c;
+__device__ __forceinline__ int* pot_at(const ProbDev& P, int k, int r, int c) {
+    return P.pot + ((size_t)k * P.g.ns + r) * P.g.ns + c;
 }
 
 // ---- CUDA-core group: shared memory of one task at a time
@@ -245,8 +250,8 @@ struct G2Smem {
 // tiny on this part, so spreading the updates over the four warps (and
 // replacing divisions by one reciprocal square root) shortens this task, which
 // is on the factorization's critical path.
-__device__ bool g2_pf(const DagArgs& A, G2Smem& S, int k, int s, int g) {
-    const Layout& L = A.L;
+__device__ bool g2_pf(const ProbDev& P, G2Smem& S, int k, int s, int g) {
+    const Layout& L = P.L;
     const int nb = L.nb, c0 = s * 32, w = min(32, nb - c0), lane = g & 31, wp = g >> 5;
     double* T = dp_tile(L, k, k);
     double* D = S.pot.D;
@@ -287,8 +292,8 @@ __device__ bool g2_pf(const DagArgs& A, G2Smem& S, int k, int s, int g) {
 // PT(k,r,s): X(r,s) <- X(r,s) L(s,s)^-T, right-looking over the 32 columns:
 // lane i scales row i of column c by 1/L_cc, then row i of the later columns
 // j > c is updated, the four warps taking the columns j = c+1.. in turn.
-__device__ void g2_pt(const DagArgs& A, G2Smem& S, int k, int r, int s, int g) {
-    const Layout& L = A.L;
+__device__ void g2_pt(const ProbDev& P, G2Smem& S, int k, int r, int s, int g) {
+    const Layout& L = P.L;
     const int nb = L.nb, c0 = s * 32, r0 = r * 32, w = min(32, nb - c0), h = min(32, nb - r0);
     const int lane = g & 31, wp = g >> 5;
     double* T = dp_tile(L, k, k);
@@ -326,8 +331,8 @@ __device__ __forceinline__ void dmma884(double& c0, double& c1, double a, double
 }
 
 // PU(k,r,c,s): sub-block (r,c) -= (r,s)(c,s)'; 4 warps x 16 x 16, DMMA.
-__device__ void g2_pu(const DagArgs& A, G2Smem& S, int k, int r, int c, int s, int g) {
-    const Layout& L = A.L;
+__device__ void g2_pu(const ProbDev& P, G2Smem& S, int k, int r, int c, int s, int g) {
+    const Layout& L = P.L;
     const int nb = L.nb, s0 = s * 32, r0 = r * 32, q0 = c * 32;
     double* T = dp_tile(L, k, k);
     double* Ar = S.pot.D;
@@ -478,9 +483,9 @@ __device__ void g2_slice_row(const Layout& L, const T* __restrict__ X, int i, in
 }
 
 // UPD(k,i,j,q): 64 x 64 sub-block q of target (i,j) -= A(i,k) A(j,k)' in FP64.
-__device__ void g2_upd(const DagArgs& A, G2Smem& S, int k, int i, int j, int q, int g) {
-    const Layout& L = A.L;
-    const int nb = L.nb, nsb = A.g.nsb64;
+__device__ void g2_upd(const ProbDev& P, G2Smem& S, int k, int i, int j, int q, int g) {
+    const Layout& L = P.L;
+    const int nb = L.nb, nsb = P.g.nsb64;
     const int sbr = q / nsb, sbc = q % nsb;
     const bool syrk = (i == j);
     if (syrk && sbr < sbc) return;
@@ -554,10 +559,15 @@ __device__ void g2_upd(const DagArgs& A, G2Smem& S, int k, int i, int j, int q, 
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
 
+// Stop the whole launch (a wait timed out): the flag every wait polls, and in a
+// single-problem launch that problem's status.
+__device__ void abort_launch(const DagArgs& A, int where) {
+    atomicExch(A.ctr + 4, 1);
+    if (!A.probs) set_timeout(A.one.L, where);
+}
+
 __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
-    const Layout& L = A.L;
     const int g = threadIdx.x - TC_THREADS;
-    const int nb = L.nb, ns = A.g.ns;
     int* prio_head = A.ctr + 0;
     int* bulk_head = A.ctr + 2;
     int* inflight = A.ctr + 3;
@@ -570,7 +580,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
             int kind = -1, idx = -1;
             const long long dl = gtimer() + DAG_WAIT_NS;
             for (unsigned spin = 0; kind < 0; ++spin) {
-                if (failed(L)) break;
+                if (aborted(A) || (!A.probs && failed(A.one.L))) break;
                 const int ph = ld_volatile(prio_head);
                 if (ph < A.n_prio) {
                     if (atomicAdd(inflight, 1) < (A.n_bulk > 0 ? PRIO_LIMIT : DAG_THREADS * 4096)) {
@@ -584,8 +594,8 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 }
                 const int bh = ld_volatile(bulk_head);
                 if (bh < A.n_bulk) {
-                    const int kb = A.bulk[bh].k;
-                    if (ld_volatile(prio_head) >= A.trsm_end[kb]) {
+                    const G2Task& tb = A.bulk[bh];
+                    if (ld_volatile(prio_head) >= prob_of(A, tb.pid).trsm_end[tb.k]) {
                         idx = atomicAdd(bulk_head, 1);
                         if (idx < A.n_bulk) {
                             kind = 1;
@@ -597,7 +607,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 }
                 __nanosleep(256);
                 if ((spin & 63u) == 63u && gtimer() > dl) {
-                    set_timeout(L, 10);
+                    abort_launch(A, 10);
                     break;
                 }
             }
@@ -608,57 +618,65 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
         if (S.task < 0) return;
         const int kind = S.task >> 30, tix = S.task & ((1 << 30) - 1);
         const G2Task t = kind == 0 ? A.prio[tix] : A.bulk[tix];
-        // ---- dependencies (thread 0 waits, the group follows)
+        const ProbDev& P = prob_of(A, t.pid);
+        const Layout& L = P.L;
+        const int nb = L.nb, ns = P.g.ns;
+        // ---- dependencies (thread 0 waits, the group follows); a task of a
+        // problem that has failed (not positive definite) is skipped
         if (g == 0) {
-            bool ok = true;
+            bool ok = !failed(L);
             const int k = t.k;
-            if (kind == 1 && ld_volatile(prio_head) < A.trsm_end[k])
-                ok = wait_ge(L, prio_head, A.trsm_end[k], 25);
-            switch (t.type) {
+            if (ok && kind == 1 && ld_volatile(prio_head) < P.trsm_end[k])
+                ok = wait_ge(A, L, prio_head, P.trsm_end[k], 25);
+            if (ok) switch (t.type) {
                 case T_PF:
-                    if (t.a == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * items_of(A, k, k), 11);
-                    ok = ok && wait_ge(L, pot_at(A, k, t.a, t.a), t.a, 12);
+                    if (t.a == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 11);
+                    ok = ok && wait_ge(A, L, pot_at(P, k, t.a, t.a), t.a, 12);
                     break;
                 case T_PT:
-                    if (t.b == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * items_of(A, k, k), 13);
-                    ok = ok && wait_ge(L, pot_at(A, k, t.b, t.b), t.b + 1, 14) &&
-                         wait_ge(L, pot_at(A, k, t.a, t.b), t.b, 15);
+                    if (t.b == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 13);
+                    ok = ok && wait_ge(A, L, pot_at(P, k, t.b, t.b), t.b + 1, 14) &&
+                         wait_ge(A, L, pot_at(P, k, t.a, t.b), t.b, 15);
                     break;
                 case T_PU:
-                    if (t.c == 0) ok = wait_ge(L, A.upd + k * L.p + k, k * items_of(A, k, k), 16);
-                    ok = ok && wait_ge(L, pot_at(A, k, t.a, t.c), t.c + 1, 17) &&
-                         wait_ge(L, pot_at(A, k, t.b, t.c), t.c + 1, 18) &&
-                         wait_ge(L, pot_at(A, k, t.a, t.b), t.c, 19);
+                    if (t.c == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 16);
+                    ok = ok && wait_ge(A, L, pot_at(P, k, t.a, t.c), t.c + 1, 17) &&
+                         wait_ge(A, L, pot_at(P, k, t.b, t.c), t.c + 1, 18) &&
+                         wait_ge(A, L, pot_at(P, k, t.a, t.b), t.c, 19);
                     break;
                 case T_TRSM:
-                    ok = wait_ge(L, pot_at(A, k, ns - 1, ns - 1), ns, 20) &&
-                         wait_ge(L, A.upd + t.a * L.p + k, k * items_of(A, t.a, k), 21);
+                    ok = wait_ge(A, L, pot_at(P, k, ns - 1, ns - 1), ns, 20) &&
+                         wait_ge(A, L, P.upd + t.a * L.p + k, k * items_of(P, t.a, k), 21);
                     break;
                 default:   // T_UPD: own sub-block's previous step only
-                    ok = wait_ge(L, A.tcnt + t.a * L.p + k, chunks_of(A, t.a, k), 22) &&
-                         wait_ge(L, A.tcnt + t.b * L.p + k, chunks_of(A, t.b, k), 23) &&
-                         wait_ge(L, sub_at(A, t.a, t.b, t.c), k, 24);
+                    ok = wait_ge(A, L, P.tcnt + t.a * L.p + k, chunks_of(P, t.a, k), 22) &&
+                         wait_ge(A, L, P.tcnt + t.b * L.p + k, chunks_of(P, t.b, k), 23) &&
+                         wait_ge(A, L, sub_at(P, t.a, t.b, t.c), k, 24);
                     break;
             }
             S.ok = ok ? 1 : 0;
             t_ready = gtimer();
         }
         g2_sync();
-        if (!S.ok) return;
+        if (!S.ok) {   // failed problem or aborted launch: drop the task
+            if (g == 0 && kind == 0) atomicSub(inflight, 1);
+            continue;
+        }
         // ---- the task
         int* done = nullptr;
+        bool ran = true;
         switch (t.type) {
             case T_PF:
-                if (!g2_pf(A, S, t.k, t.a, g)) return;
-                done = pot_at(A, t.k, t.a, t.a);
+                ran = g2_pf(P, S, t.k, t.a, g);   // false: not positive definite (status set)
+                done = pot_at(P, t.k, t.a, t.a);
                 break;
             case T_PT:
-                g2_pt(A, S, t.k, t.a, t.b, g);
-                done = pot_at(A, t.k, t.a, t.b);
+                g2_pt(P, S, t.k, t.a, t.b, g);
+                done = pot_at(P, t.k, t.a, t.b);
                 break;
             case T_PU:
-                g2_pu(A, S, t.k, t.a, t.b, t.c, g);
-                done = pot_at(A, t.k, t.a, t.b);
+                g2_pu(P, S, t.k, t.a, t.b, t.c, g);
+                done = pot_at(P, t.k, t.a, t.b);
                 break;
             case T_TRSM: {
                 const int i = t.a, k = t.k, q = t.b;
@@ -674,19 +692,21 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                     if (L.planes && r < nb) g2_slice_row<float>(L, X, i, k, r, m);
                 }
                 fence_proxy_async_global();   // the planes are read by TMA
-                done = A.tcnt + i * L.p + k;
+                done = P.tcnt + i * L.p + k;
                 break;
             }
             default:
-                g2_upd(A, S, t.k, t.a, t.b, t.c, g);
-                done = A.upd + t.a * L.p + t.b;
+                g2_upd(P, S, t.k, t.a, t.b, t.c, g);
+                done = P.upd + t.a * L.p + t.b;
                 break;
         }
         __threadfence();
         g2_sync();
         if (g == 0) {
-            if (t.type == T_UPD) red_release_add(sub_at(A, t.a, t.b, t.c), 1);
-            red_release_add(done, 1);
+            if (ran) {
+                if (t.type == T_UPD) red_release_add(sub_at(P, t.a, t.b, t.c), 1);
+                red_release_add(done, 1);
+            }
             if (kind == 0) atomicSub(inflight, 1);
             trace_put(A, t.type, t.k, t.a, t.b, t.c, t_claim, t_ready, gtimer());
         }
@@ -694,15 +714,15 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
 }
 
 // ---- tensor group: the split-BF16 update with dynamic items and dependencies
-// bounded mbarrier wait for the scheduler: gives up on a recorded failure, an
-// abort of this CTA, or after DAG_WAIT_NS
-__device__ bool dwait(const Layout& L, uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// bounded mbarrier wait for the scheduler: gives up when the launch is aborted
+// (or a single problem has failed), on an abort of this CTA, or after DAG_WAIT_NS
+__device__ bool dwait(const DagArgs& A, uint32_t bar, uint32_t parity, volatile int* abort_flag) {
     if (mbar_try(bar, parity)) return true;
     const long long dl = gtimer() + DAG_WAIT_NS;
     for (unsigned it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 255u) == 0) {
-            if (*abort_flag || failed(L)) return false;
+            if (*abort_flag || aborted(A) || (!A.probs && failed(A.one.L))) return false;
             if (gtimer() > dl) return false;
         }
     }
@@ -711,66 +731,72 @@ __device__ bool dwait(const Layout& L, uint32_t bar, uint32_t parity, volatile i
 // Tensor-queue item w: target (i,j) of step k, output block (mb, nc) of
 // TC_BM x TC_BN.  An off-band target's block is one FP32-accurate product (one
 // TMEM buffer, 10 slice pairs over the whole contraction); an in-band target's
-// block (A.g.ex) is FP64-accurate: for each of its one or two 64-column halves
+// block (with in-band updates on the tensor cores) is FP64-accurate: for each of its one or two 64-column halves
 // and each 256-long part of the contraction, the 28 slice pairs of two passes
 // into seven accumulators spanning both TMEM buffers, drained into the FP64
 // tile before the next part.  Blocks of a diagonal target wholly above its
 // diagonal are not computed.
 struct TcItem {
-    int i, j, k, mb, nc, rem;
-    bool ex, skip;
+    int i, j, k, mb, nc, rem, pid;
+    bool ex, skip, pad;
     int nh;   // in-band: 64-column halves holding columns < nb
 };
 
 __device__ __forceinline__ TcItem tc_decode(const DagArgs& A, long long w) {
-    const int per = A.g.items_tc;
-    const int nnc = (A.L.pp + TC_BN - 1) / TC_BN;
-    const int4 tg = A.tct[w / per];
+    const int4 tg = A.tct[w / A.per];
     TcItem t;
     t.i = tg.x;
     t.j = tg.y;
     t.k = tg.z;
-    t.rem = (int)(w % per);
+    t.pid = tg.w;
+    const ProbDev& P = prob_of(A, t.pid);
+    const int nnc = (P.L.pp + TC_BN - 1) / TC_BN;
+    t.rem = (int)(w % A.per);
+    t.pad = t.rem >= P.g.items_tc;   // a smaller problem of a batch: no such block
     t.mb = t.rem / nnc;
     t.nc = t.rem % nnc;
-    t.ex = A.g.ex && is_dp(t.i, t.j, A.L.band);
+    t.ex = P.g.ex && is_dp(t.i, t.j, P.L.band);
     t.skip = t.ex && t.i == t.j && t.mb < t.nc;
-    t.nh = (t.nc * TC_BN + EX_BN < A.L.nb) ? 2 : 1;
+    t.nh = (t.nc * TC_BN + EX_BN < P.L.nb) ? 2 : 1;
     return t;
 }
 
 __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUtensorMap* tmap_b,
                           const CUtensorMap* tmap_b64, uint8_t* smem, uint64_t* bars, uint32_t tmem_base,
                           volatile int* abort_flag, volatile int* ring) {
-    const Layout& L = A.L;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int s_epi_skip;
     const uint32_t bar0 = smem_u32(bars);
     auto FULL = [&](int s) { return bar0 + 8u * s; };
     auto EMPTY = [&](int s) { return bar0 + 8u * (TC_STAGES + s); };
     auto TFULL = [&](int a) { return bar0 + 8u * (2 * TC_STAGES + a); };
     auto TEMPTY = [&](int a) { return bar0 + 8u * (2 * TC_STAGES + 2 + a); };
     auto RFULL = [&](int q) { return bar0 + 8u * (2 * TC_STAGES + 4 + q); };
-    const int nb = L.nb, pp = L.pp, p = L.p;
-    const int nk = pp / TC_BK;
     constexpr int KPC = EX_KP / TC_BK;   // K chunks per part of an in-band item
-    const int nkp = (nk + KPC - 1) / KPC;
+    const bool single = A.probs == nullptr;
     if (warp == 0) {
         if (lane != 0) return;
         int it = 0;
         for (int t = 0;;) {
-            long long w = failed(L) || *abort_flag ? -1 : atomicAdd(A.ctr + 1, 1);
+            long long w = (*abort_flag || aborted(A) || (single && failed(A.one.L))) ? -1 : atomicAdd(A.ctr + 1, 1);
             if (w >= A.n_tc_items) w = -1;
             TcItem m;
             if (w >= 0) {
                 m = tc_decode(A, w);
+                const ProbDev& P = prob_of(A, m.pid);
+                if (m.pad || (!single && failed(P.L))) continue;   // no such block / problem failed
                 if (m.skip) {   // nothing below the diagonal: count the item as applied
-                    red_release_add(A.upd + m.i * p + m.j, 1);
+                    red_release_add(P.upd + m.i * P.L.p + m.j, 1);
                     continue;
                 }
-                const bool ok = wait_ge(L, A.tcnt + m.i * p + m.k, chunks_of(A, m.i, m.k), 31) &&
-                                wait_ge(L, A.tcnt + m.j * p + m.k, chunks_of(A, m.j, m.k), 32);
-                if (!ok) w = -1;
-                else fence_proxy_async_global();
+                const bool ok = wait_ge(A, P.L, P.tcnt + m.i * P.L.p + m.k, chunks_of(P, m.i, m.k), 31) &&
+                                wait_ge(A, P.L, P.tcnt + m.j * P.L.p + m.k, chunks_of(P, m.j, m.k), 32);
+                if (!ok) {
+                    if (!single && !aborted(A)) continue;   // its problem failed meanwhile
+                    w = -1;
+                } else {
+                    fence_proxy_async_global();
+                }
             }
             ring[t % RING] = (int)w;
             mbar_arrive(RFULL(t % RING));
@@ -778,16 +804,21 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             const int st0 = it % TC_STAGES;
             if (w < 0) {
                 // hand the end marker to the MMA thread through the next stage
-                if (dwait(L, EMPTY(st0), ((it / TC_STAGES) & 1) ^ 1, abort_flag)) mbar_arrive(FULL(st0));
+                if (dwait(A, EMPTY(st0), ((it / TC_STAGES) & 1) ^ 1, abort_flag)) mbar_arrive(FULL(st0));
                 ++it;
                 break;
             }
-            const int sa = L.slot[m.i * p + m.k] * NPL, sb = L.slot[m.j * p + m.k] * NPL;
+            const ProbDev& P = prob_of(A, m.pid);
+            const int p = P.L.p, nk = P.L.pp / TC_BK, nkp = (nk + KPC - 1) / KPC;
+            const int sa = P.L.slot[m.i * p + m.k] * NPL, sb = P.L.slot[m.j * p + m.k] * NPL;
+            const CUtensorMap* map_a = single ? tmap_a : P.tmap;
+            const CUtensorMap* map_b = single ? tmap_b : P.tmap + 1;
+            const CUtensorMap* map_b64 = single ? tmap_b64 : P.tmap + 2;
             bool ok = true;
             auto next_stage = [&](uint32_t bytes) -> uint8_t* {
                 const int st = it % TC_STAGES;
                 const uint32_t ph = (it / TC_STAGES) & 1;
-                if (!dwait(L, EMPTY(st), ph ^ 1, abort_flag)) return nullptr;
+                if (!dwait(A, EMPTY(st), ph ^ 1, abort_flag)) return nullptr;
                 mbar_expect_tx(FULL(st), bytes);
                 return smem + st * TC_STAGE_BYTES;
             };
@@ -801,10 +832,10 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                     const uint32_t full = FULL(it % TC_STAGES);
 #pragma unroll
                     for (int s = 0; s < TC_NS; ++s)
-                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), tmap_a, kc * TC_BK, m.mb * TC_BM, sa + s, full);
+                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), map_a, kc * TC_BK, m.mb * TC_BM, sa + s, full);
 #pragma unroll
                     for (int s = 0; s < TC_NS; ++s)
-                        tma_load_3d(smem_u32(sbase + TC_NS * TC_A_BYTES + s * TC_B_BYTES), tmap_b, kc * TC_BK,
+                        tma_load_3d(smem_u32(sbase + TC_NS * TC_A_BYTES + s * TC_B_BYTES), map_b, kc * TC_BK,
                                     m.nc * TC_BN, sb + s, full);
                 }
             } else {
@@ -823,20 +854,20 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                                 if (pass == 0) {
 #pragma unroll
                                     for (int s = 0; s < 4; ++s)
-                                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), tmap_a, kc * TC_BK,
+                                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), map_a, kc * TC_BK,
                                                     m.mb * TC_BM, sa + s, full);
 #pragma unroll
                                     for (int s = 0; s < NPL; ++s)
-                                        tma_load_3d(smem_u32(sbase + 4 * TC_A_BYTES + s * EX_B_BYTES), tmap_b64,
+                                        tma_load_3d(smem_u32(sbase + 4 * TC_A_BYTES + s * EX_B_BYTES), map_b64,
                                                     kc * TC_BK, brow, sb + s, full);
                                 } else {
 #pragma unroll
                                     for (int u = 0; u < 3; ++u)
-                                        tma_load_3d(smem_u32(sbase + u * TC_A_BYTES), tmap_a, kc * TC_BK,
+                                        tma_load_3d(smem_u32(sbase + u * TC_A_BYTES), map_a, kc * TC_BK,
                                                     m.mb * TC_BM, sa + 4 + u, full);
 #pragma unroll
                                     for (int s = 0; s < 3; ++s)
-                                        tma_load_3d(smem_u32(sbase + 3 * TC_A_BYTES + s * EX_B_BYTES), tmap_b64,
+                                        tma_load_3d(smem_u32(sbase + 3 * TC_A_BYTES + s * EX_B_BYTES), map_b64,
                                                     kc * TC_BK, brow, sb + s, full);
                                 }
                             }
@@ -844,7 +875,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                 }
             }
             if (!ok) {
-                if (!failed(L)) set_timeout(L, 33);
+                abort_launch(A, 33);
                 *abort_flag = 1;
                 break;
             }
@@ -856,7 +887,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
         int it = 0;
         int use0 = 0, use1 = 0, nxt = 0;   // completed uses of each TMEM buffer; buffer of the next off-band item
         auto bail = [&](int where) {
-            if (!failed(L)) set_timeout(L, where);
+            abort_launch(A, where);
             *abort_flag = 1;
             mbar_arrive(TFULL(0));
             mbar_arrive(TFULL(1));
@@ -864,25 +895,27 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
         for (int tc = 0;; ++tc) {
             // the first stage of the item carries the item id (or the end marker)
             const int st0 = it % TC_STAGES;
-            if (!dwait(L, FULL(st0), (it / TC_STAGES) & 1, abort_flag)) {
+            if (!dwait(A, FULL(st0), (it / TC_STAGES) & 1, abort_flag)) {
                 bail(34);
                 break;
             }
             const int w = ring[tc % RING];
             if (w < 0) break;   // end marker (the epilogue reads it from the ring)
             const TcItem m = tc_decode(A, w);
+            const ProbDev& P = prob_of(A, m.pid);
+            const int nk = P.L.pp / TC_BK, nkp = (nk + KPC - 1) / KPC;
             bool ok = true;
             bool first = true;   // FULL(it) of the item's first stage already observed
             auto stage = [&]() -> uint32_t {
                 const int st = it % TC_STAGES;
-                if (!first && !dwait(L, FULL(st), (it / TC_STAGES) & 1, abort_flag)) return 0;
+                if (!first && !dwait(A, FULL(st), (it / TC_STAGES) & 1, abort_flag)) return 0;
                 first = false;
                 tc_fence_after();
                 return smem_u32(smem + st * TC_STAGE_BYTES);
             };
             if (!m.ex) {
                 const int b = nxt;
-                if (!dwait(L, TEMPTY(b), ((b ? use1 : use0) & 1) ^ 1, abort_flag)) {
+                if (!dwait(A, TEMPTY(b), ((b ? use1 : use0) & 1) ^ 1, abort_flag)) {
                     bail(35);
                     break;
                 }
@@ -921,8 +954,8 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             } else {
                 for (int h = 0; h < m.nh && ok; ++h)
                     for (int kp = 0; kp < nkp && ok; ++kp) {
-                        if (!dwait(L, TEMPTY(0), (use0 & 1) ^ 1, abort_flag) ||
-                            !dwait(L, TEMPTY(1), (use1 & 1) ^ 1, abort_flag)) {
+                        if (!dwait(A, TEMPTY(0), (use0 & 1) ^ 1, abort_flag) ||
+                            !dwait(A, TEMPTY(1), (use1 & 1) ^ 1, abort_flag)) {
                             ok = false;
                             break;
                         }
@@ -987,8 +1020,8 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
         const int row_in = quad * 32 + lane;
         int use0 = 0, use1 = 0, nxt = 0;
         for (int tc = 0;; ++tc) {
-            if (!dwait(L, RFULL(tc % RING), (tc / RING) & 1, abort_flag)) {
-                if (!failed(L)) set_timeout(L, 37);
+            if (!dwait(A, RFULL(tc % RING), (tc / RING) & 1, abort_flag)) {
+                abort_launch(A, 37);
                 *abort_flag = 1;
                 break;
             }
@@ -996,15 +1029,26 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             if (w < 0) break;
             const TcItem m = tc_decode(A, w);
             const int i = m.i, j = m.j, k = m.k;
-            // read-modify-write of C(i,j) only after the previous step's items on it
+            const ProbDev& P = prob_of(A, m.pid);
+            const Layout& L = P.L;
+            const int nb = L.nb, pp = L.pp, p = L.p;
+            const int nk = pp / TC_BK, nkp = (nk + KPC - 1) / KPC;
+            // read-modify-write of C(i,j) only after the previous step's items on
+            // it; when its problem has failed (batched launch) the item's TMEM is
+            // still consumed, but nothing is written
             const long long te0 = gtimer();
             if (threadIdx.x == 64) {
-                if (!wait_ge(L, sub_at(A, i, j, m.rem), k, 38)) *abort_flag = 1;
+                s_epi_skip = 0;
+                if (!wait_ge(A, L, sub_at(P, i, j, m.rem), k, 38)) {
+                    if (single || aborted(A)) *abort_flag = 1;
+                    else s_epi_skip = 1;
+                }
             }
             epi_sync();
             if (*abort_flag) break;
+            const bool write = s_epi_skip == 0;
             const int r = m.mb * TC_BM + row_in;
-            const bool rv = r < nb;
+            const bool rv = write && r < nb;
             const int* eb = L.rexp + (size_t)L.slot[j * p + k] * pp;
             const int er = (r < pp) ? L.rexp[(size_t)L.slot[i * p + k] * pp + r] : 0;
             const uint32_t tlane = (uint32_t)(quad * 32) << 16;
@@ -1019,8 +1063,8 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                 float cpre[BATCH];
 #pragma unroll
                 for (int e = 0; e < BATCH; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0f;
-                if (!dwait(L, TFULL(b), (b ? use1 : use0) & 1, abort_flag) || *abort_flag) {
-                    if (!failed(L)) set_timeout(L, 39);
+                if (!dwait(A, TFULL(b), (b ? use1 : use0) & 1, abort_flag) || *abort_flag) {
+                    abort_launch(A, 39);
                     *abort_flag = 1;
                     break;
                 }
@@ -1078,8 +1122,8 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                         double cpre[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0;
-                        if (!dwait(L, TFULL(0), use0 & 1, abort_flag) ||
-                            !dwait(L, TFULL(1), use1 & 1, abort_flag) || *abort_flag) {
+                        if (!dwait(A, TFULL(0), use0 & 1, abort_flag) ||
+                            !dwait(A, TFULL(1), use1 & 1, abort_flag) || *abort_flag) {
                             ok = false;
                             break;
                         }
@@ -1115,16 +1159,16 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                     }
                 }
                 if (!ok) {
-                    if (!failed(L)) set_timeout(L, 39);
+                    abort_launch(A, 39);
                     *abort_flag = 1;
                     break;
                 }
             }
             __threadfence();
             epi_sync();
-            if (threadIdx.x == 64) {
-                red_release_add(sub_at(A, i, j, m.rem), 1);
-                red_release_add(A.upd + i * p + j, 1);
+            if (threadIdx.x == 64 && write) {
+                red_release_add(sub_at(P, i, j, m.rem), 1);
+                red_release_add(P.upd + i * p + j, 1);
                 trace_put(A, m.ex ? 11 : 10, k, i, j, m.rem, te0, te0, gtimer());
             }
         }
@@ -1180,41 +1224,141 @@ __global__ void __launch_bounds__(DAG_THREADS, 1)
     }
 }
 
-cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, cudaStream_t s) {
-    static int attr_done = 0, nsm = 0;
+static cudaError_t dag_prepare(int& nsm) {
+    static int attr_done = 0, nsm_cached = 0;
     cudaError_t e;
     if (!attr_done) {
         if ((e = cudaFuncSetAttribute(dag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DAG_DYN_SMEM)))
             return e;
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&nsm_cached, cudaDevAttrMultiProcessorCount, dev);
         attr_done = 1;
     }
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dag_kernel, DAG_THREADS, DAG_DYN_SMEM))) return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    nsm = nsm_cached;
+    return cudaSuccess;
+}
+
+// counters of one problem inside its block (after the 16 launch-wide words)
+void bind_counters(ProbDev& P, int* base) {
+    const int p = P.L.p;
+    P.upd = base;
+    P.tcnt = P.upd + (size_t)p * p;
+    P.pot = P.tcnt + (size_t)p * p;
+    P.sub = P.pot + (size_t)p * P.g.ns * P.g.ns;
+}
+
+cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, cudaStream_t s) {
+    int nsm = 0;
+    cudaError_t e = dag_prepare(nsm);
+    if (e) return e;
     if ((e = cudaMemsetAsync(sv.counters, 0, sizeof(int) * (size_t)sv.geom.n_counters, s))) return e;
     DagArgs A;
-    A.L = L;
+    memset(&A, 0, sizeof(A));
+    A.one.L = L;
+    A.one.g = sv.geom;
+    A.one.trsm_end = sv.trsm_end;
+    A.one.tmap = nullptr;
+    bind_counters(A.one, sv.counters + 16);
+    A.probs = nullptr;
     A.prio = sv.prio;
     A.bulk = sv.bulk;
-    A.trsm_end = sv.trsm_end;
     A.n_prio = sv.geom.n_prio;
     A.n_bulk = sv.geom.n_bulk;
     A.tct = sv.tct;
-    A.n_tc_items = sv.geom.n_tct * (long long)sv.geom.items_tc;
+    A.per = sv.geom.items_tc;
+    A.n_tc_items = sv.geom.n_tct * (long long)A.per;
     A.ctr = sv.counters;
-    A.upd = sv.counters + 16;
-    A.tcnt = A.upd + (size_t)L.p * L.p;
-    A.pot = A.tcnt + (size_t)L.p * L.p;
-    A.sub = A.pot + (size_t)L.p * sv.geom.ns * sv.geom.ns;
-    A.g = sv.geom;
     A.trace_ctr = (unsigned long long*)t->trace;
     A.trace = t->trace ? (geo_trace_rec*)((char*)t->trace + 64) : nullptr;
     A.trace_cap = t->trace_cap;
     CUtensorMap maps[3];
     memcpy(maps, t->tmap, sizeof(maps));
+    void* args[] = {&A, &maps[0], &maps[1], &maps[2]};
+    prof_begin(4, s);
+    e = cudaLaunchCooperativeKernel((const void*)dag_kernel, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
+    prof_end(4, s);
+    count_launch();
+    return e;
+}
+
+void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, BatchPlan& out) {
+    const int nprob = (int)g.size();
+    out.prio.clear();
+    out.bulk.clear();
+    out.tct.clear();
+    out.trsm_end.assign((size_t)nprob, std::vector<int>());
+    out.per = 1;
+    std::vector<std::vector<G2Task>> prio((size_t)nprob), bulk((size_t)nprob);
+    std::vector<std::vector<int>> tend((size_t)nprob);
+    std::vector<std::vector<int4>> tct((size_t)nprob);
+    int pmax = 0;
+    for (int b = 0; b < nprob; ++b) {
+        sched_build(g[(size_t)b], band[(size_t)b], prio[(size_t)b], bulk[(size_t)b], tend[(size_t)b],
+                    tct[(size_t)b]);
+        out.trsm_end[(size_t)b].assign((size_t)g[(size_t)b].p, 0);
+        out.per = std::max(out.per, g[(size_t)b].items_tc);
+        pmax = std::max(pmax, g[(size_t)b].p);
+    }
+    // every queue of a problem is ordered by step; step k of all problems
+    // precedes step k+1 of any
+    std::vector<size_t> ip((size_t)nprob, 0), ib((size_t)nprob, 0), it((size_t)nprob, 0);
+    for (int k = 0; k < pmax; ++k) {
+        for (int b = 0; b < nprob; ++b) {
+            const std::vector<G2Task>& q = prio[(size_t)b];
+            const size_t seg0 = ip[(size_t)b];
+            const size_t base = out.prio.size();
+            while (ip[(size_t)b] < q.size() && q[ip[(size_t)b]].k == k) {
+                G2Task tk = q[ip[(size_t)b]++];
+                tk.pid = b;
+                out.prio.push_back(tk);
+            }
+            if (k < g[(size_t)b].p)
+                out.trsm_end[(size_t)b][(size_t)k] = (int)(base + ((size_t)tend[(size_t)b][(size_t)k] - seg0));
+        }
+        for (int b = 0; b < nprob; ++b) {
+            const std::vector<G2Task>& q = bulk[(size_t)b];
+            while (ib[(size_t)b] < q.size() && q[ib[(size_t)b]].k == k) {
+                G2Task tk = q[ib[(size_t)b]++];
+                tk.pid = b;
+                out.bulk.push_back(tk);
+            }
+        }
+        for (int b = 0; b < nprob; ++b) {
+            const std::vector<int4>& q = tct[(size_t)b];
+            while (it[(size_t)b] < q.size() && q[it[(size_t)b]].z == k) {
+                int4 v = q[it[(size_t)b]++];
+                v.w = b;
+                out.tct.push_back(v);
+            }
+        }
+    }
+}
+
+cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
+                                const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
+                                int* counters, size_t counter_bytes, cudaStream_t s) {
+    int nsm = 0;
+    cudaError_t e = dag_prepare(nsm);
+    if (e) return e;
+    if ((e = cudaMemsetAsync(counters, 0, counter_bytes, s))) return e;
+    DagArgs A;
+    memset(&A, 0, sizeof(A));
+    A.probs = d_probs;
+    A.prio = prio;
+    A.bulk = bulk;
+    A.n_prio = n_prio;
+    A.n_bulk = n_bulk;
+    A.tct = tct;
+    A.per = per;
+    A.n_tc_items = n_tct * (long long)per;
+    A.ctr = counters;
+    (void)nprob;
+    CUtensorMap maps[3];
+    memset(maps, 0, sizeof(maps));   // unused: each problem's maps are in its view
     void* args[] = {&A, &maps[0], &maps[1], &maps[2]};
     prof_begin(4, s);
     e = cudaLaunchCooperativeKernel((const void*)dag_kernel, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);

@@ -1,6 +1,8 @@
 // Persistent tile-DAG scheduler of Algorithm 1 (see dag.cu): task records,
 // queue geometry and the host entry point.
 #pragma once
+#include <cuda.h>
+
 #include <vector>
 
 #include "geo_internal.cuh"
@@ -10,9 +12,10 @@ namespace geo {
 enum TaskType : int { T_PF = 0, T_PT = 1, T_PU = 2, T_TRSM = 3, T_UPD = 4 };
 
 // One CUDA-core task: PF(k; a = s), PT(k; a = r, b = s), PU(k; a = r, b = c, c = s),
-// TRSM(k; a = i, b = row chunk), UPD(k; a = i, b = j, c = 64 x 64 sub-block).
+// TRSM(k; a = i, b = row chunk), UPD(k; a = i, b = j, c = 64 x 64 sub-block);
+// pid: the problem it belongs to (0 in a single-problem launch).
 struct G2Task {
-    int type, k, a, b, c;
+    int type, k, a, b, c, pid;
 };
 
 struct SchedGeom {
@@ -30,11 +33,40 @@ struct SchedView {
     const int4* tct;     // tensor queue targets (i, j, k), in order
 };
 
+// Device view of one problem of a launch: its layout, queue geometry, its
+// dependency counters, the priority-queue index past each step's solves, and
+// (batched launches) its three tensor maps in global memory.
+struct ProbDev {
+    Layout L;
+    SchedGeom g;
+    int *upd, *tcnt, *pot, *sub;
+    const int* trsm_end;
+    const CUtensorMap* tmap;
+};
+
 // ex: in-band (FP64) updates as FP64-accurate tensor-core items instead of
 // CUDA-core DMMA items
 SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex);
 void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
                  std::vector<int>& trsm_end, std::vector<int4>& tct);
 cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, cudaStream_t s);
+
+// Batched launch: every problem's tasks in one persistent kernel.  The host
+// merges the problems' queues step by step (each problem keeps its own
+// topological order, so the merge is one too).
+struct BatchPlan {
+    std::vector<G2Task> prio, bulk;
+    std::vector<int4> tct;            // (i, j, k, problem)
+    std::vector<std::vector<int>> trsm_end;
+    int per = 1;                      // tensor items per target (largest over the problems)
+};
+void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, BatchPlan& out);
+// point P's counters into a block of P.g.n_counters - 16 ints
+void bind_counters(ProbDev& P, int* base);
+// probs: nprob device views in global memory (their counters inside `counters`,
+// zeroed by this call), queues in device memory as laid out by the caller.
+cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
+                                const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
+                                int* counters, size_t counter_bytes, cudaStream_t s);
 
 }  // namespace geo

@@ -69,6 +69,25 @@ struct MaternP {
 
 MaternP make_matern(const geo_theta& th);
 
+// Eq. 2 from the log-determinant and the quadratic form (one expression for the
+// host and the device, so both give the same bits).
+constexpr double GEO_LOG_2PI = 1.8378770664093454835606594728112;
+__host__ __device__ inline double assemble_loglik(int n, double logdet, double quad) {
+#ifdef __CUDA_ARCH__
+    // no contraction into FMAs: the same roundings as the host's
+    const double a = __dmul_rn(__dmul_rn(-0.5, (double)n), GEO_LOG_2PI);
+    return __dsub_rn(__dsub_rn(a, __dmul_rn(0.5, logdet)), __dmul_rn(0.5, quad));
+#else
+    return -0.5 * (double)n * GEO_LOG_2PI - 0.5 * logdet - 0.5 * quad;
+#endif
+}
+
+// One problem of a batched solve: its layout (the factored store) and Z.
+struct SolveJob {
+    Layout L;
+    const double* z;
+};
+
 Layout make_layout(const geo_tiles* t);
 
 // Instrumentation (api.cu): a launch counter and optional event timing of
@@ -79,8 +98,8 @@ void prof_begin(int kind, cudaStream_t s);
 void prof_end(int kind, cudaStream_t s);
 
 // Launchers (defined in their own .cu files; all asynchronous on `s`).
-cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* y, const MaternP& mp,
-                                cudaStream_t s);
+cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* y, const geo_theta& th,
+                                const geo_theta* dth, int reset_status, cudaStream_t s);
 cudaError_t launch_load_dense(const Layout& L, const double* a, cudaStream_t s);
 cudaError_t launch_to_dense(const Layout& L, double* out, cudaStream_t s);
 cudaError_t run_potrf_mp(const geo_tiles* t, const Layout& L, cudaStream_t s);
@@ -88,6 +107,7 @@ cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, do
                             cudaStream_t s);
 cudaError_t run_logdet_trsv_noalloc(const Layout& L, const double* z, double* logdet, double* quad,
                                     cudaStream_t s);
+cudaError_t launch_trsv_batch(const SolveJob* d_jobs, int nprob, double* out, cudaStream_t s);
 cudaError_t run_krige(const Layout& L, const double* x, const double* y, const double* z, const MaternP& mp,
                       const double* xn, const double* yn, int m, double* zhat, double* work, cudaStream_t s);
 

@@ -48,8 +48,18 @@ MaternP make_matern(const geo_theta& th) {
 constexpr int GEN_THREADS = 256;
 constexpr int GEN_COLS = 32;
 
+// theta: from `dth` when given (device memory: batched evaluations), else `th`.
+// With reset_status, the first CTA also clears the problem's status words (the
+// batched path has no separate reset).
 __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, const double* __restrict__ x,
-                                                                   const double* __restrict__ y, MaternP mp) {
+                                                                   const double* __restrict__ y, geo_theta th,
+                                                                   const geo_theta* __restrict__ dth,
+                                                                   int reset_status) {
+    __shared__ MaternP smp;
+    if (threadIdx.x == 0) smp = make_matern_dev(dth ? *dth : th);
+    if (reset_status && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < ST_WORDS) L.status[threadIdx.x] = 0;
+    __syncthreads();
+    const MaternP mp = smp;
     const int nb = L.nb, p = L.p;
     // decode tile index -> (i, j), lower triangle, column-major over tiles
     int t = blockIdx.y, j = 0;
@@ -155,10 +165,10 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
     }
 }
 
-cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* y, const MaternP& mp,
-                                cudaStream_t s) {
+cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* y, const geo_theta& th,
+                                const geo_theta* dth, int reset_status, cudaStream_t s) {
     dim3 grid((L.nb + GEN_COLS - 1) / GEN_COLS, L.p * (L.p + 1) / 2);
-    matern_tiles_kernel<<<grid, GEN_THREADS, 0, s>>>(L, x, y, mp);
+    matern_tiles_kernel<<<grid, GEN_THREADS, 0, s>>>(L, x, y, th, dth, reset_status);
     count_launch();
     return cudaGetLastError();
 }

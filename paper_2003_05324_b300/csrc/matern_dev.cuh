@@ -5,6 +5,24 @@
 
 namespace geo {
 
+// Parameters of Eq. 1 prepared for the entry functions below (device side, so
+// that a batched launch can read theta from device memory and a single launch
+// computes exactly the same values): kind selects a closed form for nu in
+// {1/2, 3/2, 5/2}; log_c = (nu - 1) log 2 + log Gamma(nu).
+__device__ __forceinline__ MaternP make_matern_dev(const geo_theta& th) {
+    MaternP m;
+    m.sigma2 = th.sigma2;
+    m.inv_beta = 1.0 / th.beta;
+    m.nu = th.nu;
+    m.nugget = th.nugget;
+    m.log_c = (th.nu - 1.0) * 0.69314718055994530942 + lgamma(th.nu);
+    m.kind = 0;
+    if (th.nu == 0.5) m.kind = 1;
+    else if (th.nu == 1.5) m.kind = 2;
+    else if (th.nu == 2.5) m.kind = 3;
+    return m;
+}
+
 // e^x K_nu(x), FP64, x > 0.
 __device__ __forceinline__ double ekv_fp64(double nu, double x) {
     const double h = fmin(0.2, 0.45 * rsqrt(x));

@@ -19,10 +19,9 @@ constexpr int SV_THREADS = 256;
 constexpr int SV_BS = 32;
 
 // Solve L_ii y_i = r_i in place (r_i already holds Z_i minus the earlier block
-// rows' contributions); record sum log L_aa and sum y_a^2 of this tile.
-__global__ void __launch_bounds__(SV_THREADS) trsv_diag_kernel(Layout L, int i, double* __restrict__ yv,
-                                                               double* __restrict__ part) {
-    if (failed(L)) return;
+// rows' contributions); record sum log L_aa and sum y_a^2 of this tile.  One
+// CTA of SV_THREADS threads.
+__device__ void trsv_diag_tile(const Layout& L, int i, double* __restrict__ yv, double* __restrict__ part) {
     const int nb = L.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double* A = dp_tile(L, i, i);
     double* y = yv + (size_t)i * nb;
@@ -84,6 +83,26 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_diag_kernel(Layout L, int i, 
     }
 }
 
+__global__ void __launch_bounds__(SV_THREADS) trsv_diag_kernel(Layout L, int i, double* __restrict__ yv,
+                                                               double* __restrict__ part) {
+    if (failed(L)) return;
+    trsv_diag_tile(L, i, yv, part);
+}
+
+// r-th row of y_l -= L(l,i) y_i (yi: y_i, FP64 accumulation in column order)
+__device__ __forceinline__ double trsv_row_update(const Layout& L, int l, int i, int r, const double* yi) {
+    const int nb = L.nb;
+    double acc = 0.0;
+    if (is_dp(l, i, L.band)) {
+        const double* A = dp_tile(L, l, i);
+        for (int c = 0; c < nb; ++c) acc = fma(A[(size_t)c * nb + r], yi[c], acc);
+    } else {
+        const float* A = sp_tile(L, l, i);
+        for (int c = 0; c < nb; ++c) acc = fma((double)A[(size_t)c * nb + r], yi[c], acc);
+    }
+    return acc;
+}
+
 constexpr int GV_ROWS = 128;
 
 // y_l -= L(l,i) y_i for every block row l > i.
@@ -96,15 +115,7 @@ __global__ void __launch_bounds__(GV_ROWS) trsv_update_kernel(Layout L, int i, d
     for (int c = threadIdx.x; c < nb; c += GV_ROWS) yi[c] = yv[(size_t)i * nb + c];
     __syncthreads();
     if (r >= nb) return;
-    double acc = 0.0;
-    if (is_dp(l, i, L.band)) {
-        const double* A = dp_tile(L, l, i);
-        for (int c = 0; c < nb; ++c) acc = fma(A[(size_t)c * nb + r], yi[c], acc);
-    } else {
-        const float* A = sp_tile(L, l, i);
-        for (int c = 0; c < nb; ++c) acc = fma((double)A[(size_t)c * nb + r], yi[c], acc);
-    }
-    yv[(size_t)l * nb + r] -= acc;
+    yv[(size_t)l * nb + r] -= trsv_row_update(L, l, i, r, yi);
 }
 
 __global__ void trsv_load_kernel(Layout L, const double* __restrict__ z, double* __restrict__ yv) {
@@ -134,6 +145,51 @@ static cudaError_t forward_solve(const Layout& L, double* yv, double* part, cuda
             count_launch();
         }
     }
+    return cudaGetLastError();
+}
+
+// Batched A10-A12: one CTA per problem runs its whole forward solve with the
+// same per-element arithmetic, in the same order, as the per-tile kernels
+// above (so a problem's result is the same alone and in a batch), then
+// assembles Eq. 2: out = (l, log|Sigma|, Z' Sigma^-1 Z), NaN for a problem
+// whose factorization failed.
+__global__ void __launch_bounds__(SV_THREADS) trsv_batch_kernel(const SolveJob* __restrict__ jobs,
+                                                                double* __restrict__ out_all) {
+    const SolveJob& J = jobs[blockIdx.x];
+    double* out = out_all + 3 * (size_t)blockIdx.x;
+    const Layout& L = J.L;
+    const int p = L.p, nb = L.nb, tid = threadIdx.x;
+    double* yv = L.scal + 2 * p + 8;
+    double* part = L.scal;
+    if (failed(L)) {
+        if (tid < 3) out[tid] = nan("");
+        return;
+    }
+    for (int g = tid; g < p * nb; g += SV_THREADS) yv[g] = g < L.n ? J.z[g] : 0.0;
+    __syncthreads();
+    for (int i = 0; i < p; ++i) {
+        trsv_diag_tile(L, i, yv, part);
+        __syncthreads();
+        const double* yi = yv + (size_t)i * nb;
+        for (int l = i + 1; l < p; ++l)
+            for (int r = tid; r < nb; r += SV_THREADS) yv[(size_t)l * nb + r] -= trsv_row_update(L, l, i, r, yi);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int i = 0; i < p; ++i) {
+            s0 += part[2 * i];
+            s1 += part[2 * i + 1];
+        }
+        out[0] = assemble_loglik(L.n, s0, s1);
+        out[1] = s0;
+        out[2] = s1;
+    }
+}
+
+cudaError_t launch_trsv_batch(const SolveJob* d_jobs, int nprob, double* out, cudaStream_t s) {
+    trsv_batch_kernel<<<nprob, SV_THREADS, 0, s>>>(d_jobs, out);
+    count_launch();
     return cudaGetLastError();
 }
 

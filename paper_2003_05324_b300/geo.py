@@ -78,6 +78,11 @@ class geo_mle_result(ctypes.Structure):
                 ("iterations", ctypes.c_int), ("not_spd", ctypes.c_int)]
 
 
+class geo_batch_item(ctypes.Structure):
+    _fields_ = [("t", ctypes.POINTER(geo_tiles)), ("d_x", ctypes.c_void_p), ("d_y", ctypes.c_void_p),
+                ("d_z", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libgeo.so not built at {LIB_PATH}; run paper_2003_05324_b300/build.py")
@@ -99,6 +104,9 @@ def _load():
         "geo_status": [ctypes.POINTER(geo_tiles), ctypes.POINTER(I), ctypes.POINTER(I), P],
         "geo_loglik": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, ctypes.POINTER(D), ctypes.POINTER(I), P],
         "geo_krige": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, P, P, I, P, P, P],
+        "geo_batch_workspace": [I, ctypes.POINTER(geo_batch_item), ctypes.POINTER(ctypes.c_size_t)],
+        "geo_batch_bind": [I, ctypes.POINTER(geo_batch_item), P, ctypes.c_size_t, P],
+        "geo_loglik_batch": [I, ctypes.POINTER(geo_batch_item), P, P, P, P],
         "geo_mle_default_opts": [ctypes.POINTER(geo_mle_opts)],
         "geo_mle": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, ctypes.POINTER(geo_mle_opts),
                     ctypes.POINTER(geo_mle_result), P],
@@ -354,3 +362,85 @@ def mle(x, y, z, theta0: Theta, nb: int, band: int, lp_mode: int = GEO_LP_SPLIT_
     if flags:
         ts.set_flags(flags)
     return ts.mle(x, y, z, theta0, **kw)
+
+
+class Batch:
+    """Many log-likelihood problems evaluated through one persistent
+    factorization launch (geo_loglik_batch).
+
+    problems: list of dicts with device tensors x, y, z (Morton-ordered) and
+    optional nb (default 128), band (default 1), flags.  The stores, the
+    workspace and the per-problem theta buffer are allocated once; each
+    evaluation only enqueues work, so `capture()` can record it in a CUDA graph
+    and `replay(thetas)` re-runs it with new parameters.
+    """
+
+    def __init__(self, problems, nb: int = 128, band: int = 1, device="cuda"):
+        import torch
+        self.device = torch.device(device)
+        self.stores, self._keep = [], []
+        n = len(problems)
+        self.items = (geo_batch_item * n)()
+        for b, pr in enumerate(problems):
+            x, y, z = pr["x"], pr["y"], pr["z"]
+            ts = TileStore(int(z.shape[0]), int(pr.get("nb", nb)), int(pr.get("band", band)), GEO_LP_SPLIT_BF16,
+                           device=self.device)
+            if pr.get("flags"):
+                ts.set_flags(int(pr["flags"]))
+            self.stores.append(ts)
+            self._keep.append((x, y, z))
+            self.items[b].t = ctypes.pointer(ts.t)
+            self.items[b].d_x, self.items[b].d_y, self.items[b].d_z = _ptr(x), _ptr(y), _ptr(z)
+        self.nprob = n
+        nbytes = ctypes.c_size_t(0)
+        _check(lib.geo_batch_workspace(n, self.items, ctypes.byref(nbytes)), "geo_batch_workspace")
+        self._work = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=self.device)
+        _check(lib.geo_batch_bind(n, self.items, _ptr(self._work), int(nbytes.value), _stream()), "geo_batch_bind")
+        self.theta = torch.zeros((n, 4), dtype=torch.float64, device=self.device)
+        self.out = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
+        self.graph = None
+
+    def set_theta(self, thetas):
+        import torch
+        t = torch.tensor([[th.sigma2, th.beta, th.nu, th.nugget] for th in thetas], dtype=torch.float64)
+        self.theta.copy_(t, non_blocking=False)
+
+    def loglik_async(self, stream=None):
+        """Enqueue one evaluation with the parameters in self.theta; results land
+        in self.out[b] = (l, log|Sigma|, Z' Sigma^-1 Z), NaN where not SPD."""
+        _check(lib.geo_loglik_batch(self.nprob, self.items, _ptr(self.theta), _ptr(self._work), _ptr(self.out),
+                                    _stream(stream)), "geo_loglik_batch")
+        return self.out
+
+    def loglik(self, thetas):
+        import torch
+        self.set_theta(thetas)
+        self.loglik_async()
+        torch.cuda.synchronize(self.device)
+        return self.out.cpu().numpy().copy()
+
+    def capture(self):
+        """Record one evaluation in a CUDA graph (after a warm-up evaluation)."""
+        import torch
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            self.loglik_async(s)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.loglik_async()
+        self.graph = g
+        return g
+
+    def replay(self, thetas=None):
+        import torch
+        if thetas is not None:
+            self.set_theta(thetas)
+        self.graph.replay()
+        torch.cuda.synchronize(self.device)
+        return self.out.cpu().numpy().copy()
+
+    def status(self):
+        return [ts.status() for ts in self.stores]

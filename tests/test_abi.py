@@ -73,6 +73,14 @@ def test_entry_points_reject_null_arguments_without_device_work():
     assert L.geo_tiles_bind(None, None, None, None, None, None, None) == -1
     assert L.geo_morton_order(None, None, 3, None) == -1
     assert L.geo_mle(None, None, None, None, th, None, None, None) == -1
+    nbytes = ctypes.c_size_t(0)
+    assert L.geo_batch_workspace(0, None, ctypes.byref(nbytes)) == -1
+    assert L.geo_batch_workspace(1, None, ctypes.byref(nbytes)) == -2
+    items = (geo.geo_batch_item * 1)()
+    items[0].t = ctypes.pointer(t)                 # unbound store: rejected before any device work
+    assert L.geo_batch_workspace(1, items, ctypes.byref(nbytes)) == -2
+    assert L.geo_batch_bind(1, items, None, 0, None) == -2
+    assert L.geo_loglik_batch(1, items, None, None, None, None) == -3
     assert L.geo_mle_default_opts(None) == -1
 
 
