@@ -267,7 +267,8 @@ int geo_mle(geo_tiles* t, const double* d_x, const double* d_y, const double* d_
  *   batched log-det / solve / assembly into d_out[3b .. 3b+2] = (l, log|Sigma|,
  *   Z' Sigma^-1 Z); NaN for a problem that is not positive definite (its
  *   store's status says which row).  A launch-wide timeout marks every problem
- *   with GEO_ERR_TIMEOUT.
+ *   with GEO_ERR_TIMEOUT.  A trace enabled on the first item's store
+ *   (geo_tiles_set_trace) records the tasks of all problems.
  * All return 0, -k for a bad argument k, or GEO_ERR_CUDA. */
 typedef struct geo_batch_item {
     geo_tiles* t;

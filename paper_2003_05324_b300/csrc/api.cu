@@ -484,7 +484,7 @@ struct BatchMeta {
     int nprob;
     size_t off_probs, off_jobs, off_maps, off_tend, off_prio, off_bulk, off_tct, off_ctr, total;
     long long n_prio, n_bulk, n_tct;
-    int per;
+    int per, pmax;
     size_t counter_bytes;
 };
 std::mutex g_batch_mu;
@@ -502,6 +502,7 @@ int batch_meta(int nprob, const geo_batch_item* items, BatchMeta& m, std::vector
     long long ptot = 0, ctot = 16;
     m.n_prio = m.n_bulk = m.n_tct = 0;
     m.per = 1;
+    m.pmax = 0;
     for (int b = 0; b < nprob; ++b) {
         const geo_batch_item& it = items[b];
         if (!it.t || !it.t->d_meta || !it.d_x || !it.d_y || !it.d_z) return -2;
@@ -510,6 +511,7 @@ int batch_meta(int nprob, const geo_batch_item* items, BatchMeta& m, std::vector
         const SchedGeom& g = mo.geom[batch_variant(it.t)];
         if (geoms) geoms->push_back(g);
         ptot += g.p;
+        m.pmax = std::max(m.pmax, g.p);
         ctot += g.n_counters - 16;
         m.n_prio += g.n_prio;
         m.n_bulk += g.n_bulk;
@@ -643,9 +645,11 @@ int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_
     if (run_potrf_dag_batch((const ProbDev*)(base + m.off_probs), nprob, (const G2Task*)(base + m.off_prio),
                             m.n_prio, (const G2Task*)(base + m.off_bulk), m.n_bulk,
                             (const int4*)(base + m.off_tct), m.n_tct, m.per, (int*)(base + m.off_ctr),
-                            m.counter_bytes, s))
+                            m.counter_bytes, items[0].t->trace, items[0].t->trace_cap, s))
         return GEO_ERR_CUDA;
-    if (launch_trsv_batch((const SolveJob*)(base + m.off_jobs), nprob, d_out, s)) return GEO_ERR_CUDA;
+    if (launch_trsv_batch((const SolveJob*)(base + m.off_jobs), nprob, m.pmax, d_out,
+                          (unsigned*)(base + m.off_ctr) + 8, s))
+        return GEO_ERR_CUDA;
     return GEO_OK;
 }
 

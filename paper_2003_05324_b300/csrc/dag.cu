@@ -1304,7 +1304,8 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
         pmax = std::max(pmax, g[(size_t)b].p);
     }
     // every queue of a problem is ordered by step; step k of all problems
-    // precedes step k+1 of any
+    // precedes step k+1 of any (staggering the problems' steps against each
+    // other was measured to make no difference)
     std::vector<size_t> ip((size_t)nprob, 0), ib((size_t)nprob, 0), it((size_t)nprob, 0);
     for (int k = 0; k < pmax; ++k) {
         for (int b = 0; b < nprob; ++b) {
@@ -1340,7 +1341,8 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
 
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
                                 const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
-                                int* counters, size_t counter_bytes, cudaStream_t s) {
+                                int* counters, size_t counter_bytes, void* trace, long long trace_cap,
+                                cudaStream_t s) {
     int nsm = 0;
     cudaError_t e = dag_prepare(nsm);
     if (e) return e;
@@ -1356,6 +1358,9 @@ cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task*
     A.per = per;
     A.n_tc_items = n_tct * (long long)per;
     A.ctr = counters;
+    A.trace_ctr = (unsigned long long*)trace;
+    A.trace = trace ? (geo_trace_rec*)((char*)trace + 64) : nullptr;
+    A.trace_cap = trace_cap;
     (void)nprob;
     CUtensorMap maps[3];
     memset(maps, 0, sizeof(maps));   // unused: each problem's maps are in its view

@@ -67,6 +67,7 @@ void bind_counters(ProbDev& P, int* base);
 // zeroed by this call), queues in device memory as laid out by the caller.
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
                                 const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
-                                int* counters, size_t counter_bytes, cudaStream_t s);
+                                int* counters, size_t counter_bytes, void* trace, long long trace_cap,
+                                cudaStream_t s);
 
 }  // namespace geo

@@ -107,7 +107,9 @@ cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, do
                             cudaStream_t s);
 cudaError_t run_logdet_trsv_noalloc(const Layout& L, const double* z, double* logdet, double* quad,
                                     cudaStream_t s);
-cudaError_t launch_trsv_batch(const SolveJob* d_jobs, int nprob, double* out, cudaStream_t s);
+// bar: 4 unsigned of device scratch for the launch's grid barrier
+cudaError_t launch_trsv_batch(const SolveJob* d_jobs, int nprob, int pmax, double* out, unsigned* bar,
+                              cudaStream_t s);
 cudaError_t run_krige(const Layout& L, const double* x, const double* y, const double* z, const MaternP& mp,
                       const double* xn, const double* yn, int m, double* zhat, double* work, cudaStream_t s);
 
