@@ -369,7 +369,8 @@ class Batch:
     factorization launch (geo_loglik_batch).
 
     problems: list of dicts with device tensors x, y, z (Morton-ordered) and
-    optional nb (default 128), band (default 1), flags.  The stores, the
+    optional nb (default 128), band (default 1), flags, or an existing
+    `store` (TileStore of split-BF16 mode) to evaluate in.  The stores, the
     workspace and the per-problem theta buffer are allocated once; each
     evaluation only enqueues work, so `capture()` can record it in a CUDA graph
     and `replay(thetas)` re-runs it with new parameters.
@@ -383,10 +384,12 @@ class Batch:
         self.items = (geo_batch_item * n)()
         for b, pr in enumerate(problems):
             x, y, z = pr["x"], pr["y"], pr["z"]
-            ts = TileStore(int(z.shape[0]), int(pr.get("nb", nb)), int(pr.get("band", band)), GEO_LP_SPLIT_BF16,
-                           device=self.device)
-            if pr.get("flags"):
-                ts.set_flags(int(pr["flags"]))
+            ts = pr.get("store")   # an existing split-BF16 store of this size may be reused
+            if ts is None:
+                ts = TileStore(int(z.shape[0]), int(pr.get("nb", nb)), int(pr.get("band", band)), GEO_LP_SPLIT_BF16,
+                               device=self.device)
+                if pr.get("flags"):
+                    ts.set_flags(int(pr["flags"]))
             self.stores.append(ts)
             self._keep.append((x, y, z))
             self.items[b].t = ctypes.pointer(ts.t)
@@ -399,6 +402,10 @@ class Batch:
         self.theta = torch.zeros((n, 4), dtype=torch.float64, device=self.device)
         self.out = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
         self.graph = None
+
+    def nbytes(self) -> int:
+        """Device bytes of the batch workspace (the stores not included)."""
+        return int(self._work.numel())
 
     def set_theta(self, thetas):
         import torch
