@@ -81,7 +81,10 @@ class Server:
             if d.get("krige", True):
                 krig = geo.TileStore(n, nbd, band, geo.GEO_LP_SPLIT_BF16, device=self.device)
                 krig.matern(X, Y, d["theta"])
-                krig.potrf()
+                try:
+                    krig.potrf()
+                except geo.NotSPDError:
+                    krig = None        # no resident factor: its kriging requests are rejected
             self.ds.append(dict(x=X, y=Y, z=Z, n=n, nb=nbd, theta=d["theta"], krig=krig,
                                 bytes=store_bytes(n, nbd, band)))
         self.resident_bytes = sum(d["bytes"] for d in self.ds if d["krig"] is not None)
