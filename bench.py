@@ -55,6 +55,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, world, dev):
+    """The slowest rank's time of the timed region (every rank holds the same
+    number of independent evaluations: replicas)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ms, world, steps, flops_per_eval):
+    """Whole-job evals/s and TFLOP/s: the evaluations of all ranks over the
+    slowest rank's time."""
+    sec = ms / 1000.0
+    return world * steps / sec, world * flops_per_eval * steps / sec / 1e12
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -480,16 +498,12 @@ def main():
     launches = geo.kernel_launches() - launches0
     ms = ev0.elapsed_time(ev1)
     step_ms = [step_ev[i].elapsed_time(step_ev[i + 1]) for i in range(args.steps)]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     code, info = ts.status()
     if code != 0:
         raise SystemExit(f"device status {code} (info {info}) in the timed region")
     ms_step = ms / args.steps
-    evals_per_s = world * args.steps / (ms / 1000.0)
-    tflops = world * flops * args.steps / (ms / 1000.0) / 1e12
+    evals_per_s, tflops = replica_throughput(ms, world, args.steps, flops)
 
     # per-kernel live timings (CUDA events on each kernel's own stream)
     kern = {kind: geo.profile_read(kind) for kind in range(5)}

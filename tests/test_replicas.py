@@ -1,0 +1,61 @@
+"""The multi-GPU path of the benchmark is replicas only (one factorization
+does not shard without a panel exchange per step): every rank runs the same
+evaluations, the timed region's time is the maximum over ranks and the
+throughput counts the evaluations of all ranks.  Checked here with two gloo
+ranks on the CPU."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local_ms = [120.0, 180.0][rank]
+    ms = bench.max_over_ranks(local_ms, world, "cpu")
+    evals, tflops = bench.replica_throughput(ms, world, 5, 2.0e13)
+    q.put((rank, ms, evals, tflops))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_replicas_take_the_slowest_rank_and_sum_the_work():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    out = sorted(q.get(timeout=120) for _ in range(world))
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    for rank, ms, evals, tflops in out:
+        assert ms == 180.0                                  # the slowest rank
+        assert abs(evals - 2 * 5 / 0.18) < 1e-9             # evaluations of both ranks
+        assert abs(tflops - 2 * 5 * 2.0e13 / 0.18 / 1e12) < 1e-6
+
+
+def test_single_rank_is_unchanged():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(42.0, 1, "cpu") == 42.0
+    evals, tflops = bench.replica_throughput(500.0, 1, 5, 2.0e13)
+    assert abs(evals - 10.0) < 1e-12 and abs(tflops - 200.0) < 1e-9
