@@ -1141,10 +1141,9 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                             const int ec[8] = {ea.x, ea.y, ea.z, ea.w, ebb.x, ebb.y, ebb.z, ebb.w};
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
-                                double d = (double)v[0][e];
-#pragma unroll
-                                for (int a = 1; a < EX_NACC; ++a) d += (double)v[a][e];
-                                cpre[e] = fma(-d, pow2d(er + ec[e] - 16), cpre[e]);
+                                const long long tot = ex_fixed_total(v[0][e], v[1][e], v[2][e], v[3][e], v[4][e],
+                                                                     v[5][e], v[6][e]);
+                                cpre[e] = fma(-(double)tot, pow2d(er + ec[e] - 56), cpre[e]);
                             }
 #pragma unroll
                             for (int e = 0; e < 8; ++e)

@@ -46,6 +46,7 @@ constexpr uint32_t EX_P1_BYTES = 4 * TC_A_BYTES + 7 * EX_B_BYTES;
 constexpr uint32_t EX_P2_BYTES = 3 * TC_A_BYTES + 3 * EX_B_BYTES;
 static_assert(EX_P1_BYTES <= (uint32_t)TC_STAGE_BYTES, "EX stage");
 static_assert(EX_NACC * EX_BN <= 4 * TC_BN, "EX accumulators");
+static_assert(EX_NACC == 7, "ex_fixed_total sums levels 0..4 (acc 0..5) and the level-5/6 accumulator");
 // (A slice, B slice, accumulator); pass 2's A slice index counts from slice 4
 __constant__ signed char c_ex1[EX_P1_PAIRS][3] = {
     {0, 0, 0},                                                       // level 0
@@ -200,6 +201,25 @@ __device__ __forceinline__ void slice_value(T v, int e, __nv_bfloat16* out) {
         t = (t - a) * (T)256;
         w *= (1.0f / 256.0f);
     }
+}
+
+// The seven in-band accumulators of one output as one exact fixed-point sum, in
+// units of 2^-40 of the level-0 unit.  Accumulator L <= 4 holds integers times
+// 2^-8L below 2^24 in magnitude (exact), so I_L = acc_L 2^8L is an exact
+// float-to-int conversion; the shared level-5/6 accumulator is rounded to the
+// nearest unit (2^-40, below its own FP32 accumulation error).  |level 0| <=
+// 2^22 bounds the total by 2^62 (1 + 2^-7 + ...) < 2^63.  Integer arithmetic
+// replaces the seven FP64 additions: on this part the FP64 pipe runs at 1/71
+// of the FP32 rate, and one conversion of the total to FP64 is left.
+__device__ __forceinline__ long long ex_fixed_total(float a0, float a1, float a2, float a3, float a4, float a5,
+                                                    float a56) {
+    const long long i0 = __float2int_rn(a0);
+    const long long i1 = __float2int_rn(a1 * 256.0f);
+    const long long i2 = __float2int_rn(a2 * 65536.0f);
+    const long long i3 = __float2int_rn(a3 * 16777216.0f);
+    const long long i4 = (long long)(__float2int_rn(a4 * 4294967296.0f) + __float2int_rn(a5 * 4294967296.0f));
+    const long long i56 = __float2int_rn(a56 * 1099511627776.0f);
+    return (i0 << 40) + (i1 << 32) + (i2 << 24) + (i3 << 16) + (i4 << 8) + i56;
 }
 
 // row scale exponent of a row whose largest magnitude (rounded to float) is m
