@@ -202,6 +202,18 @@ int geo_logdet_trsv_noalloc(const geo_tiles* t, const double* d_z, double* d_log
  * a GEO_ERR_* code, *h_info = 1-based failing row for GEO_ERR_NOT_SPD. */
 int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream);
 
+/* A2-A11: generation, Algorithm 1, log-determinant and forward solve of Eq. 2
+ * (Section III, Eq. 1-2; Algorithm 1), enqueued on `stream` without waiting.
+ * d_res (caller-owned device FP64[2]) receives log|Sigma| and Z' Sigma^-1 Z;
+ * Eq. 2 is then -n/2 log(2 pi) - d_res[0]/2 - d_res[1]/2.  d_x, d_y, d_z:
+ * device FP64[n], Morton-ordered, read only.  On the persistent tile-DAG path
+ * (split-BF16 stores) the forward solve runs inside the factorization launch,
+ * per element the same arithmetic as geo_logdet_trsv.  A failure (not positive
+ * definite, timeout) is recorded in the status words (geo_status) and leaves
+ * d_res undefined.  Returns GEO_OK or a negative argument index / GEO_ERR_CUDA. */
+int geo_loglik_async(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta,
+                     double* d_res, void* stream);
+
 /* A2-A12: full evaluation of Eq. 2 (generation, Algorithm 1, log-det, solve,
  * assembly).  Blocking: returns after the scalars are on the host.
  * h_out[0] = l(theta), h_out[1] = log|Sigma|, h_out[2] = Z' Sigma^-1 Z.

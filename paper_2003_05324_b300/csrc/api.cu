@@ -23,7 +23,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // tasks, bulk tasks, solve ends, tensor targets
 struct MetaOffsets {
     size_t off, slot, status, scal, sched_ctr, total;
-    size_t sched_g2[2], sched_bulk[2], sched_end[2], sched_tct[2];
+    size_t sched_g2[2], sched_bulk[2], sched_end[2], sched_tct[2], sched_y[2];
     SchedGeom geom[2];
     bool dag;
 };
@@ -43,7 +43,7 @@ static MetaOffsets meta_offsets(int p, int nb, int band, int lp_mode, int pp) {
     m.sched_ctr = b;
     for (int v = 0; v < 2; ++v) {
         m.geom[v] = sched_geom(p, nb, band, pp, v == 0);
-        m.sched_g2[v] = m.sched_bulk[v] = m.sched_end[v] = m.sched_tct[v] = b;
+        m.sched_g2[v] = m.sched_bulk[v] = m.sched_end[v] = m.sched_tct[v] = m.sched_y[v] = b;
     }
     if (m.dag) {
         b = align256(b + sizeof(int) * (size_t)m.geom[0].n_counters);
@@ -57,6 +57,8 @@ static MetaOffsets meta_offsets(int p, int nb, int band, int lp_mode, int pp) {
             b = align256(b + sizeof(int) * (size_t)p);
             m.sched_tct[v] = b;
             b = align256(b + sizeof(int4) * (size_t)std::max(g.n_tct, 1LL));
+            m.sched_y[v] = b;
+            b = align256(b + sizeof(G2Task) * (size_t)std::max(g.n_y, 1LL));
         }
     }
     m.total = b;
@@ -243,11 +245,11 @@ int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp, 
         }
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(d_meta, host.data(), mo.scal, cudaMemcpyHostToDevice, s);
-    std::vector<G2Task> prio, bulk;
+    std::vector<G2Task> prio, bulk, yq;
     std::vector<int> trsm_end;
     std::vector<int4> tct;
     for (int v = 0; v < 2 && !e && mo.dag; ++v) {
-        sched_build(mo.geom[v], lay->band, prio, bulk, trsm_end, tct);
+        sched_build(mo.geom[v], lay->band, prio, bulk, trsm_end, yq, tct);
         if (!prio.empty())
             e = cudaMemcpyAsync((char*)d_meta + mo.sched_g2[v], prio.data(), sizeof(G2Task) * prio.size(),
                                 cudaMemcpyHostToDevice, s);
@@ -259,6 +261,9 @@ int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp, 
                                 cudaMemcpyHostToDevice, s);
         if (!e && !tct.empty())
             e = cudaMemcpyAsync((char*)d_meta + mo.sched_tct[v], tct.data(), sizeof(int4) * tct.size(),
+                                cudaMemcpyHostToDevice, s);
+        if (!e && !yq.empty())
+            e = cudaMemcpyAsync((char*)d_meta + mo.sched_y[v], yq.data(), sizeof(G2Task) * yq.size(),
                                 cudaMemcpyHostToDevice, s);
         if (!e) e = cudaStreamSynchronize(s);   // the host vectors are reused for the next variant
     }
@@ -338,7 +343,13 @@ static int reset_status(const Layout& L, cudaStream_t s) {
                                                                                                  : GEO_OK;
 }
 
-static cudaError_t factor(const geo_tiles* t, const Layout& L, cudaStream_t s) {
+// Algorithm 1 on the store.  With z, the persistent tile-DAG path also runs the
+// forward solve of Eq. 2 inside the same launch and writes (log|Sigma|,
+// Z' Sigma^-1 Z) to res; *solved tells the caller whether that happened (the
+// step-by-step paths leave the solve to run_logdet_trsv).
+static cudaError_t factor(const geo_tiles* t, const Layout& L, const double* z, double* res, bool* solved,
+                          cudaStream_t s) {
+    *solved = false;
     if (L.lp_mode == GEO_LP_SPLIT_BF16 && !(t->flags & GEO_FLAG_STEPWISE)) {
         MetaOffsets mo = meta_offsets(t->lay);
         // in-band updates on the tensor cores unless the FP64 pipe is asked for
@@ -352,7 +363,9 @@ static cudaError_t factor(const geo_tiles* t, const Layout& L, cudaStream_t s) {
         sv.bulk = (const G2Task*)(base + mo.sched_bulk[v]);
         sv.trsm_end = (const int*)(base + mo.sched_end[v]);
         sv.tct = (const int4*)(base + mo.sched_tct[v]);
-        return run_potrf_dag(t, L, sv, s);
+        sv.yq = (const G2Task*)(base + mo.sched_y[v]);
+        *solved = z != nullptr;
+        return run_potrf_dag(t, L, sv, z, res, s);
     }
     return run_potrf_mp(t, L, s);
 }
@@ -363,7 +376,8 @@ int geo_potrf_mp(geo_tiles* t, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     int rc = reset_status(L, s);
     if (rc) return rc;
-    return factor(t, L, s) ? GEO_ERR_CUDA : GEO_OK;
+    bool solved = false;
+    return factor(t, L, nullptr, nullptr, &solved, s) ? GEO_ERR_CUDA : GEO_OK;
 }
 
 int geo_logdet_trsv(const geo_tiles* t, const double* d_z, double* d_logdet, double* d_quad, double* d_y,
@@ -402,6 +416,29 @@ int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream) {
     return GEO_OK;
 }
 
+static int loglik_enqueue(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta,
+                          double* d_res, cudaStream_t s) {
+    Layout L = make_layout(t);
+    int rc = reset_status(L, s);
+    if (rc) return rc;
+    if (launch_matern_tiles(L, d_x, d_y, theta, nullptr, 0, s)) return GEO_ERR_CUDA;
+    bool solved = false;
+    if (factor(t, L, d_z, d_res, &solved, s)) return GEO_ERR_CUDA;
+    if (!solved && run_logdet_trsv(L, d_z, d_res, d_res + 1, nullptr, s)) return GEO_ERR_CUDA;
+    return GEO_OK;
+}
+
+int geo_loglik_async(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta,
+                     double* d_res, void* stream) {
+    if (check_bound(t)) return -1;
+    if (!d_x) return -2;
+    if (!d_y) return -3;
+    if (!d_z) return -4;
+    if (check_theta(theta)) return -5;
+    if (!d_res) return -6;
+    return loglik_enqueue(t, d_x, d_y, d_z, theta, d_res, (cudaStream_t)stream);
+}
+
 int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta,
                double* h_out, int* h_info, void* stream) {
     if (check_bound(t)) return -1;
@@ -412,12 +449,9 @@ int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double*
     if (!h_out) return -6;
     Layout L = make_layout(t);
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = reset_status(L, s);
-    if (rc) return rc;
-    if (launch_matern_tiles(L, d_x, d_y, theta, nullptr, 0, s)) return GEO_ERR_CUDA;
-    if (factor(t, L, s)) return GEO_ERR_CUDA;
     double* res = L.scal + 2 * L.p;
-    if (run_logdet_trsv(L, d_z, res, res + 1, nullptr, s)) return GEO_ERR_CUDA;
+    const int rc = loglik_enqueue(t, d_x, d_y, d_z, theta, res, s);
+    if (rc) return rc;
     double hres[2];
     int st[2];
     cudaError_t e = cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, s);

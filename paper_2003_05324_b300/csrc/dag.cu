@@ -50,6 +50,7 @@
 
 #include "dag.cuh"
 #include "tc_common.cuh"
+#include "ysolve.cuh"
 
 namespace geo {
 
@@ -66,11 +67,15 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     g.items_tc = ceil_div(pp, TC_BM) * ceil_div(pp, TC_BN);
     g.chunks_dp = ceil_div(nb, 128);
     g.chunks_sp = ceil_div(nb, 128);
-    // counters: grab counters, upd[p*p], tcnt[p*p], pot[p*ns*ns], sub[p*p*maxitems]
+    g.chunks_y = ceil_div(nb, 128);
+    // counters: grab counters, upd[p*p], tcnt[p*p], pot[p*ns*ns], sub[p*p*maxitems],
+    // ycnt[p*chunks_y], ydone[p]
     g.max_items = std::max(g.items64, g.items_tc);
-    g.n_counters = 16 + 2 * (long long)p * p + (long long)p * g.ns * g.ns + (long long)p * p * g.max_items;
-    long long n_prio = 0, n_bulk = 0, n_tct = 0;
+    g.n_counters = 16 + 2 * (long long)p * p + (long long)p * g.ns * g.ns + (long long)p * p * g.max_items +
+                   (long long)p * g.chunks_y + p;
+    long long n_prio = 0, n_bulk = 0, n_tct = 0, n_y = 0;
     for (int k = 0; k < p; ++k) {
+        n_y += 1 + (long long)(p - k - 1) * g.chunks_y;   // YD(k), YG(i > k, chunks)
         const int ns = g.ns;
         n_prio += ns + ns * (ns - 1) / 2 + (long long)ns * (ns - 1) * (ns + 1) / 6;   // PF, PT, PU
         for (int i = k + 1; i < p; ++i) n_prio += is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
@@ -84,6 +89,7 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     g.n_bulk = n_bulk;
     g.n_g2 = n_prio + n_bulk;
     g.n_tct = n_tct;
+    g.n_y = n_y;
     return g;
 }
 
@@ -91,15 +97,23 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
 // Priority queue: A(k) C(k) for k = 0, 1, ...; bulk queue: B(0) B(1) ...;
 // trsm_end[k] = priority-queue index just past A(k)'s triangular solves.  With
 // in-band updates on the tensor cores (g.ex) every update is a tensor target
-// and the CUDA-core queues hold only the A(k).
+// and the CUDA-core queues hold only the A(k).  Forward-solve queue: Y(0) Y(1)
+// ..., Y(k) = YD(k) then YG(k; i, q) for i = k+1..p-1 -- the forward solve of
+// Eq. 2 fused into the factorization (used only by a launch given Z).
 void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
-                 std::vector<int>& trsm_end, std::vector<int4>& tct) {
+                 std::vector<int>& trsm_end, std::vector<G2Task>& yq, std::vector<int4>& tct) {
     const int p = g.p, ns = g.ns;
     const bool ex = g.ex != 0;
     prio.clear();
     bulk.clear();
     tct.clear();
+    yq.clear();
     trsm_end.assign((size_t)p, 0);
+    for (int k = 0; k < p; ++k) {
+        yq.push_back({T_YD, k, 0, 0, 0});
+        for (int i = k + 1; i < p; ++i)
+            for (int q = 0; q < g.chunks_y; ++q) yq.push_back({T_YG, k, i, q, 0});
+    }
     auto A = [&](int k) {
         for (int s = 0; s < ns; ++s) {
             prio.push_back({T_PF, k, s, 0, 0});
@@ -155,9 +169,11 @@ struct DagArgs {
     long long n_prio, n_bulk;
     const int4* tct;         // tensor targets (i, j, k, problem)
     long long n_tc_items;
+    const G2Task* yq;        // forward-solve queue of a single-problem launch given Z (else n_y = 0)
+    long long n_y;
     int per;                 // tensor items per target
     int* ctr;    // [0] priority head, [1] tensor head, [2] bulk head, [3] workers in priority tasks,
-                 // [4] abort: a wait timed out somewhere
+                 // [4] abort: a wait timed out somewhere, [5] forward-solve head
     unsigned long long* trace_ctr;   // optional task trace (nullptr: off)
     geo_trace_rec* trace;
     long long trace_cap;
@@ -193,6 +209,9 @@ __device__ __forceinline__ void trace_put(const DagArgs& A, int type, int k, int
 }
 
 __device__ __forceinline__ void g2_sync() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+struct G2Sync {
+    __device__ void operator()() const { g2_sync(); }
+};
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Wait until *p >= v (acquire).  False once the problem's status records a
@@ -242,8 +261,10 @@ struct G2Smem {
         struct {
             double Lb[(16 * 32 + 32 * 33) / 2 + 8];  // TRSM: 16 x SB stage + SB x SB diagonal block
         } tr;
+        YSolveSmem yd;                               // YD: diagonal forward solve
+        double yk[YS_MAX_NB];                        // YG: y_k
     };
-    int task, ok;
+    int task, kind, ok;
 };
 
 // PF(k,s): FP64 Cholesky of the 32 x 32 sub-block (s,s), right-looking in
@@ -563,6 +584,22 @@ __device__ void g2_upd(const ProbDev& P, G2Smem& S, int k, int i, int j, int q, 
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
 
+// Dependencies of a forward-solve task, checked without waiting (acquire loads):
+// YD(k) needs L_kk final and every earlier block row's contribution to block
+// row k; YG(k; i, q) needs y_k, the solved tile (i,k) and the contributions of
+// the steps before k to its rows.
+__device__ bool y_ready(const ProbDev& P, const G2Task& t) {
+    const int k = t.k, cy = P.g.chunks_y;
+    if (t.type == T_YD) {
+        if (ld_acquire_s32(pot_at(P, k, P.g.ns - 1, P.g.ns - 1)) < P.g.ns) return false;
+        for (int q = 0; q < cy; ++q)
+            if (ld_acquire_s32(P.ycnt + k * cy + q) < k) return false;
+        return true;
+    }
+    return ld_acquire_s32(P.ydone + k) >= 1 && ld_acquire_s32(P.tcnt + t.a * P.L.p + k) >= chunks_of(P, t.a, k) &&
+           ld_acquire_s32(P.ycnt + t.a * cy + t.b) >= k;
+}
+
 // Stop the whole launch (a wait timed out): the flag every wait polls, and in a
 // single-problem launch that problem's status.
 __device__ void abort_launch(const DagArgs& A, int where) {
@@ -575,16 +612,25 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
     int* prio_head = A.ctr + 0;
     int* bulk_head = A.ctr + 2;
     int* inflight = A.ctr + 3;
+    int* y_head = A.ctr + 5;
     __shared__ long long t_claim, t_ready;
     for (;;) {
-        // ---- claim: priority queue while fewer than PRIO_LIMIT workers are in it,
-        // otherwise the bulk queue once the priority head has passed the solves
-        // its next items need; sleep when neither is available.
+        // ---- claim: the forward-solve queue's head when its dependencies are
+        // met (so it never holds a worker waiting), else the priority queue while
+        // fewer than PRIO_LIMIT workers are in it, otherwise the bulk queue once
+        // the priority head has passed the solves its next items need; sleep
+        // when none is available.
         if (g == 0) {
             int kind = -1, idx = -1;
             const long long dl = gtimer() + DAG_WAIT_NS;
             for (unsigned spin = 0; kind < 0; ++spin) {
                 if (aborted(A) || (!A.probs && failed(A.one.L))) break;
+                const int yh = A.n_y > 0 ? ld_volatile(y_head) : 0;
+                if (yh < A.n_y && y_ready(A.one, A.yq[yh]) && atomicCAS(y_head, yh, yh + 1) == yh) {
+                    idx = yh;
+                    kind = 2;
+                    break;
+                }
                 const int ph = ld_volatile(prio_head);
                 if (ph < A.n_prio) {
                     if (atomicAdd(inflight, 1) < (A.n_bulk > 0 ? PRIO_LIMIT : DAG_THREADS * 4096)) {
@@ -606,8 +652,8 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                             break;
                         }
                     }
-                } else if (ph >= A.n_prio) {
-                    break;   // both queues exhausted
+                } else if (ph >= A.n_prio && yh >= A.n_y) {
+                    break;   // every queue exhausted
                 }
                 __nanosleep(256);
                 if ((spin & 63u) == 63u && gtimer() > dl) {
@@ -615,13 +661,14 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                     break;
                 }
             }
-            S.task = kind < 0 ? -1 : (kind << 30) | idx;
+            S.task = kind < 0 ? -1 : idx;
+            S.kind = kind;
             t_claim = gtimer();
         }
         g2_sync();
         if (S.task < 0) return;
-        const int kind = S.task >> 30, tix = S.task & ((1 << 30) - 1);
-        const G2Task t = kind == 0 ? A.prio[tix] : A.bulk[tix];
+        const int kind = S.kind, tix = S.task;
+        const G2Task t = kind == 0 ? A.prio[tix] : kind == 1 ? A.bulk[tix] : A.yq[tix];
         const ProbDev& P = prob_of(A, t.pid);
         const Layout& L = P.L;
         const int nb = L.nb, ns = P.g.ns;
@@ -651,6 +698,19 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 case T_TRSM:
                     ok = wait_ge(A, L, pot_at(P, k, ns - 1, ns - 1), ns, 20) &&
                          wait_ge(A, L, P.upd + t.a * L.p + k, k * items_of(P, t.a, k), 21);
+                    break;
+                case T_YD:   // L_kk final and every earlier block row's contribution applied
+                    if (P.z) {
+                        ok = wait_ge(A, L, pot_at(P, k, ns - 1, ns - 1), ns, 40);
+                        for (int q = 0; ok && q < P.g.chunks_y; ++q)
+                            ok = wait_ge(A, L, P.ycnt + k * P.g.chunks_y + q, k, 41);
+                    }
+                    break;
+                case T_YG:   // y_k solved, tile (i,k) solved, contributions of steps < k applied
+                    if (P.z)
+                        ok = wait_ge(A, L, P.ydone + k, 1, 42) &&
+                             wait_ge(A, L, P.tcnt + t.a * L.p + k, chunks_of(P, t.a, k), 43) &&
+                             wait_ge(A, L, P.ycnt + t.a * P.g.chunks_y + t.b, k, 44);
                     break;
                 default:   // T_UPD: own sub-block's previous step only
                     ok = wait_ge(A, L, P.tcnt + t.a * L.p + k, chunks_of(P, t.a, k), 22) &&
@@ -699,6 +759,34 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 done = P.tcnt + i * L.p + k;
                 break;
             }
+            case T_YD: {   // y_k = L_kk^-1 r_k (block row 0: r_0 = Z_0); the last one sums the partials
+                if (!P.z) break;
+                const int k = t.k;
+                double* yv = L.scal + 2 * L.p + 8;
+                if (k == 0)
+                    for (int r = g; r < nb; r += G2_THREADS) yv[r] = r < L.n ? P.z[r] : 0.0;
+                g2_sync();
+                ysolve_diag_tile(L, k, yv, L.scal, g, G2_THREADS, S.yd, G2Sync());
+                if (k == L.p - 1 && g == 0) ysolve_finish(L, L.scal, P.res, P.res + 1);
+                done = P.ydone + k;
+                break;
+            }
+            case T_YG: {   // rows of r_i -= L(i,k) y_k (step 0 starts from Z_i)
+                if (!P.z) break;
+                const int i = t.a, k = t.k;
+                double* yv = L.scal + 2 * L.p + 8;
+                for (int c = g; c < nb; c += G2_THREADS) S.yk[c] = yv[(size_t)k * nb + c];
+                g2_sync();
+                const int r = t.b * G2_THREADS + g;
+                if (r < nb) {
+                    const double acc = yrow_update(L, i, k, r, S.yk);
+                    const size_t gi = (size_t)i * nb + r;
+                    const double base = (k == 0) ? (gi < (size_t)L.n ? P.z[gi] : 0.0) : yv[gi];
+                    yv[gi] = base - acc;
+                }
+                done = P.ycnt + i * P.g.chunks_y + t.b;
+                break;
+            }
             default:
                 g2_upd(P, S, t.k, t.a, t.b, t.c, g);
                 done = P.upd + t.a * L.p + t.b;
@@ -707,7 +795,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
         __threadfence();
         g2_sync();
         if (g == 0) {
-            if (ran) {
+            if (ran && done) {   // (no counter: a solve task of a launch without Z)
                 if (t.type == T_UPD) red_release_add(sub_at(P, t.a, t.b, t.c), 1);
                 red_release_add(done, 1);
             }
@@ -1252,9 +1340,12 @@ void bind_counters(ProbDev& P, int* base) {
     P.tcnt = P.upd + (size_t)p * p;
     P.pot = P.tcnt + (size_t)p * p;
     P.sub = P.pot + (size_t)p * P.g.ns * P.g.ns;
+    P.ycnt = P.sub + (size_t)p * p * P.g.max_items;
+    P.ydone = P.ycnt + (size_t)p * P.g.chunks_y;
 }
 
-cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, cudaStream_t s) {
+cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, const double* z, double* res,
+                          cudaStream_t s) {
     int nsm = 0;
     cudaError_t e = dag_prepare(nsm);
     if (e) return e;
@@ -1265,6 +1356,10 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
     A.one.g = sv.geom;
     A.one.trsm_end = sv.trsm_end;
     A.one.tmap = nullptr;
+    A.one.z = z;
+    A.one.res = res;
+    A.yq = z ? sv.yq : nullptr;
+    A.n_y = z ? sv.geom.n_y : 0;
     bind_counters(A.one, sv.counters + 16);
     A.probs = nullptr;
     A.prio = sv.prio;
@@ -1297,10 +1392,11 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
     out.per = 1;
     std::vector<std::vector<G2Task>> prio((size_t)nprob), bulk((size_t)nprob);
     std::vector<std::vector<int>> tend((size_t)nprob);
+    std::vector<G2Task> yq_unused;
     std::vector<std::vector<int4>> tct((size_t)nprob);
     int pmax = 0;
     for (int b = 0; b < nprob; ++b) {
-        sched_build(g[(size_t)b], band[(size_t)b], prio[(size_t)b], bulk[(size_t)b], tend[(size_t)b],
+        sched_build(g[(size_t)b], band[(size_t)b], prio[(size_t)b], bulk[(size_t)b], tend[(size_t)b], yq_unused,
                     tct[(size_t)b]);
         out.trsm_end[(size_t)b].assign((size_t)g[(size_t)b].p, 0);
         out.per = std::max(out.per, g[(size_t)b].items_tc);
@@ -1308,7 +1404,8 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
     }
     // every queue of a problem is ordered by step; step k of all problems
     // precedes step k+1 of any (staggering the problems' steps against each
-    // other was measured to make no difference)
+    // other was measured to make no difference).  A batched launch solves after
+    // the factorization (its own kernel), so the forward-solve queue is unused.
     std::vector<size_t> ip((size_t)nprob, 0), ib((size_t)nprob, 0), it((size_t)nprob, 0);
     for (int k = 0; k < pmax; ++k) {
         for (int b = 0; b < nprob; ++b) {

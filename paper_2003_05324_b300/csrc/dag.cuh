@@ -9,18 +9,20 @@
 
 namespace geo {
 
-enum TaskType : int { T_PF = 0, T_PT = 1, T_PU = 2, T_TRSM = 3, T_UPD = 4 };
+enum TaskType : int { T_PF = 0, T_PT = 1, T_PU = 2, T_TRSM = 3, T_UPD = 4, T_YD = 5, T_YG = 6 };
 
 // One CUDA-core task: PF(k; a = s), PT(k; a = r, b = s), PU(k; a = r, b = c, c = s),
-// TRSM(k; a = i, b = row chunk), UPD(k; a = i, b = j, c = 64 x 64 sub-block);
+// TRSM(k; a = i, b = row chunk), UPD(k; a = i, b = j, c = 64 x 64 sub-block),
+// YD(k) diagonal forward solve of block row k, YG(k; a = i, b = row chunk)
+// r_i -= L(i,k) y_k;
 // pid: the problem it belongs to (0 in a single-problem launch).
 struct G2Task {
     int type, k, a, b, c, pid;
 };
 
 struct SchedGeom {
-    int p, ex, ns, nsb64, items64, items_tc, max_items, chunks_dp, chunks_sp;
-    long long n_counters, n_g2, n_prio, n_bulk, n_tct;
+    int p, ex, ns, nsb64, items64, items_tc, max_items, chunks_dp, chunks_sp, chunks_y;
+    long long n_counters, n_g2, n_prio, n_bulk, n_tct, n_y;
 };
 
 // Device view of the scheduler's tables inside the meta buffer.
@@ -31,15 +33,19 @@ struct SchedView {
     const G2Task* bulk;  // CUDA-core bulk queue, in order
     const int* trsm_end; // [p] priority index past A(k)'s solves
     const int4* tct;     // tensor queue targets (i, j, k), in order
+    const G2Task* yq;    // forward-solve queue Y(0) Y(1) ..., in order
 };
 
 // Device view of one problem of a launch: its layout, queue geometry, its
-// dependency counters, the priority-queue index past each step's solves, and
-// (batched launches) its three tensor maps in global memory.
+// dependency counters, the priority-queue index past each step's solves,
+// (batched launches) its three tensor maps in global memory, and Z for the
+// forward solve fused into the factorization (nullptr: factor only).
 struct ProbDev {
     Layout L;
     SchedGeom g;
-    int *upd, *tcnt, *pot, *sub;
+    int *upd, *tcnt, *pot, *sub, *ycnt, *ydone;
+    const double* z;
+    double* res;   // (log|Sigma|, Z' Sigma^-1 Z) of the fused solve
     const int* trsm_end;
     const CUtensorMap* tmap;
 };
@@ -47,9 +53,13 @@ struct ProbDev {
 // ex: in-band (FP64) updates as FP64-accurate tensor-core items instead of
 // CUDA-core DMMA items
 SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex);
+// yq: the forward-solve queue (claimed only when its head is ready)
 void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
-                 std::vector<int>& trsm_end, std::vector<int4>& tct);
-cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, cudaStream_t s);
+                 std::vector<int>& trsm_end, std::vector<G2Task>& yq, std::vector<int4>& tct);
+// z: Z for the fused forward solve (log-det and quadratic form into res[0..1]),
+// or nullptr to factor only
+cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, const double* z, double* res,
+                          cudaStream_t s);
 
 // Batched launch: every problem's tasks in one persistent kernel.  The host
 // merges the problems' queues step by step (each problem keeps its own

@@ -13,95 +13,28 @@
 
 #include "geo_internal.cuh"
 #include "matern_dev.cuh"
+#include "ysolve.cuh"
 
 namespace geo {
 
 constexpr int SV_THREADS = 256;
-constexpr int SV_BS = 32;
+
+struct BlockSync {
+    __device__ void operator()() const { __syncthreads(); }
+};
 
 // Solve L_ii y_i = r_i in place (r_i already holds Z_i minus the earlier block
-// rows' contributions); record sum log L_aa and sum y_a^2 of this tile.  One
+// rows' contributions); record 2 sum log L_aa and sum y_a^2 of this tile.  One
 // CTA of SV_THREADS threads.
 __device__ void trsv_diag_tile(const Layout& L, int i, double* __restrict__ yv, double* __restrict__ part) {
-    const int nb = L.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double* A = dp_tile(L, i, i);
-    double* y = yv + (size_t)i * nb;
-    __shared__ double ys[SV_BS];
-    __shared__ double Db[SV_BS * (SV_BS + 1)];
-    __shared__ double rinv[SV_BS];
-    __shared__ double red[2][SV_THREADS / 32];
-    for (int c0 = 0; c0 < nb; c0 += SV_BS) {
-        const int w = min(SV_BS, nb - c0);
-        for (int idx = tid; idx < w * w; idx += SV_THREADS) {
-            const int r = idx % w, c = idx / w;
-            Db[r * (SV_BS + 1) + c] = A[(size_t)(c0 + c) * nb + c0 + r];
-        }
-        __syncthreads();
-        if (tid < w) rinv[tid] = 1.0 / Db[tid * (SV_BS + 1) + tid];
-        __syncthreads();
-        if (warp == 0) {
-            double v = lane < w ? y[c0 + lane] : 0.0;
-            for (int c = 0; c < w; ++c) {
-                const double xc = __shfl_sync(0xffffffffu, v, c) * rinv[c];
-                if (lane == c) v = xc;
-                if (lane > c && lane < w) v = fma(-Db[lane * (SV_BS + 1) + c], xc, v);
-            }
-            if (lane < w) {
-                ys[lane] = v;
-                y[c0 + lane] = v;
-            }
-        }
-        __syncthreads();
-        for (int r = c0 + w + tid; r < nb; r += SV_THREADS) {
-            double acc = 0.0;
-            for (int c = 0; c < w; ++c) acc = fma(A[(size_t)(c0 + c) * nb + r], ys[c], acc);
-            y[r] -= acc;
-        }
-        __syncthreads();
-    }
-    double ld = 0.0, q = 0.0;
-    for (int a = tid; a < nb; a += SV_THREADS) {
-        ld += log(A[(size_t)a * nb + a]);
-        q = fma(y[a], y[a], q);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        ld += __shfl_down_sync(0xffffffffu, ld, o);
-        q += __shfl_down_sync(0xffffffffu, q, o);
-    }
-    if (lane == 0) {
-        red[0][warp] = ld;
-        red[1][warp] = q;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double s0 = 0.0, s1 = 0.0;
-        for (int w2 = 0; w2 < SV_THREADS / 32; ++w2) {
-            s0 += red[0][w2];
-            s1 += red[1][w2];
-        }
-        part[2 * i] = 2.0 * s0;
-        part[2 * i + 1] = s1;
-    }
+    __shared__ YSolveSmem S;
+    ysolve_diag_tile(L, i, yv, part, (int)threadIdx.x, SV_THREADS, S, BlockSync());
 }
 
 __global__ void __launch_bounds__(SV_THREADS) trsv_diag_kernel(Layout L, int i, double* __restrict__ yv,
                                                                double* __restrict__ part) {
     if (failed(L)) return;
     trsv_diag_tile(L, i, yv, part);
-}
-
-// r-th row of y_l -= L(l,i) y_i (yi: y_i, FP64 accumulation in column order)
-__device__ __forceinline__ double trsv_row_update(const Layout& L, int l, int i, int r, const double* yi) {
-    const int nb = L.nb;
-    double acc = 0.0;
-    if (is_dp(l, i, L.band)) {
-        const double* A = dp_tile(L, l, i);
-        for (int c = 0; c < nb; ++c) acc = fma(A[(size_t)c * nb + r], yi[c], acc);
-    } else {
-        const float* A = sp_tile(L, l, i);
-        for (int c = 0; c < nb; ++c) acc = fma((double)A[(size_t)c * nb + r], yi[c], acc);
-    }
-    return acc;
 }
 
 constexpr int GV_ROWS = 128;
@@ -116,7 +49,7 @@ __global__ void __launch_bounds__(GV_ROWS) trsv_update_kernel(Layout L, int i, d
     for (int c = threadIdx.x; c < nb; c += GV_ROWS) yi[c] = yv[(size_t)i * nb + c];
     __syncthreads();
     if (r >= nb) return;
-    yv[(size_t)l * nb + r] -= trsv_row_update(L, l, i, r, yi);
+    yv[(size_t)l * nb + r] -= yrow_update(L, l, i, r, yi);
 }
 
 __global__ void trsv_load_kernel(Layout L, const double* __restrict__ z, double* __restrict__ yv) {
@@ -126,13 +59,7 @@ __global__ void trsv_load_kernel(Layout L, const double* __restrict__ z, double*
 
 __global__ void trsv_finish_kernel(Layout L, const double* __restrict__ part, double* logdet, double* quad) {
     if (threadIdx.x != 0) return;
-    double s0 = 0.0, s1 = 0.0;
-    for (int i = 0; i < L.p; ++i) {
-        s0 += part[2 * i];
-        s1 += part[2 * i + 1];
-    }
-    *logdet = s0;
-    *quad = s1;
+    ysolve_finish(L, part, logdet, quad);
 }
 
 static cudaError_t forward_solve(const Layout& L, double* yv, double* part, cudaStream_t s) {
@@ -221,7 +148,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_batch_kernel(const SolveJob* 
                 double* yv = L.scal + 2 * L.p + 8;
                 const double* yi = yv + (size_t)i * L.nb;
                 for (int r = tid; r < L.nb; r += SV_THREADS)
-                    yv[(size_t)l * L.nb + r] -= trsv_row_update(L, l, i, r, yi);
+                    yv[(size_t)l * L.nb + r] -= yrow_update(L, l, i, r, yi);
             }
             u0 += nl;
         }
@@ -237,10 +164,7 @@ __global__ void __launch_bounds__(SV_THREADS) trsv_batch_kernel(const SolveJob* 
         }
         if (tid == 0) {
             double s0 = 0.0, s1 = 0.0;
-            for (int i = 0; i < L.p; ++i) {
-                s0 += L.scal[2 * i];
-                s1 += L.scal[2 * i + 1];
-            }
+            ysolve_finish(L, L.scal, &s0, &s1);
             out[0] = assemble_loglik(L.n, s0, s1);
             out[1] = s0;
             out[2] = s1;

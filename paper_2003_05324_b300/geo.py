@@ -103,6 +103,7 @@ def _load():
         "geo_logdet_trsv_noalloc": [ctypes.POINTER(geo_tiles), P, P, P, P],
         "geo_status": [ctypes.POINTER(geo_tiles), ctypes.POINTER(I), ctypes.POINTER(I), P],
         "geo_loglik": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, ctypes.POINTER(D), ctypes.POINTER(I), P],
+        "geo_loglik_async": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, P, P],
         "geo_krige": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, P, P, I, P, P, P],
         "geo_batch_workspace": [I, ctypes.POINTER(geo_batch_item), ctypes.POINTER(ctypes.c_size_t)],
         "geo_batch_bind": [I, ctypes.POINTER(geo_batch_item), P, ctypes.c_size_t, P],
@@ -273,12 +274,13 @@ class TileStore:
 
     def loglik_async(self, x, y, z, theta: Theta, stream=None):
         """Generation, factorization, log-det and solve enqueued on the stream without
-        waiting; returns device scalars (logdet, quad).  Assembly of Eq. 2 from them
-        is two scalar operations (`assemble`)."""
-        self.matern(x, y, theta, stream)
-        _check(lib.geo_potrf_mp(ctypes.byref(self.t), _stream(stream)), "geo_potrf_mp")
-        ld, q, _ = self.logdet_trsv(z, stream)
-        return ld, q
+        waiting (geo_loglik_async); returns device scalars (logdet, quad).  Assembly
+        of Eq. 2 from them is two scalar operations (`assemble`)."""
+        import torch
+        res = torch.empty(2, dtype=torch.float64, device=self._dp.device)
+        _check(lib.geo_loglik_async(ctypes.byref(self.t), _ptr(x), _ptr(y), _ptr(z), theta.c(), _ptr(res),
+                                    _stream(stream)), "geo_loglik_async")
+        return res[0:1], res[1:2]
 
     def assemble(self, ld: float, q: float) -> float:
         return -0.5 * self.n * LOG_2PI - 0.5 * ld - 0.5 * q

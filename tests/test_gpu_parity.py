@@ -316,6 +316,33 @@ def test_loglik_markov_closed_form_fp64(G, mode):
     assert abs(l - want) <= 1e-10 * abs(want)
 
 
+@pytest.mark.parametrize("n,nb,band,flags", [(1000, 96, 2, 0), (1000, 96, 2, 4), (333, 32, 3, 0), (40, 64, 1, 0),
+                                             (1536, 512, 1, 0)])
+def test_fused_solve_equals_standalone_solve(G, n, nb, band, flags):
+    """The forward solve run inside the factorization launch (geo_loglik,
+    geo_loglik_async) performs, per element, the operations of the standalone
+    geo_logdet_trsv in the same order: the two give the same bits."""
+    th = G.Theta(1.0, 0.1, 0.5, 1e-6)
+    x, y = inputs.uniform_points(n, seed=21)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.white_noise(n, seed=22)
+    X, Y, Z = dev(x), dev(y), dev(z)
+    ts = G.TileStore(n, nb, band, G.GEO_LP_SPLIT_BF16)
+    ts.set_flags(flags)
+    l, ld, q = ts.loglik(X, Y, Z, th)
+    lda, qa = ts.loglik_async(X, Y, Z, th)
+    torch.cuda.synchronize()
+    ts.matern(X, Y, th)
+    ts.potrf()
+    lds, qs, _ = ts.logdet_trsv(Z)
+    torch.cuda.synchronize()
+    assert ld == float(lds) and q == float(qs)
+    assert float(lda) == ld and float(qa) == q
+    want = O.loglik_dense(x, y, z, oracle_theta(th))["loglik"]
+    assert abs(l - want) <= 1e-6 * abs(want)
+
+
 def test_loglik_deterministic(G):
     th = G.Theta(1.0, 0.1, 1.0)
     x, y, z = problem(30, 3, th)
