@@ -77,7 +77,8 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     for (int k = 0; k < p; ++k) {
         n_y += 1 + (long long)(p - k - 1) * g.chunks_y;   // YD(k), YG(i > k, chunks)
         const int ns = g.ns;
-        n_prio += ns + ns * (ns - 1) / 2 + (long long)ns * (ns - 1) * (ns + 1) / 6;   // PF, PT, PU
+        // PC, then PT and PU without the chain's PT(s+1, s) and PU(s+1, s+1, s)
+        n_prio += 1 + ns * (ns - 1) / 2 - (ns - 1) + (long long)ns * (ns - 1) * (ns + 1) / 6 - (ns - 1);
         for (int i = k + 1; i < p; ++i) n_prio += is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
         for (int j = k + 1; j < p; ++j)
             for (int i = j; i < p; ++i) {
@@ -115,11 +116,12 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
             for (int q = 0; q < g.chunks_y; ++q) yq.push_back({T_YG, k, i, q, 0});
     }
     auto A = [&](int k) {
+        prio.push_back({T_PC, k, 0, 0, 0});
         for (int s = 0; s < ns; ++s) {
-            prio.push_back({T_PF, k, s, 0, 0});
-            for (int r = s + 1; r < ns; ++r) prio.push_back({T_PT, k, r, s, 0});
+            for (int r = s + 2; r < ns; ++r) prio.push_back({T_PT, k, r, s, 0});
             for (int c = s + 1; c < ns; ++c)
-                for (int r = c; r < ns; ++r) prio.push_back({T_PU, k, r, c, s});
+                for (int r = c; r < ns; ++r)
+                    if (!(r == s + 1 && c == s + 1)) prio.push_back({T_PU, k, r, c, s});
         }
         for (int i = k + 1; i < p; ++i) {
             const int nq = is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
@@ -264,7 +266,7 @@ struct G2Smem {
         YSolveSmem yd;                               // YD: diagonal forward solve
         double yk[YS_MAX_NB];                        // YG: y_k
     };
-    int task, kind, ok;
+    int task, kind, ok, rows_ok;
 };
 
 // PF(k,s): FP64 Cholesky of the 32 x 32 sub-block (s,s), right-looking in
@@ -395,6 +397,143 @@ __device__ void g2_pu(const ProbDev& P, G2Smem& S, int k, int r, int c, int s, i
             }
 }
 
+// ---- PC(k): the critical chain of dpotrf(k), one task.
+// In the right-looking sub-block Cholesky of diagonal tile k the chain
+// PF(s) -> PT(s+1, s) -> PU(s+1, s+1, s) -> PF(s+1) -> ... decides how long the
+// factorization of the tile takes.  Run as separate tasks, every link pays a
+// claim, a dependency wait, a reload of its operands from L2 and a release;
+// with FP64 at 1/64 of the FP32 rate on this part those handoffs cost more than
+// the arithmetic.  PC(k) runs the whole chain in one CUDA-core group with the
+// two blocks it carries (L(s,s) and L(s+1,s)) kept in shared memory; the other
+// PT and PU tasks of the tile (off the chain) stay in the queue, and the
+// counters pot(k, r, c) keep their meaning: PC raises pot(s,s) by 2 (the last
+// update PU(s,s,s-1) and PF(s); 1 for s = 0) and pot(s+1,s) by 1 (PT(s+1,s)).
+
+// D (w x w lower, 32 x 33 row-major in shared memory) <- its Cholesky factor;
+// false if a pivot is not positive (status set, the same in every thread).
+__device__ bool pc_factor(const Layout& L, double* D, int w, int row0, int g) {
+    const int lane = g & 31, wp = g >> 5;
+    for (int c = 0; c < w; ++c) {
+        const double d = D[c * 33 + c];
+        if (!(d > 0.0)) {
+            if (g == 0 && atomicCAS(L.status + ST_CODE, 0, GEO_ERR_NOT_SPD) == 0) L.status[ST_INFO] = row0 + c + 1;
+            return false;
+        }
+        const double rs = rsqrt(d);
+        g2_sync();
+        if (g < w - c) D[(c + g) * 33 + c] = (g == 0) ? d * rs : D[(c + g) * 33 + c] * rs;
+        g2_sync();
+        const int i = c + 1 + lane;
+        if (i < w) {
+            const double li = D[i * 33 + c];
+            for (int j = c + 1 + ((wp - (c + 1)) & 3); j <= i; j += 4) D[i * 33 + j] = fma(-li, D[j * 33 + c], D[i * 33 + j]);
+        }
+        g2_sync();
+    }
+    return true;
+}
+
+// X (h x w, 32 x 33) <- X D^-T with D the factored block (reciprocal pivots in
+// D's padding column 32).
+__device__ void pc_solve(double* D, double* X, int h, int w, int g) {
+    const int lane = g & 31, wp = g >> 5;
+    if (g < w) D[g * 33 + 32] = 1.0 / D[g * 33 + g];
+    g2_sync();
+    for (int c = 0; c < w; ++c) {
+        if (g < h) X[g * 33 + c] *= D[c * 33 + 32];
+        g2_sync();
+        if (lane < h) {
+            const double xc = X[lane * 33 + c];
+            for (int j = c + 1 + ((wp - (c + 1)) & 3); j < w; j += 4)
+                X[lane * 33 + j] = fma(-xc, D[j * 33 + c], X[lane * 33 + j]);
+        }
+        g2_sync();
+    }
+}
+
+// D (lower 32 x 32) -= X X' with X 32 x 32 (zero beyond its rows), DMMA, the
+// contraction in steps of 4 as in PU.
+__device__ void pc_syrk(double* D, const double* X, int g) {
+    const int lane = g & 31, wp = g >> 5, gi = lane >> 2, tq = lane & 3;
+    const int wr = (wp >> 1) * 16, wc = (wp & 1) * 16;
+    if (wr < wc) return;   // that quadrant lies above the diagonal
+    double acc[2][2][2] = {{{0.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 0.0}}};
+#pragma unroll
+    for (int kk = 0; kk < 32; kk += 4) {
+        double af[2], bf[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) af[a] = X[(wr + a * 8 + gi) * 33 + kk + tq];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) bf[b] = X[(wc + b * 8 + gi) * 33 + kk + tq];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) dmma884(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int rr = wr + a * 8 + gi, cc = wc + b * 8 + 2 * tq + e;
+                if (rr >= cc) D[rr * 33 + cc] -= acc[a][b][e];
+            }
+}
+
+__device__ bool g2_pchain(const DagArgs& A, const ProbDev& P, G2Smem& S, int k, int g) {
+    const Layout& L = P.L;
+    const int nb = L.nb, ns = P.g.ns;
+    double* T = dp_tile(L, k, k);
+    double* D = S.pot.D;
+    double* X = S.pot.X;
+    for (int s = 0; s < ns; ++s) {
+        const int c0 = s * 32, w = min(32, nb - c0);
+        // (s,s) after the other workers' updates t <= s-2; the last one, from
+        // the block solved in the previous step, is applied here
+        if (g == 0) S.rows_ok = (s < 2 || wait_ge(A, L, pot_at(P, k, s, s), s - 1, 46)) ? 1 : 0;
+        g2_sync();
+        if (!S.rows_ok) return false;
+        for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
+            const int r = idx % 32, c = idx / 32;
+            D[r * 33 + c] = (r < w && c < w && r >= c) ? T[(size_t)(c0 + c) * nb + c0 + r] : 0.0;
+        }
+        g2_sync();
+        if (s > 0) {
+            pc_syrk(D, X, g);
+            g2_sync();
+        }
+        if (!pc_factor(L, D, w, k * nb + c0, g)) return false;
+        for (int idx = g; idx < w * w; idx += G2_THREADS) {
+            const int r = idx % w, c = idx / w;
+            if (r >= c) T[(size_t)(c0 + c) * nb + c0 + r] = D[r * 33 + c];
+        }
+        __threadfence();
+        g2_sync();
+        if (g == 0) red_release_add(pot_at(P, k, s, s), s == 0 ? 1 : 2);
+        if (s + 1 == ns) break;
+        // PT(s+1, s) after the other workers' updates t < s of that block
+        const int r0 = c0 + 32, h = min(32, nb - r0);
+        if (g == 0) S.rows_ok = (s == 0 || wait_ge(A, L, pot_at(P, k, s + 1, s), s, 47)) ? 1 : 0;
+        g2_sync();
+        if (!S.rows_ok) return false;
+        for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
+            const int a = idx % 32, b = idx / 32;
+            X[a * 33 + b] = (a < h && b < w) ? T[(size_t)(c0 + b) * nb + r0 + a] : 0.0;
+        }
+        g2_sync();
+        pc_solve(D, X, h, w, g);
+        for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
+            const int a = idx % 32, b = idx / 32;
+            if (a < h && b < w) T[(size_t)(c0 + b) * nb + r0 + a] = X[a * 33 + b];
+        }
+        __threadfence();
+        g2_sync();
+        if (g == 0) red_release_add(pot_at(P, k, s + 1, s), 1);
+    }
+    return true;
+}
+
 // TRSM rows [r0, r0 + nrows) of panel tile (i,k) against L_kk (T = double for a
 // band tile, float against FP32(L_kk) otherwise); thread g owns row r0 + g.
 // Left-looking over super-blocks of SB columns held in registers: each earlier
@@ -402,9 +541,11 @@ __device__ void g2_pu(const ProbDev& P, G2Smem& S, int k, int r, int c, int s, i
 // reads in flight at a time; the earlier columns' contributions are summed 16
 // terms at a time before entering the accumulator.  L is staged through shared
 // memory 16 x SB (and SB x SB for the diagonal block).  Returns max |x| of the row.
-template <typename T, int SB>
+// ready(hi): called by the whole group before rows [0, hi) of L_kk are first
+// read; false (the same in every thread) abandons the solve, returning -1.
+template <typename T, int SB, typename Ready>
 __device__ float g2_trsm_rows(const double* __restrict__ Lkk, T* __restrict__ X, int nb, int r0, int nrows, int g,
-                              G2Smem& S) {
+                              G2Smem& S, Ready& ready) {
     const int r = r0 + g;
     const bool valid = g < nrows && r < nb;
     T* Lst = reinterpret_cast<T*>(S.tr.Lb);            // [16][SB]
@@ -412,6 +553,7 @@ __device__ float g2_trsm_rows(const double* __restrict__ Lkk, T* __restrict__ X,
     float rowmax = 0.0f;
     for (int sb0 = 0; sb0 < nb; sb0 += SB) {
         const int w = min(SB, nb - sb0);
+        if (!ready(sb0 + w)) return -1.0f;
         T acc[SB];
 #pragma unroll
         for (int jj = 0; jj < SB; ++jj) acc[jj] = (valid && jj < w) ? X[(size_t)(sb0 + jj) * nb + r] : (T)0;
@@ -684,6 +826,9 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                     if (t.a == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 11);
                     ok = ok && wait_ge(A, L, pot_at(P, k, t.a, t.a), t.a, 12);
                     break;
+                case T_PC:   // the tile's trailing updates; the chain waits for the rest as it goes
+                    ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 11);
+                    break;
                 case T_PT:
                     if (t.b == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 13);
                     ok = ok && wait_ge(A, L, pot_at(P, k, t.b, t.b), t.b + 1, 14) &&
@@ -695,8 +840,8 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                          wait_ge(A, L, pot_at(P, k, t.b, t.c), t.c + 1, 18) &&
                          wait_ge(A, L, pot_at(P, k, t.a, t.b), t.c, 19);
                     break;
-                case T_TRSM:
-                    ok = wait_ge(A, L, pot_at(P, k, ns - 1, ns - 1), ns, 20) &&
+                case T_TRSM:   // the first sub-block of L_kk; the solve waits for later ones as it goes
+                    ok = wait_ge(A, L, pot_at(P, k, 0, 0), 1, 20) &&
                          wait_ge(A, L, P.upd + t.a * L.p + k, k * items_of(P, t.a, k), 21);
                     break;
                 case T_YD:   // L_kk final and every earlier block row's contribution applied
@@ -734,6 +879,9 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 ran = g2_pf(P, S, t.k, t.a, g);   // false: not positive definite (status set)
                 done = pot_at(P, t.k, t.a, t.a);
                 break;
+            case T_PC:   // signals its own sub-blocks as it goes
+                ran = g2_pchain(A, P, S, t.k, g);
+                break;
             case T_PT:
                 g2_pt(P, S, t.k, t.a, t.b, g);
                 done = pot_at(P, t.k, t.a, t.b);
@@ -746,14 +894,28 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 const int i = t.a, k = t.k, q = t.b;
                 const double* Lkk = dp_tile(L, k, k);
                 const int r = q * 128 + g;
+                // POTRF(k) finishes L_kk's 32-row sub-blocks in order (sub-block
+                // row s is final once (s,s) is factored): the solve of this tile
+                // runs alongside it, waiting only before rows not yet final
+                int s_done = 0;
+                auto ready = [&](int hi) -> bool {
+                    const int s = (hi - 1) / 32;
+                    if (s < s_done) return true;
+                    if (g == 0) S.rows_ok = wait_ge(A, L, pot_at(P, k, s, s), s + 1, 45) ? 1 : 0;
+                    g2_sync();
+                    s_done = s + 1;
+                    return S.rows_ok != 0;
+                };
                 if (is_dp(i, k, L.band)) {
                     double* X = dp_tile(L, i, k);
-                    const float m = g2_trsm_rows<double, 16>(Lkk, X, nb, q * 128, 128, g, S);
-                    if (L.planes && r < nb) g2_slice_row<double>(L, X, i, k, r, m);
+                    const float m = g2_trsm_rows<double, 16>(Lkk, X, nb, q * 128, 128, g, S, ready);
+                    ran = m >= 0.0f;
+                    if (ran && L.planes && r < nb) g2_slice_row<double>(L, X, i, k, r, m);
                 } else {
                     float* X = sp_tile(L, i, k);
-                    const float m = g2_trsm_rows<float, 32>(Lkk, X, nb, q * 128, 128, g, S);
-                    if (L.planes && r < nb) g2_slice_row<float>(L, X, i, k, r, m);
+                    const float m = g2_trsm_rows<float, 32>(Lkk, X, nb, q * 128, 128, g, S, ready);
+                    ran = m >= 0.0f;
+                    if (ran && L.planes && r < nb) g2_slice_row<float>(L, X, i, k, r, m);
                 }
                 fence_proxy_async_global();   // the planes are read by TMA
                 done = P.tcnt + i * L.p + k;
