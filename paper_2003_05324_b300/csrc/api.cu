@@ -142,8 +142,9 @@ Layout make_layout(const geo_tiles* t) {
     L.tickets = L.status + ST_WORDS;
     L.scal = (double*)(base + mo.scal);
     L.planes = (__nv_bfloat16*)t->d_planes;
-    L.rexp = t->d_planes ? (int*)((char*)t->d_planes +
-                                  align256((size_t)NPL * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots))
+    L.npl = planes_per_slot(g.band, g.p);
+    L.rexp = t->d_planes ? (int*)((char*)t->d_planes + align256((size_t)L.npl * g.pp * g.pp *
+                                                                sizeof(__nv_bfloat16) * (size_t)g.n_slots))
                          : nullptr;
     return L;
 }
@@ -201,9 +202,11 @@ int geo_layout_init(int n, int nb, int band, int lp_mode, geo_layout* out) {
     const size_t tile = (size_t)nb * nb;
     g.bytes_dp = align256(sizeof(double) * tile * (size_t)ndp);
     g.bytes_sp = align256(sizeof(float) * tile * (size_t)std::max(nsp, 1LL));
-    // NPL BF16 slice planes of every panel tile, then one int32 row exponent per plane row
+    // the slice planes of every panel tile (2 bytes per entry), then one int32
+    // row exponent per plane row
     g.bytes_planes = (lp_mode == GEO_LP_SPLIT_BF16 && p > 1)
-                         ? align256((size_t)NPL * g.pp * g.pp * sizeof(__nv_bfloat16) * (size_t)g.n_slots) +
+                         ? align256((size_t)planes_per_slot(g.band, p) * g.pp * g.pp * sizeof(__nv_bfloat16) *
+                                    (size_t)g.n_slots) +
                                align256(sizeof(int) * (size_t)g.pp * (size_t)g.n_slots)
                          : 0;
     g.bytes_meta = meta_offsets(g).total;

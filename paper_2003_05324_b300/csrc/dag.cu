@@ -622,8 +622,9 @@ __device__ float g2_trsm_rows(const double* __restrict__ Lkk, T* __restrict__ X,
     return rowmax;
 }
 
-// Fixed-point slicing of one solved row (slice_value): row exponent and the
-// NPL BF16 planes of the whole padded row, from the row's stored precision.
+// Fixed-point slicing of one solved row: row exponent, the NPL BF16 planes
+// (slice_value) and, in a store with off-band tiles, the NPLH FP16 planes
+// (slice_value_h) of the whole padded row, from the row's stored precision.
 template <typename T>
 __device__ void g2_slice_row(const Layout& L, const T* __restrict__ X, int i, int k, int r, float m) {
     const int nb = L.nb, pp = L.pp;
@@ -646,6 +647,21 @@ __device__ void g2_slice_row(const Layout& L, const T* __restrict__ X, int i, in
 #pragma unroll
         for (int s = 0; s < NPL; ++s)
             *reinterpret_cast<uint4*>(P0 + s * pstride + c0) = *reinterpret_cast<const uint4*>(sl[s]);
+        if (L.npl > NPL) {
+            __align__(16) __half sh[NPLH][8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = c0 + q;
+                const T v = (c < nb) ? X[(size_t)c * nb + r] : (T)0;
+                __half d[NPLH];
+                slice_value_h<T>(v, e, d);
+#pragma unroll
+                for (int s = 0; s < NPLH; ++s) sh[s][q] = d[s];
+            }
+#pragma unroll
+            for (int s = 0; s < NPLH; ++s)
+                *reinterpret_cast<uint4*>(P0 + (NPL + s) * pstride + c0) = *reinterpret_cast<const uint4*>(sh[s]);
+        }
     }
 }
 
@@ -1064,7 +1080,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             }
             const ProbDev& P = prob_of(A, m.pid);
             const int p = P.L.p, nk = P.L.pp / TC_BK, nkp = (nk + KPC - 1) / KPC;
-            const int sa = P.L.slot[m.i * p + m.k] * NPL, sb = P.L.slot[m.j * p + m.k] * NPL;
+            const int sa = P.L.slot[m.i * p + m.k] * P.L.npl, sb = P.L.slot[m.j * p + m.k] * P.L.npl;
             const CUtensorMap* map_a = single ? tmap_a : P.tmap;
             const CUtensorMap* map_b = single ? tmap_b : P.tmap + 1;
             const CUtensorMap* map_b64 = single ? tmap_b64 : P.tmap + 2;
@@ -1076,21 +1092,22 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                 mbar_expect_tx(FULL(st), bytes);
                 return smem + st * TC_STAGE_BYTES;
             };
-            if (!m.ex) {
+            if (!m.ex) {   // FP16 planes NPL.. of the 8/12/12 split
                 for (int kc = 0; kc < nk && ok; ++kc, ++it) {
-                    uint8_t* sbase = next_stage(TC_STAGE_BYTES);
+                    uint8_t* sbase = next_stage(TC_H_STAGE_BYTES);
                     if (!sbase) {
                         ok = false;
                         break;
                     }
                     const uint32_t full = FULL(it % TC_STAGES);
 #pragma unroll
-                    for (int s = 0; s < TC_NS; ++s)
-                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), map_a, kc * TC_BK, m.mb * TC_BM, sa + s, full);
+                    for (int s = 0; s < TC_HA; ++s)
+                        tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), map_a, kc * TC_BK, m.mb * TC_BM, sa + NPL + s,
+                                    full);
 #pragma unroll
-                    for (int s = 0; s < TC_NS; ++s)
-                        tma_load_3d(smem_u32(sbase + TC_NS * TC_A_BYTES + s * TC_B_BYTES), map_b, kc * TC_BK,
-                                    m.nc * TC_BN, sb + s, full);
+                    for (int s = 0; s < TC_HB; ++s)
+                        tma_load_3d(smem_u32(sbase + TC_HA * TC_A_BYTES + s * TC_B_BYTES), map_b, kc * TC_BK,
+                                    m.nc * TC_BN, sb + NPL + s, full);
                 }
             } else {
                 for (int h = 0; h < m.nh && ok; ++h) {
@@ -1182,17 +1199,17 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                         break;
                     }
 #pragma unroll
-                    for (int q = 0; q < TC_NPAIRS; ++q) {
-                        const uint32_t a_addr = sbase + c_pair_a[q] * TC_A_BYTES;
-                        const uint32_t b_addr = sbase + TC_NS * TC_A_BYTES + c_pair_b[q] * TC_B_BYTES;
+                    for (int q = 0; q < TC_HPAIRS; ++q) {
+                        const uint32_t a_addr = sbase + c_hpair_a[q] * TC_A_BYTES;
+                        const uint32_t b_addr = sbase + TC_HA * TC_A_BYTES + c_hpair_b[q] * TC_B_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; ++kk) {
                             if (q == 0)
                                 umma_bf16(dst0, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
-                                          (kc | kk) != 0);
+                                          (kc | kk) != 0, TC_IDESC_F16);
                             else
                                 umma_bf16(dst1, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
-                                          (kc | (q - 1) | kk) != 0);
+                                          (kc | (q - 1) | kk) != 0, TC_IDESC_F16);
                         }
                     }
                     umma_commit(EMPTY(it % TC_STAGES));
@@ -1353,7 +1370,8 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                             for (int e = 0; e < 16; ++e) ec[e] = 0;
                         }
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) cpre[cc + e] -= (v0[e] + v1[e]) * pow2f(er + ec[e] - 16);
+                        for (int e = 0; e < 16; ++e)
+                            cpre[cc + e] -= fmaf(v1[e], 1.0f / 4096.0f, v0[e]) * pow2f(er + ec[e] - 16);
                     }
 #pragma unroll
                     for (int e = 0; e < BATCH; ++e)

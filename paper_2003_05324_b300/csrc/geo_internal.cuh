@@ -4,12 +4,13 @@
 // stored contiguously: in the FP64 store when i - j < band (Algorithm 1's
 // diag_thick), otherwise in the FP32 store.  `off[i*p + j]` is its element
 // offset inside the store of its precision (-1 for the upper triangle).
-// Panel tiles (i > j) also own a slot of NPL = 7 BF16 planes (fixed-point
-// slices of their value, scaled per row: 8 bits each, 56 bits in all), each
+// Panel tiles (i > j) also own a slot of planes: NPL = 7 BF16 planes
+// (fixed-point slices of their value, scaled per row: 8 bits each, 56 bits in
+// all) read by the in-band (FP64-accurate) products, and -- when the store has
+// off-band tiles -- NPLH = 4 FP16 planes of an 8/12/12-bit split of the same
+// row-scaled value read by the off-band (FP32-accurate) products.  Each plane is
 // pp x pp row-major with the column (the contraction index of the updates)
-// contiguous and zero padding beyond nb, plus one scale exponent per row.  The
-// off-band (FP32-accurate) products read the first four planes, the in-band
-// (FP64-accurate) products all seven.
+// contiguous and zero padding beyond nb; one scale exponent per row.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -24,6 +25,7 @@ enum { ST_CODE = 0, ST_INFO = 1, ST_TIMEOUT_WHERE = 2, ST_BAR_COUNT = 4, ST_BAR_
 
 struct Layout {
     int n, nb, p, band, pp, lp_mode, flags;
+    int npl;        // planes per panel-tile slot: NPL, or NPL + NPLH with off-band tiles
     double* dp;
     float* sp;
     const long long* off;
@@ -35,14 +37,17 @@ struct Layout {
     double* scal;   // scalar scratch: per-tile log-det and quad partials [2*p], results [2]
 };
 
-constexpr int NPL = 7;   // slice planes stored per panel tile
+constexpr int NPL = 7;    // BF16 8-bit slice planes (in-band products)
+constexpr int NPLH = 4;   // FP16 planes a0, a1, a2 2^-12, a1 2^-12 of the 8/12/12 split (off-band products)
+// planes per slot of a store with band b and p tiles per side
+__host__ __device__ inline int planes_per_slot(int band, int p) { return band < p ? NPL + NPLH : NPL; }
 
 __host__ __device__ inline bool is_dp(int i, int j, int band) { return (i - j) < band; }
 
 __device__ __forceinline__ double* dp_tile(const Layout& L, int i, int j) { return L.dp + L.off[i * L.p + j]; }
 __device__ __forceinline__ float* sp_tile(const Layout& L, int i, int j) { return L.sp + L.off[i * L.p + j]; }
 __device__ __forceinline__ __nv_bfloat16* plane(const Layout& L, int i, int j, int s) {
-    return L.planes + ((size_t)L.slot[i * L.p + j] * NPL + s) * (size_t)L.pp * L.pp;
+    return L.planes + ((size_t)L.slot[i * L.p + j] * L.npl + s) * (size_t)L.pp * L.pp;
 }
 __device__ __forceinline__ bool failed(const Layout& L) {
     return *((volatile int*)L.status + ST_CODE) != 0;

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int i, j;
                 decode_lp_target(w / per_target, k, p, L.band, i, j);
                 const int rem = w % per_target, mb = rem / nnc, nc = rem % nnc;
-                const int sa = L.slot[i * p + k] * NPL, sb = L.slot[j * p + k] * NPL;
+                const int sa = L.slot[i * p + k] * L.npl, sb = L.slot[j * p + k] * L.npl;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int st = it % TC_STAGES;
                     const uint32_t ph = (it / TC_STAGES) & 1;
@@ -339,12 +339,12 @@ static PFN_encodeTiled get_encode() {
     return fn;
 }
 
-// 3D map over all planes: (K = pp, rows = pp, plane index = NPL * n_slots); the
+// 3D map over all planes: (K = pp, rows = pp, plane index = npl * n_slots); the
 // box is 32 columns (64 bytes, the swizzle width) by `rows` rows.
 static int make_plane_map(const Layout& L, long long nslots, int rows, CUtensorMap* map) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return 1;
-    cuuint64_t dims[3] = {(cuuint64_t)L.pp, (cuuint64_t)L.pp, (cuuint64_t)(NPL * nslots)};
+    cuuint64_t dims[3] = {(cuuint64_t)L.pp, (cuuint64_t)L.pp, (cuuint64_t)(L.npl * nslots)};
     cuuint64_t strides[2] = {(cuuint64_t)L.pp * 2, (cuuint64_t)L.pp * L.pp * 2};
     cuuint32_t box[3] = {TC_BK, (cuuint32_t)rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};

@@ -26,6 +26,34 @@ namespace geo {
 
 static double host_lgamma(double v) { return lgamma(v); }
 
+// The table of the FP32 exponential (matern_dev.cuh), from the double exp2.
+static const ExpTab& exp_table() {
+    static const ExpTab tab = [] {
+        ExpTab t;
+        for (int j = 0; j < 32; ++j) {
+            const double e = exp2(-j / 32.0);
+            t.hi[j] = (float)e;
+            t.lo[j] = (float)(e - (double)t.hi[j]);
+        }
+        const double c = log(2.0) / 32.0;
+        const double c_hi = rint(c * 65536.0) / 65536.0;   // c in [2^-6, 2^-5): 11 significant bits
+        t.c_hi = (float)c_hi;
+        t.c_lo = (float)(c - c_hi);
+        t.inv_c = (float)(1.0 / c);
+        for (int j = 0; j < 64; ++j) {
+            const double cj = 1.0 + j / 64.0, l = log(cj);
+            t.lnc_hi[j] = (float)l;
+            t.lnc_lo[j] = (float)(l - (double)t.lnc_hi[j]);
+            t.inv_cj[j] = (float)(1.0 / cj);
+        }
+        const double ln2 = log(2.0), ln2_hi = rint(ln2 * 65536.0) / 65536.0;   // 16 significant bits
+        t.ln2_hi = (float)ln2_hi;
+        t.ln2_lo = (float)(ln2 - ln2_hi);
+        return t;
+    }();
+    return tab;
+}
+
 MaternP make_matern(const geo_theta& th) {
     MaternP m;
     m.sigma2 = th.sigma2;
@@ -54,9 +82,13 @@ constexpr int GEN_COLS = 32;
 __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, const double* __restrict__ x,
                                                                    const double* __restrict__ y, geo_theta th,
                                                                    const geo_theta* __restrict__ dth,
-                                                                   int reset_status) {
+                                                                   int reset_status, ExpTab etab) {
     __shared__ MaternP smp;
+    __shared__ ExpTab stab;
     if (threadIdx.x == 0) smp = make_matern_dev(dth ? *dth : th);
+    static_assert(sizeof(ExpTab) % sizeof(float) == 0, "ExpTab words");
+    for (int w = threadIdx.x; w < (int)(sizeof(ExpTab) / sizeof(float)); w += GEN_THREADS)
+        reinterpret_cast<float*>(&stab)[w] = reinterpret_cast<const float*>(&etab)[w];
     if (reset_status && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < ST_WORDS) L.status[threadIdx.x] = 0;
     __syncthreads();
     const MaternP mp = smp;
@@ -85,6 +117,7 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
     __syncthreads();
     const bool dp = is_dp(i, j, L.band);
     const float s2f = (float)mp.sigma2, nuf = (float)mp.nu, lcf = (float)mp.log_c;
+    const float nul = (float)(mp.nu - (double)nuf);
     const float lcl = (float)(mp.log_c - (double)lcf), s2l = (float)(mp.sigma2 - (double)s2f);
     for (int a = threadIdx.x; a < nb; a += GEN_THREADS) {
         const int ga = i * nb + a;
@@ -156,7 +189,7 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
                     if (xh == 0.0f) v = s2f;
                     else {
                         const float xl = (fmaf(-xh, xh, r2h) + r2l) / (2.0f * xh);
-                        v = matern_fp32(xh, xl, mp, s2f, s2l, nuf, lcf, lcl);
+                        v = matern_fp32(xh, xl, mp, s2f, s2l, nuf, nul, lcf, lcl, stab);
                     }
                 }
                 T[(size_t)(c0 + c) * nb + a] = v;
@@ -168,7 +201,7 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
 cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* y, const geo_theta& th,
                                 const geo_theta* dth, int reset_status, cudaStream_t s) {
     dim3 grid((L.nb + GEN_COLS - 1) / GEN_COLS, L.p * (L.p + 1) / 2);
-    matern_tiles_kernel<<<grid, GEN_THREADS, 0, s>>>(L, x, y, th, dth, reset_status);
+    matern_tiles_kernel<<<grid, GEN_THREADS, 0, s>>>(L, x, y, th, dth, reset_status, exp_table());
     count_launch();
     return cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 // descriptors, tcgen05 MMA / commit / load, release-acquire counters).
 #pragma once
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include "geo_internal.cuh"
 
@@ -24,6 +25,22 @@ constexpr long long TC_WAIT_NS = 2000000000LL;      // 2 s per wait
 // smallest weight first, -> the second accumulator
 __constant__ int c_pair_a[TC_NPAIRS] = {0, 0, 1, 2, 3, 0, 1, 2, 0, 1};
 __constant__ int c_pair_b[TC_NPAIRS] = {0, 3, 2, 1, 0, 2, 1, 0, 1, 0};
+
+// ---- FP32-accurate products of the persistent scheduler's off-band items:
+// FP16 planes of an 8/12/12-bit split (slice_value_h).  A stage holds the A
+// planes h0 = a0, h1 = a1, h2 = a2 2^-12 and the B planes h0..h2 and h3 = b1
+// 2^-12.  With t = a0 + e a1 + e^2 a2 (e = 2^-12) for each operand,
+//   t_A t_B = a0 b0 + e [a0 b1 + a1 b0 + a0 (b2 e) + (a2 e) b0 + a1 (b1 e)] + O(e^3):
+// six products instead of the ten of the 8-bit BF16 split (fewer shared-memory
+// operand reads per flop, which bound the 8-bit split's MMA rate).  a0 b0
+// (|a0|, |b0| <= 128) sums exactly in FP32 for K <= 1024 (below 2^24); the
+// bracket, 2^-12 below it, goes to the second accumulator, smallest weights
+// first.  The epilogue forms acc0 + 2^-12 acc1.
+constexpr int TC_HA = 3, TC_HB = 4, TC_HPAIRS = 6;
+constexpr uint32_t TC_H_STAGE_BYTES = TC_HA * TC_A_BYTES + TC_HB * TC_B_BYTES;
+static_assert(TC_H_STAGE_BYTES <= (uint32_t)TC_STAGE_BYTES, "FP16 stage");
+__constant__ int c_hpair_a[TC_HPAIRS] = {0, 1, 0, 2, 0, 1};
+__constant__ int c_hpair_b[TC_HPAIRS] = {0, 3, 2, 0, 1, 0};
 
 // ---- FP64-accurate products for in-band (FP64) targets ("EX" items).
 // Seven slices a_0..a_6 per operand (|a_s| <= 128, 56 bits below the row
@@ -107,6 +124,9 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N, M
 constexpr uint32_t TC_IDESC =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+
+// kind::f16 with FP16 A and B (the FP16 off-band planes), D = F32
+constexpr uint32_t TC_IDESC_F16 = (1u << 4) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 
 constexpr uint32_t EX_IDESC =
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(EX_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
@@ -220,6 +240,25 @@ __device__ __forceinline__ long long ex_fixed_total(float a0, float a1, float a2
     const long long i4 = (long long)(__float2int_rn(a4 * 4294967296.0f) + __float2int_rn(a5 * 4294967296.0f));
     const long long i56 = __float2int_rn(a56 * 1099511627776.0f);
     return (i0 << 40) + (i1 << 32) + (i2 << 24) + (i3 << 16) + (i4 << 8) + i56;
+}
+
+// The FP16 planes of one value for the off-band products: with t = v 2^(8-e)
+// (|t| < 128), a0 = rint(t), a1 = rint(2^12 (t - a0)), a2 = rint(2^12 (2^12 (t -
+// a0) - a1)), so |a0| <= 128, |a1|, |a2| <= 2048 and t = a0 + a1 2^-12 + a2
+// 2^-24 + O(2^-25) (32 bits below the row scale, as the four 8-bit slices).
+// Stored: a0, a1, a2 2^-12, a1 2^-12 -- integers up to 2048 and those integers
+// times 2^-12 (normal FP16 numbers), all exact.  Every step is exact in T.
+template <typename T>
+__device__ __forceinline__ void slice_value_h(T v, int e, __half* out) {
+    const T t = (sizeof(T) == 8) ? (T)ldexp((double)v, 8 - e) : (T)ldexpf((float)v, 8 - e);
+    const T a0 = rint(t);
+    const T r1 = (t - a0) * (T)4096;
+    const T a1 = rint(r1);
+    const T a2 = rint((r1 - a1) * (T)4096);
+    out[0] = __float2half_rn((float)a0);
+    out[1] = __float2half_rn((float)a1);
+    out[2] = __float2half_rn((float)a2 * (1.0f / 4096.0f));
+    out[3] = __float2half_rn((float)a1 * (1.0f / 4096.0f));
 }
 
 // row scale exponent of a row whose largest magnitude (rounded to float) is m

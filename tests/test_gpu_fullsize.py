@@ -8,7 +8,8 @@ oracle computes one by one and properties that hold at any size:
 
   * Eq. 1: sampled rows of the generated lower triangle against the oracle's
     Matern function entry by entry (FP64 band: 1e-13 relative; FP32 tiles:
-    8 ulps of FP32, the bound of the compensated closed-form generator).
+    the exact value correctly rounded up to 2^-27 relative, the bound of the
+    float-pair closed-form generator).
   * Algorithm 1: sampled entries of L L' against Sigma.  Pairs inside one
     diagonal tile are formed in FP64-accurate arithmetic from the stored
     factor, so their residual is FP64 rounding (1e-12 of (|L||L'|)_ab).
@@ -96,7 +97,9 @@ def test_fullsize_generation_factor_solve(G, workload):
         dp = (a // NB - b // NB) < BAND
         err = np.abs(got - want)
         assert np.all(err[dp] <= 1e-13 * np.abs(want[dp]) + 1e-15), a
-        assert np.all(err[~dp] <= 8 * U32 * np.abs(want[~dp]) + 2.0 ** -126), a
+        w32 = np.abs(want[~dp])
+        bound = 0.5 * np.spacing(w32.astype(np.float32)).astype(np.float64) + 2.0 ** -27 * w32
+        assert np.all(err[~dp] <= bound), a
         assert np.all(row[a + 1:] == 0.0)
 
     # ---- Algorithm 1: sampled entries of L L' against Sigma
