@@ -3,8 +3,9 @@
 Workload (one step = one evaluation of Eq. 2, all of generation, Algorithm 1,
 log-determinant and solve): n = 40,000 locations on a 200 x 200 jittered grid
 (seed 0) in Morton order, Matern sigma2 = 1, beta = 0.1, nu = 0.5, tile 500,
-FP64 band of `--band` tiles, off-band updates as split-BF16 products on the
-tensor cores.  Inputs are synthetic (measurements from a seeded spectral
+FP64 band of `--band` tiles, off-band updates as FP32-accurate fixed-point
+slice products on the tensor cores (FP16 planes of an 8/12/12-bit split), in-band
+updates as FP64-accurate products of seven 8-bit BF16 slices.  Inputs are synthetic (measurements from a seeded spectral
 Matern-field simulation).  The working set (3.3 GB of tiles) is far larger than
 L2, so consecutive steps do not hit in L2.
 
@@ -196,8 +197,25 @@ def run_reference(args):
 
 FP64_MEASURED_TFLOPS = 0.97  # DMMA, measured by csrc/tools/fp64_peak_probe.cu on a B300
 FP32_MEASURED_TFLOPS = 68.9  # FFMA, same probe
-TC_PAIRS = 10                # BF16 slice products per off-band split update
+TC_PAIRS = 6                 # FP16 slice products per off-band update (persistent DAG kernel)
+TC_PAIRS_STEPWISE = 10       # BF16 slice products per off-band update (step-by-step kernel)
 EX_PAIRS = 28                # BF16 slice products per FP64-accurate in-band update
+
+# DRAM bytes (read + write) of one launch of the factorization kernel on this
+# workload (n = 40,000, tile 500, band 1, default flags), from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/dag_kernel_n40000_band1.md),
+# keyed by a hash of the kernel's sources: a changed kernel reports null.
+DAG_SOURCES = ("dag.cu", "dag.cuh", "tc_common.cuh", "geo_internal.cuh", "ysolve.cuh")
+DAG_TRAFFIC = {"0373ca2324450ade": 243.63e9 + 109.67e9}
+
+
+def dag_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in DAG_SOURCES:
+        with open(os.path.join(ROOT, "paper_2003_05324_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def algorithmic_flops(p, nb, band):
@@ -251,7 +269,7 @@ def kernel_rows(ts, args, kern):
              ("FP32 pipe (off-band trsm)", f32 + (lp if args.lp != "bf16" else 0.0), FP32_MEASURED_TFLOPS, "alu",
               "FP32 FFMA measured by fp64_peak_probe (68.9 TFLOP/s)")]
     if tc:
-        units.append(("tensor cores (off-band split-BF16 x %d%s)" % (
+        units.append(("tensor cores (off-band FP16 slices x %d%s)" % (
                       TC_PAIRS, ", in-band FP64-accurate x %d" % EX_PAIRS if ex else ""), tc, bf16_peak, "tensor",
                       "bf16 " + bf16_src))
     rows = []
@@ -268,7 +286,8 @@ def kernel_rows(ts, args, kern):
                      "unit_lower_bounds_ms": {u[1]: u[0] * 1e3 for u in lb}})
     names = {0: ("fp64_update (dsyrk+dgemm, DMMA)", f64u, FP64_MEASURED_TFLOPS, "alu",
                  "FP64 DMMA measured by fp64_peak_probe"),
-             1: ("offband_update (split-BF16 tcgen05)", tc, bf16_peak, "tensor", "bf16 " + bf16_src)}
+             1: ("offband_update (split-BF16 tcgen05)", lp * TC_PAIRS_STEPWISE, bf16_peak, "tensor",
+                 "bf16 " + bf16_src)}
     for kind, (name, f, pk, bound, src) in names.items():
         kms, kn = kern[kind]
         if kn and f:
@@ -282,6 +301,12 @@ def kernel_rows(ts, args, kern):
         roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
         roofline["kernel"] = dominant["kernel"]
         roofline["traffic"] = None
+        if dominant["kernel"].startswith("dag_kernel") and ts.n == M_GRID ** 2 and ts.band == 1 and \
+                args.lp == "bf16" and not (args.dmma or args.gen64):
+            t = DAG_TRAFFIC.get(dag_source_hash())
+            roofline["traffic"] = t
+            roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this "
+                                          "kernel build" if t is not None else "no capture of this kernel build")
     return rows, roofline
 
 

@@ -1,6 +1,9 @@
 // Throughput probe for the roofline denominators this library reports against:
 // FP64 DFMA, FP64 DMMA (mma.sync m8n8k4) and FP32 FFMA, each a bounded loop of
-// independent FMA chains.  Build: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o probe fp64_peak_probe.cu
+// independent FMA chains; and the latency of dependent chains of FP64 FMA,
+// rsqrt, division, log and FP64 -> FP32 conversion in one warp (clock64), the
+// costs that bound a factorization's critical path when FP64 is slow.
+// Build: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o probe fp64_peak_probe.cu
 #include <cstdio>
 #include <cuda_runtime.h>
 #define ITERS 4096
@@ -41,6 +44,28 @@ __global__ void dmma_k(double* out, double a) {
   double s = 0; for (int c = 0; c < 4; ++c) s += acc[c][0] + acc[c][1];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// one warp, `active` lanes, a dependent chain of n operations of one kind
+__global__ void chain_k(double* out, long long* cyc, int n, int active, int mode) {
+  const int lane = threadIdx.x;
+  double a = 1.0 + lane * 1e-3;
+  const double b = 0.999999, c = 1e-7;
+  float fa = 1.0f + lane * 1e-3f;
+  __syncwarp();
+  const long long t0 = clock64();
+  if (lane < active) {
+    if (mode == 0) { for (int i = 0; i < n; ++i) a = fma(a, b, c); }
+    else if (mode == 1) { for (int i = 0; i < n; ++i) a = rsqrt(a) + 0.5; }
+    else if (mode == 2) { for (int i = 0; i < n; ++i) fa = fmaf(fa, 0.999999f, 1e-7f); a = fa; }
+    else if (mode == 3) { for (int i = 0; i < n; ++i) a = 1.0 / a + 0.25; }
+    else if (mode == 4) { for (int i = 0; i < n; ++i) a = (double)(float)a * b; }
+    else { for (int i = 0; i < n; ++i) a = log(a) + 1.5; }
+  }
+  __syncwarp();
+  const long long t1 = clock64();
+  out[lane] = a;
+  if (lane == 0) *cyc = t1 - t0;
+}
+
 int main() {
   int sms; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   int clk; cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
@@ -65,6 +90,15 @@ int main() {
     flops = 2.0 * 16 * 4 * (double)ITERS * grid * thr;
     printf("FFMA bps=%d: %.3f ms  %.3f TFLOP/s\n", blocksPerSM, ms, flops / ms / 1e9);
   }
+  long long* cyc; cudaMalloc(&cyc, sizeof(long long));
+  const char* names[] = {"dfma", "drsqrt + dadd", "ffma", "ddiv + dadd", "f2f.f32.f64 + dmul", "dlog + dadd"};
+  for (int mode = 0; mode < 6; ++mode)
+    for (int active : {32, 1}) {
+      chain_k<<<1, 32>>>(d, cyc, 256, active, mode);
+      chain_k<<<1, 32>>>(d, cyc, 256, active, mode);
+      long long h = 0; cudaMemcpy(&h, cyc, sizeof(h), cudaMemcpyDeviceToHost);
+      printf("latency %-20s lanes=%2d: %.1f cycles per step\n", names[mode], active, (double)h / 256);
+    }
   cudaError_t err = cudaDeviceSynchronize();
   printf("status %s\n", cudaGetErrorString(err));
   return err != cudaSuccess;
