@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--evals", type=int, default=60)
     ap.add_argument("--profile", action="store_true", help="Eq. 3: sigma2 profiled")
     ap.add_argument("--dmma", action="store_true")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="after the estimate, evaluate l at theta-hat and theta-true with every tile FP64")
     a = ap.parse_args()
     x, y = inputs.jittered_grid(a.m, seed=0)
     perm = geo.morton_order(x, y)
@@ -42,11 +44,30 @@ def main():
     if a.dmma:
         ts.set_flags(geo.GEO_FLAG_FP64_DMMA)
     th0 = geo.Theta(0.5, 0.05, 0.5, a.nugget)
+    th_true = geo.Theta(a.sigma2, a.beta, a.nu, a.nugget)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    l_mp_true = ts.loglik(X, Y, Z, th_true)[0]
+    t_eval = time.perf_counter() - t0
     t0 = time.perf_counter()
     r = ts.mle(X, Y, Z, th0, max_evals=a.evals, profile=a.profile)
     wall = time.perf_counter() - t0
     th = r["theta"]
-    print(json.dumps({"n": n, "nb": a.nb, "band": a.band, "theta_true": [a.sigma2, a.beta, a.nu, a.nugget],
+    extra = {"seconds_first_eval": t_eval, "loglik_mp_theta_true": l_mp_true,
+             "tflops_per_eval": n ** 3 / 3.0 / (wall / max(r["evals"], 1)) / 1e12}
+    if a.compare_fp64:
+        l_mp_hat = r["loglik"]
+        del ts
+        torch.cuda.empty_cache()
+        t64 = geo.TileStore(n, a.nb, 10 ** 6, geo.GEO_LP_SPLIT_BF16)
+        t0 = time.perf_counter()
+        l64_true = t64.loglik(X, Y, Z, th_true)[0]
+        extra["seconds_fp64_eval"] = time.perf_counter() - t0
+        l64_hat = t64.loglik(X, Y, Z, geo.Theta(th.sigma2, th.beta, th.nu, a.nugget))[0]
+        extra.update({"loglik_fp64_theta_true": l64_true, "loglik_fp64_theta_hat": l64_hat,
+                      "rel_err_theta_true": abs(l_mp_true - l64_true) / abs(l64_true),
+                      "rel_err_theta_hat": abs(l_mp_hat - l64_hat) / abs(l64_hat)})
+    print(json.dumps({**extra, "n": n, "nb": a.nb, "band": a.band, "theta_true": [a.sigma2, a.beta, a.nu, a.nugget],
                       "theta_hat": [th.sigma2, th.beta, th.nu], "loglik": r["loglik"], "evals": r["evals"],
                       "iterations": r["iterations"], "not_spd": r["not_spd"], "seconds": wall,
                       "seconds_per_eval": wall / max(r["evals"], 1), "profile": a.profile,
