@@ -92,9 +92,15 @@ typedef struct geo_tiles {
 
 /* One record of the device-side task trace (tensor-core mode scheduler):
  * type 0..4 = potrf sub-block factor / solve / update, panel trsm, FP64 (DMMA)
- * update item; 10 = tensor-core off-band update item, 11 = tensor-core
- * in-band (FP64-accurate) update item.  Times are %globaltimer nanoseconds:
- * claimed, dependencies satisfied, finished. */
+ * update item; 5, 6 = forward-solve diagonal / block-row task; 7, 8 = the
+ * dpotrf chain tasks PC, PC2 (a = 0); 10 = tensor-core off-band update item,
+ * 11 = tensor-core in-band (FP64-accurate) update item; 12, 13 = one sub-step
+ * s (in a) of PC: the factor of (s,s), the solve of (s+1,s), with t_claim =
+ * sub-step start, t_ready = its dependencies met, t_end = done; 14 = one
+ * (column slice, contraction part) of an in-band item (c = slice * parts +
+ * part), t_ready = its products done, t_end = drained.  Times are
+ * %globaltimer nanoseconds: t_claim when the task was taken, t_ready when its
+ * dependencies were met, t_end when it finished. */
 typedef struct geo_trace_rec {
     int type, sm, k, a, b, c;
     long long t_claim, t_ready, t_end;

@@ -77,8 +77,10 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     for (int k = 0; k < p; ++k) {
         n_y += 1 + (long long)(p - k - 1) * g.chunks_y;   // YD(k), YG(i > k, chunks)
         const int ns = g.ns;
-        // PC, then PT and PU without the chain's PT(s+1, s) and PU(s+1, s+1, s)
-        n_prio += 1 + ns * (ns - 1) / 2 - (ns - 1) + (long long)ns * (ns - 1) * (ns + 1) / 6 - (ns - 1);
+        // PC, PC2, then PT and PU without the chains' PT(s+1, s), PU(s+1, s+1, s),
+        // PT(s+2, s) and PU(s+2, s+1, s)
+        const long long n2 = std::max(0, ns - 2);
+        n_prio += 2 + ns * (ns - 1) / 2 - (ns - 1) - n2 + (long long)ns * (ns - 1) * (ns + 1) / 6 - (ns - 1) - n2;
         for (int i = k + 1; i < p; ++i) n_prio += is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
         for (int j = k + 1; j < p; ++j)
             for (int i = j; i < p; ++i) {
@@ -117,11 +119,13 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
     }
     auto A = [&](int k) {
         prio.push_back({T_PC, k, 0, 0, 0});
+        prio.push_back({T_PC2, k, 0, 0, 0});
         for (int s = 0; s < ns; ++s) {
-            for (int r = s + 2; r < ns; ++r) prio.push_back({T_PT, k, r, s, 0});
+            for (int r = s + 3; r < ns; ++r) prio.push_back({T_PT, k, r, s, 0});
             for (int c = s + 1; c < ns; ++c)
                 for (int r = c; r < ns; ++r)
-                    if (!(r == s + 1 && c == s + 1)) prio.push_back({T_PU, k, r, c, s});
+                    if (!(r == s + 1 && c == s + 1) && !(r == s + 2 && c == s + 1))
+                        prio.push_back({T_PU, k, r, c, s});
         }
         for (int i = k + 1; i < p; ++i) {
             const int nq = is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
@@ -452,33 +456,22 @@ __device__ void pc_solve(double* D, double* X, int h, int w, int g) {
 }
 
 // D (lower 32 x 32) -= X X' with X 32 x 32 (zero beyond its rows), DMMA, the
-// contraction in steps of 4 as in PU.
+// contraction in steps of 4 as in PU.  The ten 8 x 8 tiles on and below the
+// diagonal are spread over the four warps (3, 3, 2, 2): DMMA throughput per
+// SM sub-partition, not latency, bounds this product on the chain.
 __device__ void pc_syrk(double* D, const double* X, int g) {
     const int lane = g & 31, wp = g >> 5, gi = lane >> 2, tq = lane & 3;
-    const int wr = (wp >> 1) * 16, wc = (wp & 1) * 16;
-    if (wr < wc) return;   // that quadrant lies above the diagonal
-    double acc[2][2][2] = {{{0.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 0.0}}};
+    for (int t = wp; t < 10; t += 4) {
+        const int tr = t < 1 ? 0 : t < 3 ? 1 : t < 6 ? 2 : 3;   // lower tiles in row order
+        const int tc = t - tr * (tr + 1) / 2;
+        double c0 = 0.0, c1 = 0.0;
 #pragma unroll
-    for (int kk = 0; kk < 32; kk += 4) {
-        double af[2], bf[2];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) af[a] = X[(wr + a * 8 + gi) * 33 + kk + tq];
-#pragma unroll
-        for (int b = 0; b < 2; ++b) bf[b] = X[(wc + b * 8 + gi) * 33 + kk + tq];
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) dmma884(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
+        for (int kk = 0; kk < 32; kk += 4)
+            dmma884(c0, c1, X[(tr * 8 + gi) * 33 + kk + tq], X[(tc * 8 + gi) * 33 + kk + tq]);
+        const int rr = tr * 8 + gi, cc = tc * 8 + 2 * tq;
+        if (rr >= cc) D[rr * 33 + cc] -= c0;
+        if (rr >= cc + 1) D[rr * 33 + cc + 1] -= c1;
     }
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int rr = wr + a * 8 + gi, cc = wc + b * 8 + 2 * tq + e;
-                if (rr >= cc) D[rr * 33 + cc] -= acc[a][b][e];
-            }
 }
 
 __device__ bool g2_pchain(const DagArgs& A, const ProbDev& P, G2Smem& S, int k, int g) {
@@ -487,15 +480,19 @@ __device__ bool g2_pchain(const DagArgs& A, const ProbDev& P, G2Smem& S, int k, 
     double* T = dp_tile(L, k, k);
     double* D = S.pot.D;
     double* X = S.pot.X;
+    long long t0 = 0, t1 = 0, t2 = 0;   // sub-step times for the optional task trace (thread 0)
     for (int s = 0; s < ns; ++s) {
         const int c0 = s * 32, w = min(32, nb - c0);
         // (s,s) after the other workers' updates t <= s-2; the last one, from
         // the block solved in the previous step, is applied here
+        if (g == 0 && A.trace) t0 = gtimer();
         if (g == 0) S.rows_ok = (s < 2 || wait_ge(A, L, pot_at(P, k, s, s), s - 1, 46)) ? 1 : 0;
+        if (g == 0 && A.trace) t1 = gtimer();
         g2_sync();
         if (!S.rows_ok) return false;
-        for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
-            const int r = idx % 32, c = idx / 32;
+#pragma unroll
+        for (int u = 0; u < 32 * 32 / G2_THREADS; ++u) {   // all loads in flight at once
+            const int idx = g + u * G2_THREADS, r = idx % 32, c = idx / 32;
             D[r * 33 + c] = (r < w && c < w && r >= c) ? T[(size_t)(c0 + c) * nb + c0 + r] : 0.0;
         }
         g2_sync();
@@ -511,14 +508,20 @@ __device__ bool g2_pchain(const DagArgs& A, const ProbDev& P, G2Smem& S, int k, 
         __threadfence();
         g2_sync();
         if (g == 0) red_release_add(pot_at(P, k, s, s), s == 0 ? 1 : 2);
+        if (g == 0 && A.trace) {
+            t2 = gtimer();
+            trace_put(A, 12, k, s, 0, 0, t0, t1, t2);   // wait, then update + factor of (s,s)
+        }
         if (s + 1 == ns) break;
         // PT(s+1, s) after the other workers' updates t < s of that block
         const int r0 = c0 + 32, h = min(32, nb - r0);
         if (g == 0) S.rows_ok = (s == 0 || wait_ge(A, L, pot_at(P, k, s + 1, s), s, 47)) ? 1 : 0;
+        if (g == 0 && A.trace) t1 = gtimer();
         g2_sync();
         if (!S.rows_ok) return false;
-        for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
-            const int a = idx % 32, b = idx / 32;
+#pragma unroll
+        for (int u = 0; u < 32 * 32 / G2_THREADS; ++u) {
+            const int idx = g + u * G2_THREADS, a = idx % 32, b = idx / 32;
             X[a * 33 + b] = (a < h && b < w) ? T[(size_t)(c0 + b) * nb + r0 + a] : 0.0;
         }
         g2_sync();
@@ -530,6 +533,92 @@ __device__ bool g2_pchain(const DagArgs& A, const ProbDev& P, G2Smem& S, int k, 
         __threadfence();
         g2_sync();
         if (g == 0) red_release_add(pot_at(P, k, s + 1, s), 1);
+        if (g == 0 && A.trace) trace_put(A, 13, k, s, 0, 0, t2, t1, gtimer());   // wait, then solve of (s+1,s)
+    }
+    return true;
+}
+
+// ---- PC2(k): the chain one sub-block below PC(k).  For each s it solves
+// (s+2, s) against L(s,s) as soon as PF(s) is done, then applies (s+2, s+1) -=
+// L(s+2, s) L(s+1, s)', the update PT(s+2, s+1) of PC's next step waits for.
+// Run as separate tasks these two links, each paying a claim, a dependency
+// wait and reloads, set the pace of PC; here they overlap PC's own work.
+// Raises pot(s+2, s) and pot(s+2, s+1) by 1 each.
+__device__ bool g2_pchain2(const DagArgs& A, const ProbDev& P, G2Smem& S, int k, int g) {
+    const Layout& L = P.L;
+    const int nb = L.nb, ns = P.g.ns;
+    const int lane = g & 31, wp = g >> 5, gi = lane >> 2, tq = lane & 3;
+    double* T = dp_tile(L, k, k);
+    double* D = S.pot.D;
+    double* X = S.pot.X;
+    for (int s = 0; s + 2 < ns; ++s) {
+        const int c0 = s * 32, r0 = c0 + 64, q0 = c0 + 32;
+        const int w = 32, h = min(32, nb - r0);
+        // PT(s+2, s): L(s,s) final, and the other workers' updates t < s of (s+2, s)
+        if (g == 0)
+            S.rows_ok = (wait_ge(A, L, pot_at(P, k, s, s), s + 1, 48) &&
+                         (s == 0 || wait_ge(A, L, pot_at(P, k, s + 2, s), s, 49)))
+                            ? 1
+                            : 0;
+        g2_sync();
+        if (!S.rows_ok) return false;
+#pragma unroll
+        for (int u = 0; u < 32 * 32 / G2_THREADS; ++u) {
+            const int idx = g + u * G2_THREADS, a = idx % 32, b = idx / 32;
+            D[a * 33 + b] = (a >= b) ? T[(size_t)(c0 + b) * nb + c0 + a] : 0.0;
+            X[a * 33 + b] = (a < h) ? T[(size_t)(c0 + b) * nb + r0 + a] : 0.0;
+        }
+        g2_sync();
+        pc_solve(D, X, h, w, g);
+        for (int idx = g; idx < 32 * 32; idx += G2_THREADS) {
+            const int a = idx % 32, b = idx / 32;
+            if (a < h) T[(size_t)(c0 + b) * nb + r0 + a] = X[a * 33 + b];
+        }
+        __threadfence();
+        g2_sync();
+        if (g == 0) red_release_add(pot_at(P, k, s + 2, s), 1);
+        // PU(s+2, s+1, s): L(s+1, s) from PC, and the updates t < s of (s+2, s+1)
+        if (g == 0)
+            S.rows_ok = (wait_ge(A, L, pot_at(P, k, s + 1, s), s + 1, 57) &&
+                         (s == 0 || wait_ge(A, L, pot_at(P, k, s + 2, s + 1), s, 58)))
+                            ? 1
+                            : 0;
+        g2_sync();
+        if (!S.rows_ok) return false;
+#pragma unroll
+        for (int u = 0; u < 32 * 32 / G2_THREADS; ++u) {
+            const int idx = g + u * G2_THREADS, a = idx % 32, b = idx / 32;
+            D[a * 33 + b] = T[(size_t)(c0 + b) * nb + q0 + a];   // L(s+1, s): 32 full rows
+        }
+        g2_sync();
+        {
+            const int wr = (wp >> 1) * 16, wc = (wp & 1) * 16;
+            double acc[2][2][2] = {{{0.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 0.0}}};
+#pragma unroll
+            for (int kk = 0; kk < 32; kk += 4) {
+                double af[2], bf[2];
+#pragma unroll
+                for (int a = 0; a < 2; ++a) af[a] = X[(wr + a * 8 + gi) * 33 + kk + tq];
+#pragma unroll
+                for (int b = 0; b < 2; ++b) bf[b] = D[(wc + b * 8 + gi) * 33 + kk + tq];
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) dmma884(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int rr = wr + a * 8 + gi, cc = wc + b * 8 + 2 * tq + e;
+                        if (rr < h) T[(size_t)(q0 + cc) * nb + r0 + rr] -= acc[a][b][e];
+                    }
+        }
+        __threadfence();
+        g2_sync();
+        if (g == 0) red_release_add(pot_at(P, k, s + 2, s + 1), 1);
     }
     return true;
 }
@@ -843,6 +932,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                     ok = ok && wait_ge(A, L, pot_at(P, k, t.a, t.a), t.a, 12);
                     break;
                 case T_PC:   // the tile's trailing updates; the chain waits for the rest as it goes
+                case T_PC2:
                     ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 11);
                     break;
                 case T_PT:
@@ -897,6 +987,9 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 break;
             case T_PC:   // signals its own sub-blocks as it goes
                 ran = g2_pchain(A, P, S, t.k, g);
+                break;
+            case T_PC2:
+                ran = g2_pchain2(A, P, S, t.k, g);
                 break;
             case T_PT:
                 g2_pt(P, S, t.k, t.a, t.b, g);
@@ -1391,6 +1484,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                     if (diag) ncol = min(ncol, max(0, r - c_begin + 1));   // lower triangle only
                     double* Crow = C + (size_t)c_begin * nb + (rv ? r : 0);
                     for (int kp = 0; kp < nkp; ++kp) {
+                        const long long tp0 = (A.trace && threadIdx.x == 64) ? gtimer() : 0;
                         double cpre[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) cpre[e] = (e < ncol) ? Crow[(size_t)e * nb] : 0.0;
@@ -1399,6 +1493,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                             ok = false;
                             break;
                         }
+                        const long long tp1 = (A.trace && threadIdx.x == 64) ? gtimer() : 0;
                         tc_fence_after();
 #pragma unroll 1
                         for (int cc = 0; cc < EX_BN; cc += 8) {
@@ -1427,6 +1522,8 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                         mbar_arrive(TEMPTY(1));
                         ++use0;
                         ++use1;
+                        if (A.trace && threadIdx.x == 64)   // one (slice, part): products done, drained
+                            trace_put(A, 14, k, i, j, h * nkp + kp, tp0, tp1, gtimer());
                     }
                 }
                 if (!ok) {

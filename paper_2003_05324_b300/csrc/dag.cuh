@@ -9,12 +9,13 @@
 
 namespace geo {
 
-enum TaskType : int { T_PF = 0, T_PT = 1, T_PU = 2, T_TRSM = 3, T_UPD = 4, T_YD = 5, T_YG = 6, T_PC = 7 };
+enum TaskType : int { T_PF = 0, T_PT = 1, T_PU = 2, T_TRSM = 3, T_UPD = 4, T_YD = 5, T_YG = 6, T_PC = 7, T_PC2 = 8 };
 
 // One CUDA-core task: PF(k; a = s), PT(k; a = r, b = s), PU(k; a = r, b = c, c = s),
 // TRSM(k; a = i, b = row chunk), UPD(k; a = i, b = j, c = 64 x 64 sub-block),
 // YD(k) diagonal forward solve of block row k, YG(k; a = i, b = row chunk)
-// r_i -= L(i,k) y_k, PC(k) the critical chain of dpotrf(k) (see dag.cu);
+// r_i -= L(i,k) y_k, PC(k) the critical chain of dpotrf(k) and PC2(k) the
+// chain one sub-block below it (see dag.cu);
 // pid: the problem it belongs to (0 in a single-problem launch).
 struct G2Task {
     int type, k, a, b, c, pid;
