@@ -57,6 +57,13 @@ namespace geo {
 // ------------------------------------------------------------- host side ---
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// Rows per panel-solve task: FP64 (in-band) tiles in chunks of 32 rows, each
+// row's contraction split over the group's four warps (FP64 is per warp
+// instruction and slow on this part, so one warp per 32 rows would set the
+// pace of the whole step); FP32 tiles in chunks of 128, one thread per row.
+constexpr int DP_TRSM_ROWS = 32;
+constexpr int SP_TRSM_ROWS = 128;
+
 SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     SchedGeom g;
     g.p = p;
@@ -65,8 +72,8 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     g.nsb64 = ceil_div(nb, 64);
     g.items64 = g.nsb64 * g.nsb64;
     g.items_tc = ceil_div(pp, TC_BM) * ceil_div(pp, TC_BN);
-    g.chunks_dp = ceil_div(nb, 128);
-    g.chunks_sp = ceil_div(nb, 128);
+    g.chunks_dp = ceil_div(nb, DP_TRSM_ROWS);
+    g.chunks_sp = ceil_div(nb, SP_TRSM_ROWS);
     g.chunks_y = ceil_div(nb, 128);
     // counters: grab counters, upd[p*p], tcnt[p*p], pot[p*ns*ns], sub[p*p*maxitems],
     // ycnt[p*chunks_y], ydone[p]
@@ -267,6 +274,12 @@ struct G2Smem {
         struct {
             double Lb[(16 * 32 + 32 * 33) / 2 + 8];  // TRSM: 16 x SB stage + SB x SB diagonal block
         } tr;
+        struct {                                     // FP64 TRSM (g2_trsm_dp)
+            double Ls[4][16 * 8];                    // per-warp 16 x 8 stage of L_kk
+            double part[3][32][9];                   // warps 1..3: partial sums per row
+            double Ld[8 * 17];                       // diagonal 8 x 8 block
+            float rmax[32];                          // row maxima for the slicing
+        } trd;
         YSolveSmem yd;                               // YD: diagonal forward solve
         double yk[YS_MAX_NB];                        // YG: y_k
     };
@@ -754,6 +767,132 @@ __device__ void g2_slice_row(const Layout& L, const T* __restrict__ X, int i, in
     }
 }
 
+// FP64 panel solve of rows [r0, r0 + 32) of tile (i,k) against L_kk: lane l
+// owns row r0 + l; for each 8-column super-block the contraction over the
+// earlier columns is split over the four warps (16-column stages dealt in
+// turn, each stage summed in registers), the partials are added in a fixed
+// order, and warp 0 finishes the diagonal block.  ready(hi) as in
+// g2_trsm_rows.  Leaves each row's max |x| in S.trd.rmax; false if abandoned.
+// (8 columns at a time keep the registers of this path below those of the
+// tensor group's epilogue, which shares the kernel's register budget.)
+template <typename Ready>
+__device__ bool g2_trsm_dp(const double* __restrict__ Lkk, double* __restrict__ X, int nb, int r0, int g,
+                           G2Smem& S, Ready& ready) {
+    constexpr int SB = 8, TS = 16;
+    const int lane = g & 31, wp = g >> 5, r = r0 + lane;
+    const bool valid = r < nb;
+    double* Ls = S.trd.Ls[wp];
+    float rowmax = 0.0f;
+    for (int sb0 = 0; sb0 < nb; sb0 += SB) {
+        const int w = min(SB, nb - sb0);
+        if (!ready(sb0 + w)) return false;
+        double part[SB];
+#pragma unroll
+        for (int jj = 0; jj < SB; ++jj) part[jj] = 0.0;
+        const int tend = sb0 & ~(TS - 1);   // whole stages of TS earlier columns; the rest below
+        for (int t0 = TS * wp; t0 < tend; t0 += 4 * TS) {
+#pragma unroll
+            for (int u = 0; u < TS * SB / 32; ++u) {
+                const int idx = lane + 32 * u, tt = idx / SB, jj = idx % SB;
+                Ls[idx] = (jj < w) ? Lkk[(size_t)(t0 + tt) * nb + sb0 + jj] : 0.0;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int tt = 0; tt < TS; ++tt) {
+                const double xv = valid ? X[(size_t)(t0 + tt) * nb + r] : 0.0;
+#pragma unroll
+                for (int jj = 0; jj < SB; ++jj) part[jj] = fma(xv, Ls[tt * SB + jj], part[jj]);
+            }
+            __syncwarp();
+        }
+        if (wp == 0) {
+            // the columns [tend, sb0) (a partial stage) and the diagonal block
+            for (int idx = lane; idx < SB * SB; idx += 32) {
+                const int jj = idx / SB, ii = idx % SB;
+                S.trd.Ld[jj * 17 + ii] = (jj < w && ii <= jj) ? Lkk[(size_t)(sb0 + ii) * nb + sb0 + jj] : 0.0;
+            }
+            for (int t = tend; t < sb0; ++t) {
+                const double xv = valid ? X[(size_t)t * nb + r] : 0.0;
+#pragma unroll
+                for (int jj = 0; jj < SB; ++jj)
+                    part[jj] = fma(xv, (jj < w) ? Lkk[(size_t)t * nb + sb0 + jj] : 0.0, part[jj]);
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < SB; ++jj) S.trd.part[wp - 1][lane][jj] = part[jj];
+        }
+        g2_sync();
+        if (wp == 0 && valid) {
+            double acc[SB];
+#pragma unroll
+            for (int jj = 0; jj < SB; ++jj) {
+                const double s4 = (part[jj] + S.trd.part[0][lane][jj]) + (S.trd.part[1][lane][jj] + S.trd.part[2][lane][jj]);
+                acc[jj] = (jj < w) ? X[(size_t)(sb0 + jj) * nb + r] - s4 : 0.0;
+            }
+#pragma unroll
+            for (int jj = 0; jj < SB; ++jj) {
+                if (jj < w) {
+                    const double xv = acc[jj] / S.trd.Ld[jj * 17 + jj];
+                    acc[jj] = xv;
+#pragma unroll
+                    for (int j2 = jj + 1; j2 < SB; ++j2) acc[j2] = fma(-xv, S.trd.Ld[j2 * 17 + jj], acc[j2]);
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < SB; ++jj)
+                if (jj < w) {
+                    X[(size_t)(sb0 + jj) * nb + r] = acc[jj];
+                    rowmax = fmaxf(rowmax, fabsf((float)acc[jj]));
+                }
+        }
+        g2_sync();
+    }
+    if (wp == 0) S.trd.rmax[lane] = rowmax;
+    g2_sync();
+    return true;
+}
+
+// Fixed-point slicing of the 32 rows solved by g2_trsm_dp: each warp slices a
+// quarter of the padded columns of every row (lane = row), FP64 values.
+__device__ void g2_slice_rows_dp(const Layout& L, const double* __restrict__ X, int i, int k, int r0, int g,
+                                 G2Smem& S) {
+    const int nb = L.nb, pp = L.pp, lane = g & 31, wp = g >> 5, r = r0 + lane;
+    if (r >= nb) return;
+    const int e = row_exponent(S.trd.rmax[lane]);
+    const int slot = L.slot[i * L.p + k];
+    if (wp == 0) L.rexp[(size_t)slot * pp + r] = e;
+    __nv_bfloat16* P0 = plane(L, i, k, 0) + (size_t)r * pp;
+    const size_t pstride = (size_t)pp * pp;
+    const int q4 = pp / 4;   // pp is a multiple of 64: quarters of 16 columns or more
+    for (int c0 = wp * q4; c0 < (wp + 1) * q4; c0 += 8) {
+        __align__(16) __nv_bfloat16 sl[NPL][8];
+        __align__(16) __half sh[NPLH][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = c0 + q;
+            const double v = (c < nb) ? X[(size_t)c * nb + r] : 0.0;
+            __nv_bfloat16 d[NPL];
+            slice_value<double>(v, e, d);
+#pragma unroll
+            for (int s2 = 0; s2 < NPL; ++s2) sl[s2][q] = d[s2];
+            if (L.npl > NPL) {
+                __half dh[NPLH];
+                slice_value_h<double>(v, e, dh);
+#pragma unroll
+                for (int s2 = 0; s2 < NPLH; ++s2) sh[s2][q] = dh[s2];
+            }
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < NPL; ++s2)
+            *reinterpret_cast<uint4*>(P0 + s2 * pstride + c0) = *reinterpret_cast<const uint4*>(sl[s2]);
+        if (L.npl > NPL) {
+#pragma unroll
+            for (int s2 = 0; s2 < NPLH; ++s2)
+                *reinterpret_cast<uint4*>(P0 + (NPL + s2) * pstride + c0) = *reinterpret_cast<const uint4*>(sh[s2]);
+        }
+    }
+}
+
 // UPD(k,i,j,q): 64 x 64 sub-block q of target (i,j) -= A(i,k) A(j,k)' in FP64.
 __device__ void g2_upd(const ProbDev& P, G2Smem& S, int k, int i, int j, int q, int g) {
     const Layout& L = P.L;
@@ -1002,7 +1141,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
             case T_TRSM: {
                 const int i = t.a, k = t.k, q = t.b;
                 const double* Lkk = dp_tile(L, k, k);
-                const int r = q * 128 + g;
+                const int r = q * SP_TRSM_ROWS + g;
                 // POTRF(k) finishes L_kk's 32-row sub-blocks in order (sub-block
                 // row s is final once (s,s) is factored): the solve of this tile
                 // runs alongside it, waiting only before rows not yet final
@@ -1017,12 +1156,11 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 };
                 if (is_dp(i, k, L.band)) {
                     double* X = dp_tile(L, i, k);
-                    const float m = g2_trsm_rows<double, 16>(Lkk, X, nb, q * 128, 128, g, S, ready);
-                    ran = m >= 0.0f;
-                    if (ran && L.planes && r < nb) g2_slice_row<double>(L, X, i, k, r, m);
+                    ran = g2_trsm_dp(Lkk, X, nb, q * DP_TRSM_ROWS, g, S, ready);
+                    if (ran && L.planes) g2_slice_rows_dp(L, X, i, k, q * DP_TRSM_ROWS, g, S);
                 } else {
                     float* X = sp_tile(L, i, k);
-                    const float m = g2_trsm_rows<float, 32>(Lkk, X, nb, q * 128, 128, g, S, ready);
+                    const float m = g2_trsm_rows<float, 32>(Lkk, X, nb, q * SP_TRSM_ROWS, SP_TRSM_ROWS, g, S, ready);
                     ran = m >= 0.0f;
                     if (ran && L.planes && r < nb) g2_slice_row<float>(L, X, i, k, r, m);
                 }
