@@ -6,17 +6,21 @@
 //   tensor group (warps 0..5)  trailing updates on the tensor cores: TMA warp,
 //                              single-thread MMA issue, 4 epilogue warps, items
 //                              (128 x 128 output blocks) taken one at a time from
-//                              the tensor queue.  Off-band targets: the
-//                              FP32-accurate sgemm of lp_gemm.cu; in-band (FP64)
+//                              the tensor queue.  Off-band targets: FP32-accurate
+//                              products of FP16 slice planes (six MMAs per K
+//                              step, tc_common.cuh); in-band (FP64)
 //                              targets, by default: the FP64-accurate dsyrk /
 //                              dgemm of the seven-slice products (tc_common.cuh);
 //   CUDA-core group (warps 6..9) everything else, from the CUDA-core queue:
-//       PF(k,s)      dpotrf of 32 x 32 sub-block (s,s) of diagonal tile k
-//       PT(k,r,s)    solve of sub-block (r,s) against it
+//       PC(k)        critical chain of dpotrf(k): for each 32 x 32 sub-block
+//                    step s, the factor of (s,s), the solve of (s+1,s) and
+//                    the update of (s+1,s+1)
+//       PC2(k)       the chain below it: solve of (s+2,s), update of (s+2,s+1)
+//       PT(k,r,s)    solve of sub-block (r,s) against L(s,s)
 //       PU(k,r,c,s)  sub-block update (r,c) -= (r,s)(c,s)'      (DMMA f64)
 //       TRSM(k,i,q)  rows of panel tile (i,k): dtrsm (band) or strsm (off band),
 //                    followed, for tensor-core mode, by the fixed-point slicing
-//                    of the solved rows (row exponent + four BF16 planes)
+//                    of the solved rows (row exponent + slice planes)
 //       UPD(k,i,j,q) 64 x 64 sub-block of a dsyrk / in-band dgemm    (DMMA f64;
 //                    only with GEO_FLAG_FP64_DMMA, otherwise these updates
 //                    are tensor items)
@@ -27,12 +31,17 @@
 //               of step k waits only for step k-1 on its own sub-block)
 //   tcnt[i][k]  solved row chunks of panel tile (i,k)
 //   pot[k][r][c] operations applied to sub-block (r,c) of diagonal tile k, in
-//               order: PU for s = 0..min(r,c)-1, then PT (r > c) or PF (r == c)
+//               order: PU for s = 0..min(r,c)-1, then PT (r > c) or the
+//               factor (r == c), whichever task (PT, PU, PC, PC2) runs them
 // The queues are ordered topologically:
-//   priority:  A(0) C(0) A(1) C(1) ...     A(k) = potrf(k) sub-tasks + trsm(k),
+//   priority:  A(0) C(0) A(1) C(1) ...     A(k) = PC(k) PC2(k), the other
+//                                          potrf(k) sub-tasks, trsm(k),
 //                                          C(k) = FP64 items of step k on column k+1
 //   bulk:      B(0) B(1) ...               B(k) = FP64 items of step k on columns >= k+2
 //   tensor:    C'(0) B'(0) C'(1) B'(1) ... (tensor items, same split by column)
+//   solve:     YD(0) YG(0;..) YD(1) ...    forward solve L y = Z fused into the
+//                                          factorization; its head is claimed
+//                                          only once its inputs are final
 // (with the in-band updates on the tensor cores, C(k) and B(k) are empty).
 // At most PRIO_LIMIT CUDA-core groups work in the priority queue at once (its
 // tasks form narrow dependency chains; the others keep the FP64 pipes busy with
@@ -269,7 +278,7 @@ struct G2Smem {
             double As[2][64 * 12], Bs[2][64 * 12];   // UPD: double-buffered K chunks of 8
         } upd;
         struct {
-            double D[32 * 33], X[32 * 33];           // PF / PT / PU operands
+            double D[32 * 33], X[32 * 33];           // PC / PT / PU operands
         } pot;
         struct {
             double Lb[(16 * 32 + 32 * 33) / 2 + 8];  // TRSM: 16 x SB stage + SB x SB diagonal block
@@ -285,53 +294,6 @@ struct G2Smem {
     };
     int task, kind, ok, rows_ok;
 };
-
-// PF(k,s): FP64 Cholesky of the 32 x 32 sub-block (s,s), right-looking in
-// shared memory with the whole group: per column c, every thread takes
-// r = 1/sqrt(d_cc); lane i scales row c+i of column c; then the trailing lower
-// triangle is updated with lanes over rows and the four warps over columns
-// (column j handled by warp j mod 4).  FP64 throughput per SM sub-partition is
-// tiny on this part, so spreading the updates over the four warps (and
-// replacing divisions by one reciprocal square root) shortens this task, which
-// is on the factorization's critical path.
-__device__ bool g2_pf(const ProbDev& P, G2Smem& S, int k, int s, int g) {
-    const Layout& L = P.L;
-    const int nb = L.nb, c0 = s * 32, w = min(32, nb - c0), lane = g & 31, wp = g >> 5;
-    double* T = dp_tile(L, k, k);
-    double* D = S.pot.D;
-    for (int idx = g; idx < w * w; idx += G2_THREADS) {
-        const int r = idx % w, c = idx / w;
-        D[r * 33 + c] = T[(size_t)(c0 + c) * nb + c0 + r];
-    }
-    g2_sync();
-    bool ok = true;
-    for (int c = 0; c < w; ++c) {
-        const double d = D[c * 33 + c];
-        if (!(d > 0.0)) {   // the same d in every thread: all leave together
-            if (g == 0 && atomicCAS(L.status + ST_CODE, 0, GEO_ERR_NOT_SPD) == 0)
-                L.status[ST_INFO] = k * nb + c0 + c + 1;
-            ok = false;
-            break;
-        }
-        const double rs = rsqrt(d);
-        g2_sync();   // everyone has read d before it is overwritten
-        if (g < w - c) D[(c + g) * 33 + c] = (g == 0) ? d * rs : D[(c + g) * 33 + c] * rs;
-        g2_sync();
-        const int i = c + 1 + lane;
-        if (i < w) {
-            const double li = D[i * 33 + c];
-            int j = c + 1 + ((wp - (c + 1)) & 3);
-            for (; j <= i; j += 4) D[i * 33 + j] = fma(-li, D[j * 33 + c], D[i * 33 + j]);
-        }
-        g2_sync();
-    }
-    if (!ok) return false;
-    for (int idx = g; idx < w * w; idx += G2_THREADS) {
-        const int r = idx % w, c = idx / w;
-        if (r >= c) T[(size_t)(c0 + c) * nb + c0 + r] = D[r * 33 + c];
-    }
-    return true;
-}
 
 // PT(k,r,s): X(r,s) <- X(r,s) L(s,s)^-T, right-looking over the 32 columns:
 // lane i scales row i of column c by 1/L_cc, then row i of the later columns
@@ -1066,10 +1028,6 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
             if (ok && kind == 1 && ld_volatile(prio_head) < P.trsm_end[k])
                 ok = wait_ge(A, L, prio_head, P.trsm_end[k], 25);
             if (ok) switch (t.type) {
-                case T_PF:
-                    if (t.a == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 11);
-                    ok = ok && wait_ge(A, L, pot_at(P, k, t.a, t.a), t.a, 12);
-                    break;
                 case T_PC:   // the tile's trailing updates; the chain waits for the rest as it goes
                 case T_PC2:
                     ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 11);
@@ -1120,10 +1078,6 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
         int* done = nullptr;
         bool ran = true;
         switch (t.type) {
-            case T_PF:
-                ran = g2_pf(P, S, t.k, t.a, g);   // false: not positive definite (status set)
-                done = pot_at(P, t.k, t.a, t.a);
-                break;
             case T_PC:   // signals its own sub-blocks as it goes
                 ran = g2_pchain(A, P, S, t.k, g);
                 break;

@@ -9,9 +9,10 @@
 
 namespace geo {
 
-enum TaskType : int { T_PF = 0, T_PT = 1, T_PU = 2, T_TRSM = 3, T_UPD = 4, T_YD = 5, T_YG = 6, T_PC = 7, T_PC2 = 8 };
+// (type 0 is unused: the sub-block factors run inside PC)
+enum TaskType : int { T_PT = 1, T_PU = 2, T_TRSM = 3, T_UPD = 4, T_YD = 5, T_YG = 6, T_PC = 7, T_PC2 = 8 };
 
-// One CUDA-core task: PF(k; a = s), PT(k; a = r, b = s), PU(k; a = r, b = c, c = s),
+// One CUDA-core task: PT(k; a = r, b = s), PU(k; a = r, b = c, c = s),
 // TRSM(k; a = i, b = row chunk), UPD(k; a = i, b = j, c = 64 x 64 sub-block),
 // YD(k) diagonal forward solve of block row k, YG(k; a = i, b = row chunk)
 // r_i -= L(i,k) y_k, PC(k) the critical chain of dpotrf(k) and PC2(k) the
