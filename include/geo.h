@@ -93,7 +93,8 @@ typedef struct geo_tiles {
 /* One record of the device-side task trace (tensor-core mode scheduler):
  * type 0..4 = potrf sub-block factor / solve / update, panel trsm, FP64 (DMMA)
  * update item; 5, 6 = forward-solve diagonal / block-row task; 7, 8 = the
- * dpotrf chain tasks PC, PC2 (a = 0); 10 = tensor-core off-band update item,
+ * dpotrf chain tasks PC, PC2 (a = 0); 10 = tensor-core off-band update item
+ * (t_claim = its epilogue started, t_ready = its products were done),
  * 11 = tensor-core in-band (FP64-accurate) update item; 12, 13 = one sub-step
  * s (in a) of PC: the factor of (s,s), the solve of (s+1,s), with t_claim =
  * sub-step start, t_ready = its dependencies met, t_end = done; 14 = one

@@ -164,13 +164,22 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
     // tensor queue in right-looking order, C'(k) B'(k) per step.  (A
     // left-looking order -- all updates of column j before column j+1 -- was
     // measured 2x slower: it chains the j updates of each block of the next
-    // panel into the critical path.)
+    // panel into the critical path.)  B'(k) takes column k+2 (the next step's
+    // look-ahead column) first, then the other columns in groups of SWEEP_W,
+    // row by row: the items in flight then read the panel blocks of one row
+    // and of SWEEP_W columns instead of sweeping the whole panel once per
+    // column, which keeps more of the panel's slice planes in L2.
+    constexpr int SWEEP_W = 8;
     for (int k = 0; k < p; ++k) {
         for (int i = k + 1; i < p; ++i)                  // C'(k): column k+1
             if (ex || !is_dp(i, k + 1, band)) tct.push_back(make_int4(i, k + 1, k, 0));
-        for (int j = k + 2; j < p; ++j)                  // B'(k): columns >= k+2
+        for (int j = k + 2; j < std::min(p, k + 3); ++j)   // B'(k): column k+2
             for (int i = j; i < p; ++i)
                 if (ex || !is_dp(i, j, band)) tct.push_back(make_int4(i, j, k, 0));
+        for (int j0 = k + 3; j0 < p; j0 += SWEEP_W)       // columns >= k+3
+            for (int i = j0; i < p; ++i)
+                for (int j = j0; j < std::min(j0 + SWEEP_W, i + 1); ++j)
+                    if (ex || !is_dp(i, j, band)) tct.push_back(make_int4(i, j, k, 0));
     }
 }
 
@@ -1493,6 +1502,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             // it; when its problem has failed (batched launch) the item's TMEM is
             // still consumed, but nothing is written
             const long long te0 = gtimer();
+            long long te1 = te0;   // products done (off-band), for the trace
             if (threadIdx.x == 64) {
                 s_epi_skip = 0;
                 if (!wait_ge(A, L, sub_at(P, i, j, m.rem), k, 38)) {
@@ -1524,6 +1534,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                     *abort_flag = 1;
                     break;
                 }
+                if (A.trace) te1 = gtimer();
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + tlane + b * (2 * TC_BN);
 #pragma unroll 1
@@ -1629,7 +1640,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             if (threadIdx.x == 64 && write) {
                 red_release_add(sub_at(P, i, j, m.rem), 1);
                 red_release_add(P.upd + i * p + j, 1);
-                trace_put(A, m.ex ? 11 : 10, k, i, j, m.rem, te0, te0, gtimer());
+                trace_put(A, m.ex ? 11 : 10, k, i, j, m.rem, te0, te1, gtimer());
             }
         }
     }
