@@ -675,14 +675,16 @@ int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_
     cudaStream_t s = (cudaStream_t)stream;
     char* base = (char*)d_work;
     const geo_theta dummy = {1.0, 1.0, 0.5, 0.0};
+    bool small_dp = false;
     for (int b = 0; b < nprob; ++b) {
         const Layout L = make_layout(items[b].t);
+        small_dp = small_dp || dag_small_dp(L.nb, L.band);
         if (launch_matern_tiles(L, items[b].d_x, items[b].d_y, dummy, d_theta + b, 1, s)) return GEO_ERR_CUDA;
     }
     if (run_potrf_dag_batch((const ProbDev*)(base + m.off_probs), nprob, (const G2Task*)(base + m.off_prio),
                             m.n_prio, (const G2Task*)(base + m.off_bulk), m.n_bulk,
                             (const int4*)(base + m.off_tct), m.n_tct, m.per, (int*)(base + m.off_ctr),
-                            m.counter_bytes, items[0].t->trace, items[0].t->trace_cap, s))
+                            m.counter_bytes, items[0].t->trace, items[0].t->trace_cap, small_dp, s))
         return GEO_ERR_CUDA;
     if (launch_trsv_batch((const SolveJob*)(base + m.off_jobs), nprob, m.pmax, d_out,
                           (unsigned*)(base + m.off_ctr) + 8, s))

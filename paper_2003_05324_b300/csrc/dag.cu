@@ -66,12 +66,21 @@ namespace geo {
 // ------------------------------------------------------------- host side ---
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-// Rows per panel-solve task: FP64 (in-band) tiles in chunks of 32 rows, each
-// row's contraction split over the group's four warps (FP64 is per warp
-// instruction and slow on this part, so one warp per 32 rows would set the
-// pace of the whole step); FP32 tiles in chunks of 128, one thread per row.
+// Rows per panel-solve task: FP64 (in-band) tiles of at least DP_SPLIT_MIN_NB
+// rows in chunks of 32 rows, each row's contraction split over the group's four
+// warps (FP64 is per warp instruction and slow on this part, so one warp per 32
+// rows would set the pace of the whole step); smaller FP64 tiles, and FP32
+// tiles, in chunks of 128, one thread per row.  (On tiles of 128 the split's
+// per-column-block diagonal solves cost more SM time than they save, and the
+// many-problem launches that use such tiles have parallelism to spare: the
+// all-FP64 batch of 256 problems took 3.69 s with the split and 3.13 s
+// without; on tiles of 500 the split halves the step.)  The row-per-thread
+// FP64 solve lives only in the kernel instantiation of launches that hold such
+// tiles (dag_kernel<true>): in the other one its code would cost the FP32 and
+// tensor paths registers.
 constexpr int DP_TRSM_ROWS = 32;
 constexpr int SP_TRSM_ROWS = 128;
+__host__ __device__ inline int dp_trsm_rows(int nb) { return nb >= DP_SPLIT_MIN_NB ? DP_TRSM_ROWS : SP_TRSM_ROWS; }
 
 SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     SchedGeom g;
@@ -81,7 +90,7 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     g.nsb64 = ceil_div(nb, 64);
     g.items64 = g.nsb64 * g.nsb64;
     g.items_tc = ceil_div(pp, TC_BM) * ceil_div(pp, TC_BN);
-    g.chunks_dp = ceil_div(nb, DP_TRSM_ROWS);
+    g.chunks_dp = ceil_div(nb, dp_trsm_rows(nb));
     g.chunks_sp = ceil_div(nb, SP_TRSM_ROWS);
     g.chunks_y = ceil_div(nb, 128);
     // counters: grab counters, upd[p*p], tcnt[p*p], pot[p*ns*ns], sub[p*p*maxitems],
@@ -964,6 +973,7 @@ __device__ void abort_launch(const DagArgs& A, int where) {
     if (!A.probs) set_timeout(A.one.L, where);
 }
 
+template <bool kSmallDP>
 __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
     const int g = threadIdx.x - TC_THREADS;
     int* prio_head = A.ctr + 0;
@@ -1117,10 +1127,21 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                     s_done = s + 1;
                     return S.rows_ok != 0;
                 };
-                if (is_dp(i, k, L.band)) {
+                if (is_dp(i, k, L.band) && nb >= DP_SPLIT_MIN_NB) {
                     double* X = dp_tile(L, i, k);
                     ran = g2_trsm_dp(Lkk, X, nb, q * DP_TRSM_ROWS, g, S, ready);
                     if (ran && L.planes) g2_slice_rows_dp(L, X, i, k, q * DP_TRSM_ROWS, g, S);
+                } else if (is_dp(i, k, L.band)) {
+                    if constexpr (kSmallDP) {
+                        double* X = dp_tile(L, i, k);
+                        const float m =
+                            g2_trsm_rows<double, 16>(Lkk, X, nb, q * SP_TRSM_ROWS, SP_TRSM_ROWS, g, S, ready);
+                        ran = m >= 0.0f;
+                        if (ran && L.planes && r < nb) g2_slice_row<double>(L, X, i, k, r, m);
+                    } else {   // the host launches dag_kernel<true> for such tiles
+                        if (g == 0) abort_launch(A, 46);
+                        ran = false;
+                    }
                 } else {
                     float* X = sp_tile(L, i, k);
                     const float m = g2_trsm_rows<float, 32>(Lkk, X, nb, q * SP_TRSM_ROWS, SP_TRSM_ROWS, g, S, ready);
@@ -1646,6 +1667,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
     }
 }
 
+template <bool kSmallDP>
 __global__ void __launch_bounds__(DAG_THREADS, 1)
     dag_kernel(DagArgs A, const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
                const __grid_constant__ CUtensorMap tmap_b64) {
@@ -1685,7 +1707,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     if (threadIdx.x < TC_THREADS) tc_worker(A, &tmap_a, &tmap_b, &tmap_b64, smem, bars, tmem_base, abort_flag, ring);
-    else g2_worker(A, g2s);
+    else g2_worker<kSmallDP>(A, g2s);
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -1695,11 +1717,13 @@ __global__ void __launch_bounds__(DAG_THREADS, 1)
     }
 }
 
+template <bool kSmallDP>
 static cudaError_t dag_prepare(int& nsm) {
     static int attr_done = 0, nsm_cached = 0;
     cudaError_t e;
     if (!attr_done) {
-        if ((e = cudaFuncSetAttribute(dag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DAG_DYN_SMEM)))
+        if ((e = cudaFuncSetAttribute(dag_kernel<kSmallDP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)DAG_DYN_SMEM)))
             return e;
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1707,7 +1731,8 @@ static cudaError_t dag_prepare(int& nsm) {
         attr_done = 1;
     }
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dag_kernel, DAG_THREADS, DAG_DYN_SMEM))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dag_kernel<kSmallDP>, DAG_THREADS, DAG_DYN_SMEM)))
+        return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
     nsm = nsm_cached;
     return cudaSuccess;
@@ -1727,7 +1752,8 @@ void bind_counters(ProbDev& P, int* base) {
 cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, const double* z, double* res,
                           cudaStream_t s) {
     int nsm = 0;
-    cudaError_t e = dag_prepare(nsm);
+    const bool small_dp = dag_small_dp(L.nb, L.band);
+    cudaError_t e = small_dp ? dag_prepare<true>(nsm) : dag_prepare<false>(nsm);
     if (e) return e;
     if ((e = cudaMemsetAsync(sv.counters, 0, sizeof(int) * (size_t)sv.geom.n_counters, s))) return e;
     DagArgs A;
@@ -1757,7 +1783,8 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
     memcpy(maps, t->tmap, sizeof(maps));
     void* args[] = {&A, &maps[0], &maps[1], &maps[2]};
     prof_begin(4, s);
-    e = cudaLaunchCooperativeKernel((const void*)dag_kernel, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
+    e = cudaLaunchCooperativeKernel(small_dp ? (const void*)dag_kernel<true> : (const void*)dag_kernel<false>,
+                                    dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
     prof_end(4, s);
     count_launch();
     return e;
@@ -1822,9 +1849,9 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
                                 const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
                                 int* counters, size_t counter_bytes, void* trace, long long trace_cap,
-                                cudaStream_t s) {
+                                bool small_dp, cudaStream_t s) {
     int nsm = 0;
-    cudaError_t e = dag_prepare(nsm);
+    cudaError_t e = small_dp ? dag_prepare<true>(nsm) : dag_prepare<false>(nsm);
     if (e) return e;
     if ((e = cudaMemsetAsync(counters, 0, counter_bytes, s))) return e;
     DagArgs A;
@@ -1846,7 +1873,8 @@ cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task*
     memset(maps, 0, sizeof(maps));   // unused: each problem's maps are in its view
     void* args[] = {&A, &maps[0], &maps[1], &maps[2]};
     prof_begin(4, s);
-    e = cudaLaunchCooperativeKernel((const void*)dag_kernel, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
+    e = cudaLaunchCooperativeKernel(small_dp ? (const void*)dag_kernel<true> : (const void*)dag_kernel<false>,
+                                    dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
     prof_end(4, s);
     count_launch();
     return e;

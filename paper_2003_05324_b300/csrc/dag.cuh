@@ -22,6 +22,11 @@ struct G2Task {
     int type, k, a, b, c, pid;
 };
 
+// FP64 panel tiles of at least this many rows are solved in 32-row tasks with
+// the contraction split over the group's warps, smaller ones one row per thread
+constexpr int DP_SPLIT_MIN_NB = 256;
+inline bool dag_small_dp(int nb, int band) { return nb < DP_SPLIT_MIN_NB && band > 1; }
+
 struct SchedGeom {
     int p, ex, ns, nsb64, items64, items_tc, max_items, chunks_dp, chunks_sp, chunks_y;
     long long n_counters, n_g2, n_prio, n_bulk, n_tct, n_y;
@@ -77,9 +82,11 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
 void bind_counters(ProbDev& P, int* base);
 // probs: nprob device views in global memory (their counters inside `counters`,
 // zeroed by this call), queues in device memory as laid out by the caller.
+// small_dp: some problem has FP64 panel tiles (band > 1) of fewer than
+// DP_SPLIT_MIN_NB rows (dag_small_dp), solved one row per thread
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
                                 const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
                                 int* counters, size_t counter_bytes, void* trace, long long trace_cap,
-                                cudaStream_t s);
+                                bool small_dp, cudaStream_t s);
 
 }  // namespace geo
