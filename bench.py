@@ -391,11 +391,17 @@ def run_batch(geo, dev):
             "speedup_vs_fp64": statistics.median(dms) / t}
 
 
+SERVE_SWEEP_RATES = (2.0, 5.0, 10.0, 20.0, 50.0)
+SERVE_SWEEP_WINDOW = 4.0
+
+
 def run_serve(geo, dev, window):
     """Serving: 16 resident datasets (n ~ U[1k, 50k], four of them in [10k, 40k]
     hold a resident factor for kriging), Poisson arrivals at 200/s for `window`
     seconds, 70 % log-likelihood (random theta) and 30 % kriging (100 new
-    points, nu 1/2 or 3/2), admission by an HBM budget of 120 GB."""
+    points, nu 1/2 or 3/2), admission by an HBM budget of 120 GB; then the
+    same mix at SERVE_SWEEP_RATES for SERVE_SWEEP_WINDOW seconds each, to
+    locate the highest rate the server sustains."""
     import torch
     from paper_2003_05324_b300 import inputs, serve
     rng = np.random.default_rng(7)
@@ -416,24 +422,40 @@ def run_serve(geo, dev, window):
         dss.append(dict(x=xo[perm], y=yo[perm], z=zo[perm], theta=th, nb=500, krige=kr))
         truth.append((x[n:], y[n:], z[n:]) if kr else None)
     S = serve.Server(dss, hbm_budget_bytes=120 << 30, nb=500)
-    reqs, t = [], 0.0
-    q = 0
-    while True:
-        t += float(rng.exponential(1.0 / 200.0))
-        if t > window:
-            break
-        if rng.uniform() < 0.7:
-            d = int(rng.integers(0, 16))
-            reqs.append(serve.Request("loglik", d, theta=geo.Theta(float(rng.uniform(0.5, 2.0)),
-                                                                    float(rng.uniform(0.02, 0.3)), dss[d]["theta"].nu,
-                                                                    dss[d]["theta"].nugget),
-                                      t_arrival=t, id=q))
-        else:
-            d = int(rng.integers(12, 16))
-            xt, yt, _ = truth[d]
-            reqs.append(serve.Request("krige", d, xnew=xt, ynew=yt, t_arrival=t, id=q))
-        q += 1
+
+    def arrivals(rate, win, rng):
+        reqs, t, q = [], 0.0, 0
+        while True:
+            t += float(rng.exponential(1.0 / rate))
+            if t > win:
+                return reqs
+            if rng.uniform() < 0.7:
+                d = int(rng.integers(0, 16))
+                reqs.append(serve.Request("loglik", d, theta=geo.Theta(float(rng.uniform(0.5, 2.0)),
+                                                                        float(rng.uniform(0.02, 0.3)),
+                                                                        dss[d]["theta"].nu, dss[d]["theta"].nugget),
+                                          t_arrival=t, id=q))
+            else:
+                d = int(rng.integers(12, 16))
+                xt, yt, _ = truth[d]
+                reqs.append(serve.Request("krige", d, xnew=xt, ynew=yt, t_arrival=t, id=q))
+            q += 1
+
+    reqs = arrivals(200.0, window, rng)
     results, stats = S.run(reqs, admit_until=window)
+    # arrival-rate sweep (same datasets and request mix, seed 8): the highest
+    # rate at which every request that arrived in the window was served is the
+    # sustainable knee; above it the queue grows with the window
+    sweep = []
+    rng_s = np.random.default_rng(8)
+    for rate in SERVE_SWEEP_RATES:
+        rq = arrivals(rate, SERVE_SWEEP_WINDOW, rng_s)
+        b0 = S.batches
+        _, st = S.run(rq, admit_until=SERVE_SWEEP_WINDOW)
+        sweep.append({"rate_per_s": rate, "requests": len(rq), "completed": st["completed"],
+                      "queued": st["queued"], "rejected": st["rejected"], "launches": S.batches - b0,
+                      "evals_per_s": st["evals_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"]})
+    ok = [r["rate_per_s"] for r in sweep if r["queued"] == 0 and r["completed"] + r["rejected"] == r["requests"]]
     # kriging accuracy: MSPE of the served (mixed-precision) predictions and of
     # the FP64 path's, against the held-out field values
     mspe = []
@@ -453,6 +475,8 @@ def run_serve(geo, dev, window):
         del ts
     stats.update({"arrival_rate_per_s": 200, "window_s": window, "requests": len(reqs),
                   "datasets_n": ns, "hbm_budget_gb": 120, "kriging_mspe": mspe,
+                  "rate_sweep": sweep, "sweep_window_s": SERVE_SWEEP_WINDOW,
+                  "sustainable_rate_per_s": max(ok) if ok else None,
                   "note": "offered load exceeds capacity: requests still queued at the end are reported, not served"})
     return stats
 
