@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--dmma", action="store_true",
                     help="in-band (FP64) updates on the FP64 pipe instead of FP64-accurate tensor-core products")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-evaluation measurement")
+    ap.add_argument("--no-dst", action="store_true", help="skip the DST / IND approximation timings")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-window", type=float, default=3.0, help="seconds of Poisson arrivals served")
     return ap.parse_args()
@@ -391,6 +392,7 @@ def run_batch(geo, dev):
             "speedup_vs_fp64": statistics.median(dms) / t}
 
 
+DST_BANDS = (1, 2, 4)
 SERVE_SWEEP_RATES = (2.0, 5.0, 10.0, 20.0, 50.0)
 SERVE_SWEEP_WINDOW = 4.0
 
@@ -628,6 +630,34 @@ def main():
             sweep.append(ent)
             del tsb
 
+    # the DST / IND approximation (Section III): tiles at distance >= d zeroed,
+    # the kept ones FP64; NOT_SPD when the truncation is indefinite
+    dst = []
+    if not args.no_dst:
+        for dd in DST_BANDS:
+            tsd = geo.TileStore(n, NB, dd, geo.GEO_LP_SPLIT_BF16, device=dev)
+            tsd.set_flags(geo.GEO_FLAG_DST)
+            ent = {"d": dd}
+            try:
+                tsd.loglik(X, Y, Z, th)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ldd, qd = tsd.loglik_async(X, Y, Z, th)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                td = e0.elapsed_time(e1) / 1000.0
+                ld_, qd_ = float(ldd), float(qd)
+                ld_ok = math.isfinite(ld_) and math.isfinite(qd_)
+                ent.update({"seconds_per_eval": td, "speedup_vs_mp": (ms_step / 1000.0) / td})
+                if ld_ok:
+                    ent["loglik"] = tsd.assemble(ld_, qd_)
+                    if fp64:
+                        ent["rel_diff_vs_fp64"] = abs(ent["loglik"] - fp64["loglik"]) / abs(fp64["loglik"])
+            except geo.NotSPDError:
+                ent["status"] = "not positive definite (the truncated covariance is indefinite)"
+            dst.append(ent)
+            del tsd
+
     if rank != 0:
         return
     p50 = statistics.median(step_ms)
@@ -656,6 +686,8 @@ def main():
     }
     if sweep is not None:
         out["band_sweep"] = sweep
+    if dst:
+        out["dst"] = dst
     if not args.no_batch and world == 1:
         out["batch"] = run_batch(geo, dev)
     if not args.no_serve and world == 1:

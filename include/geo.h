@@ -126,6 +126,17 @@ typedef struct geo_trace_rec {
  * 256-long part of the contraction into the FP64 tile: its rounding error is
  * no larger than that of FP64 accumulation (measured against exact sums). */
 #define GEO_FLAG_FP64_DMMA 4
+/* Approximation option (tensor-core mode, default scheduler): the Diagonal
+ * Super-Tile (DST) method of Section III, the tile form of the independent-
+ * blocks (IND) approximation.  Tile (i,j) of the covariance is kept, in FP64,
+ * when i - j < band and set to zero otherwise; the factorization, log-
+ * determinant and solve then follow Eq. 2 for that matrix.  Its Cholesky
+ * factor has the same tile band, so no task is scheduled for the zero tiles:
+ * the work falls from O(n^3) to O(n nb^2 band^2).  With band = 1 the tiles are
+ * independent blocks.  The zeroed matrix need not be positive definite: a
+ * failing pivot reports GEO_ERR_NOT_SPD as for any other matrix.  Not with
+ * GEO_FLAG_STEPWISE or GEO_FLAG_FP64_DMMA (geo_tiles_set_flags returns -2). */
+#define GEO_FLAG_DST 8
 
 /* A1, "appropriate ordering" (Section IV): Z-order permutation of n locations.
  * Each coordinate c (expected in [0,1]) is quantised to q = clamp(floor(c*2^16),

@@ -34,6 +34,9 @@ Function -> paper passage -> what pins it (tests/test_oracle_pins.py):
                                                                         Fig. 2 op trace
   loglik_mp                    Eq. 2 on the Algorithm 1 factor          within FP32-level
                                                                         error of dense
+  dst_covariance / loglik_dst   DST / IND approximation (Section III)    d = 1: sum of the
+                                                                        blocks' own Eq. 2;
+                                                                        d >= p: dense Eq. 2
   krige                        prediction (Section VI-B); simple        interpolation at
                                kriging reading                          observed points
   profile_sigma2               Eq. 3 and theta1_opt = Z'S~^-1 Z / n     argmax of Eq. 2
@@ -260,6 +263,32 @@ def loglik_mp(x, y, z, theta: Theta, nb, band):
     n = len(z)
     S = covariance(x, y, theta=theta)
     L, info = mp_tile_cholesky(S, nb, band)
+    if info != 0:
+        return dict(loglik=float("nan"), logdet=float("nan"), quad=float("nan"), info=info)
+    logdet, quad = factor_logdet_quad(L, z)
+    return dict(loglik=_assemble(n, logdet, quad), logdet=logdet, quad=quad, info=0)
+
+
+# ------------------------------------------- DST / IND (Section III-B) ---
+def dst_covariance(S, nb, d):
+    """Diagonal Super-Tile approximation (Section III): the covariance with
+    every tile (i, j) whose tile distance |i - j| is d or more set to zero
+    (tiles of nb rows and columns, the last one possibly short).  d = 1 keeps
+    the diagonal tiles only: the independent-blocks (IND) method."""
+    n = S.shape[0]
+    blk = np.arange(n) // nb
+    far = np.abs(blk[:, None] - blk[None, :]) >= d
+    A = np.array(S, dtype=np.float64, copy=True)
+    A[far] = 0.0
+    return A
+
+
+def loglik_dst(x, y, z, theta: Theta, nb, d):
+    """Eq. 2 for the DST covariance, which the method keeps in full (double)
+    precision: dense float64 Cholesky of the zeroed matrix."""
+    n = len(z)
+    S = dst_covariance(covariance(x, y, theta=theta), nb, d)
+    L, info = dense_factor(S)
     if info != 0:
         return dict(loglik=float("nan"), logdet=float("nan"), quad=float("nan"), info=info)
     logdet, quad = factor_logdet_quad(L, z)

@@ -19,12 +19,14 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // meta buffer: off[p*p] int64 | slot[p*p] int32 | status[16] + tickets[2p] int32 |
 // scal doubles | (tensor-core mode) scheduler counters | per scheduling variant
-// (0: in-band updates on the tensor cores, 1: on the FP64 pipe): CUDA-core
-// tasks, bulk tasks, solve ends, tensor targets
+// (0: in-band updates on the tensor cores, 1: on the FP64 pipe, 2: the DST
+// approximation): CUDA-core tasks, bulk tasks, solve ends, tensor targets
+constexpr int N_VARIANTS = 3;
 struct MetaOffsets {
     size_t off, slot, status, scal, sched_ctr, total;
-    size_t sched_g2[2], sched_bulk[2], sched_end[2], sched_tct[2], sched_y[2];
-    SchedGeom geom[2];
+    size_t sched_g2[N_VARIANTS], sched_bulk[N_VARIANTS], sched_end[N_VARIANTS], sched_tct[N_VARIANTS],
+        sched_y[N_VARIANTS];
+    SchedGeom geom[N_VARIANTS];
     bool dag;
 };
 
@@ -41,13 +43,13 @@ static MetaOffsets meta_offsets(int p, int nb, int band, int lp_mode, int pp) {
     b = align256(b + sizeof(double) * ((size_t)2 * p + 8 + (size_t)p * nb));
     m.dag = (lp_mode == GEO_LP_SPLIT_BF16);
     m.sched_ctr = b;
-    for (int v = 0; v < 2; ++v) {
-        m.geom[v] = sched_geom(p, nb, band, pp, v == 0);
+    for (int v = 0; v < N_VARIANTS; ++v) {
+        m.geom[v] = sched_geom(p, nb, band, pp, v != 1, v == 2);
         m.sched_g2[v] = m.sched_bulk[v] = m.sched_end[v] = m.sched_tct[v] = m.sched_y[v] = b;
     }
     if (m.dag) {
-        b = align256(b + sizeof(int) * (size_t)m.geom[0].n_counters);
-        for (int v = 0; v < 2; ++v) {
+        b = align256(b + sizeof(int) * (size_t)m.geom[0].n_counters);   // the same counters for every variant
+        for (int v = 0; v < N_VARIANTS; ++v) {
             const SchedGeom& g = m.geom[v];
             m.sched_g2[v] = b;
             b = align256(b + sizeof(G2Task) * (size_t)g.n_prio);
@@ -251,7 +253,7 @@ int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp, 
     std::vector<G2Task> prio, bulk, yq;
     std::vector<int> trsm_end;
     std::vector<int4> tct;
-    for (int v = 0; v < 2 && !e && mo.dag; ++v) {
+    for (int v = 0; v < N_VARIANTS && !e && mo.dag; ++v) {
         sched_build(mo.geom[v], lay->band, prio, bulk, trsm_end, yq, tct);
         if (!prio.empty())
             e = cudaMemcpyAsync((char*)d_meta + mo.sched_g2[v], prio.data(), sizeof(G2Task) * prio.size(),
@@ -297,7 +299,10 @@ int geo_tiles_release(geo_tiles* t) {
 
 int geo_tiles_set_flags(geo_tiles* t, int flags) {
     if (!t) return -1;
-    if (flags & ~(GEO_FLAG_FP64_OFFBAND_GEN | GEO_FLAG_STEPWISE | GEO_FLAG_FP64_DMMA)) return -2;
+    if (flags & ~(GEO_FLAG_FP64_OFFBAND_GEN | GEO_FLAG_STEPWISE | GEO_FLAG_FP64_DMMA | GEO_FLAG_DST)) return -2;
+    if ((flags & GEO_FLAG_DST) &&
+        ((flags & (GEO_FLAG_STEPWISE | GEO_FLAG_FP64_DMMA)) || t->lay.lp_mode != GEO_LP_SPLIT_BF16))
+        return -2;
     t->flags = flags;
     return GEO_OK;
 }
@@ -350,14 +355,21 @@ static int reset_status(const Layout& L, cudaStream_t s) {
 // forward solve of Eq. 2 inside the same launch and writes (log|Sigma|,
 // Z' Sigma^-1 Z) to res; *solved tells the caller whether that happened (the
 // step-by-step paths leave the solve to run_logdet_trsv).
+// scheduling variant of a bound store: in-band updates on the tensor cores (0)
+// unless the FP64 pipe is asked for or there are no slice planes (a single
+// tile: 1); the DST approximation (2)
+static int sched_variant(const geo_tiles* t) {
+    if (!t->d_planes || t->lay.bytes_planes == 0) return 1;
+    if (t->flags & GEO_FLAG_DST) return 2;
+    return (t->flags & GEO_FLAG_FP64_DMMA) ? 1 : 0;
+}
+
 static cudaError_t factor(const geo_tiles* t, const Layout& L, const double* z, double* res, bool* solved,
                           cudaStream_t s) {
     *solved = false;
     if (L.lp_mode == GEO_LP_SPLIT_BF16 && !(t->flags & GEO_FLAG_STEPWISE)) {
         MetaOffsets mo = meta_offsets(t->lay);
-        // in-band updates on the tensor cores unless the FP64 pipe is asked for
-        // (or there are no slice planes: a single tile)
-        const int v = ((t->flags & GEO_FLAG_FP64_DMMA) || !t->d_planes || t->lay.bytes_planes == 0) ? 1 : 0;
+        const int v = sched_variant(t);
         SchedView sv;
         sv.geom = mo.geom[v];
         char* base = (char*)t->d_meta;
@@ -527,9 +539,7 @@ struct BatchMeta {
 std::mutex g_batch_mu;
 std::vector<std::pair<const void*, BatchMeta>> g_batches;   // bound workspaces
 
-int batch_variant(const geo_tiles* t) {
-    return ((t->flags & GEO_FLAG_FP64_DMMA) || !t->d_planes || t->lay.bytes_planes == 0) ? 1 : 0;
-}
+int batch_variant(const geo_tiles* t) { return sched_variant(t); }
 
 int batch_meta(int nprob, const geo_batch_item* items, BatchMeta& m, std::vector<SchedGeom>* geoms) {
     if (nprob < 1) return -1;

@@ -82,10 +82,11 @@ constexpr int DP_TRSM_ROWS = 32;
 constexpr int SP_TRSM_ROWS = 128;
 __host__ __device__ inline int dp_trsm_rows(int nb) { return nb >= DP_SPLIT_MIN_NB ? DP_TRSM_ROWS : SP_TRSM_ROWS; }
 
-SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
+SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex, bool dst) {
     SchedGeom g;
     g.p = p;
     g.ex = ex ? 1 : 0;
+    g.dst = dst ? 1 : 0;
     g.ns = ceil_div(nb, 32);
     g.nsb64 = ceil_div(nb, 64);
     g.items64 = g.nsb64 * g.nsb64;
@@ -99,16 +100,20 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
     g.n_counters = 16 + 2 * (long long)p * p + (long long)p * g.ns * g.ns + (long long)p * p * g.max_items +
                    (long long)p * g.chunks_y + p;
     long long n_prio = 0, n_bulk = 0, n_tct = 0, n_y = 0;
+    // with DST, panel tiles (i,k) at i - k >= band are zero: no solve, no
+    // update reads them, no forward-solve contribution
+    const int reach = dst ? band : p;   // rows i < k + reach of panel k are nonzero
     for (int k = 0; k < p; ++k) {
-        n_y += 1 + (long long)(p - k - 1) * g.chunks_y;   // YD(k), YG(i > k, chunks)
+        const int iend = (int)std::min<long long>(p, (long long)k + reach);
+        n_y += 1 + (long long)(iend - k - 1) * g.chunks_y;   // YD(k), YG(i > k, chunks)
         const int ns = g.ns;
         // PC, PC2, then PT and PU without the chains' PT(s+1, s), PU(s+1, s+1, s),
         // PT(s+2, s) and PU(s+2, s+1, s)
         const long long n2 = std::max(0, ns - 2);
         n_prio += 2 + ns * (ns - 1) / 2 - (ns - 1) - n2 + (long long)ns * (ns - 1) * (ns + 1) / 6 - (ns - 1) - n2;
-        for (int i = k + 1; i < p; ++i) n_prio += is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
-        for (int j = k + 1; j < p; ++j)
-            for (int i = j; i < p; ++i) {
+        for (int i = k + 1; i < iend; ++i) n_prio += is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
+        for (int j = k + 1; j < iend; ++j)
+            for (int i = j; i < iend; ++i) {
                 if (is_dp(i, j, band) && !ex) (j == k + 1 ? n_prio : n_bulk) += g.items64;
                 else n_tct += 1;
             }
@@ -127,11 +132,13 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex) {
 // in-band updates on the tensor cores (g.ex) every update is a tensor target
 // and the CUDA-core queues hold only the A(k).  Forward-solve queue: Y(0) Y(1)
 // ..., Y(k) = YD(k) then YG(k; i, q) for i = k+1..p-1 -- the forward solve of
-// Eq. 2 fused into the factorization (used only by a launch given Z).
+// Eq. 2 fused into the factorization (used only by a launch given Z).  With
+// the DST approximation (g.dst) only rows i < k + band of each step exist.
 void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
                  std::vector<int>& trsm_end, std::vector<G2Task>& yq, std::vector<int4>& tct) {
     const int p = g.p, ns = g.ns;
     const bool ex = g.ex != 0;
+    auto iend = [&](int k) { return g.dst ? std::min(p, k + band) : p; };
     prio.clear();
     bulk.clear();
     tct.clear();
@@ -139,7 +146,7 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
     trsm_end.assign((size_t)p, 0);
     for (int k = 0; k < p; ++k) {
         yq.push_back({T_YD, k, 0, 0, 0});
-        for (int i = k + 1; i < p; ++i)
+        for (int i = k + 1; i < iend(k); ++i)
             for (int q = 0; q < g.chunks_y; ++q) yq.push_back({T_YG, k, i, q, 0});
     }
     auto A = [&](int k) {
@@ -152,7 +159,7 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
                     if (!(r == s + 1 && c == s + 1) && !(r == s + 2 && c == s + 1))
                         prio.push_back({T_PU, k, r, c, s});
         }
-        for (int i = k + 1; i < p; ++i) {
+        for (int i = k + 1; i < iend(k); ++i) {
             const int nq = is_dp(i, k, band) ? g.chunks_dp : g.chunks_sp;
             for (int q = 0; q < nq; ++q) prio.push_back({T_TRSM, k, i, q, 0});
         }
@@ -180,13 +187,14 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
     // column, which keeps more of the panel's slice planes in L2.
     constexpr int SWEEP_W = 8;
     for (int k = 0; k < p; ++k) {
-        for (int i = k + 1; i < p; ++i)                  // C'(k): column k+1
+        const int ie = iend(k);
+        for (int i = k + 1; i < ie; ++i)                 // C'(k): column k+1
             if (ex || !is_dp(i, k + 1, band)) tct.push_back(make_int4(i, k + 1, k, 0));
-        for (int j = k + 2; j < std::min(p, k + 3); ++j)   // B'(k): column k+2
-            for (int i = j; i < p; ++i)
+        for (int j = k + 2; j < std::min(ie, k + 3); ++j)  // B'(k): column k+2
+            for (int i = j; i < ie; ++i)
                 if (ex || !is_dp(i, j, band)) tct.push_back(make_int4(i, j, k, 0));
-        for (int j0 = k + 3; j0 < p; j0 += SWEEP_W)       // columns >= k+3
-            for (int i = j0; i < p; ++i)
+        for (int j0 = k + 3; j0 < ie; j0 += SWEEP_W)      // columns >= k+3
+            for (int i = j0; i < ie; ++i)
                 for (int j = j0; j < std::min(j0 + SWEEP_W, i + 1); ++j)
                     if (ex || !is_dp(i, j, band)) tct.push_back(make_int4(i, j, k, 0));
     }
@@ -275,6 +283,12 @@ __device__ bool wait_ge(const DagArgs& A, const Layout& L, const int* p, int v, 
     }
 }
 
+// first step whose update reaches block row i (0, or with DST the first step
+// k' whose panel tile (i,k') is nonzero), and the number of such steps before k
+__device__ __forceinline__ int first_step(const ProbDev& P, int i) {
+    return P.g.dst ? max(0, i - P.L.band + 1) : 0;
+}
+__device__ __forceinline__ int steps_before(const ProbDev& P, int i, int k) { return k - first_step(P, i); }
 // update items applied to tile (i,j) per step
 __device__ __forceinline__ int items_of(const ProbDev& P, int i, int j) {
     return (is_dp(i, j, P.L.band) && !P.g.ex) ? P.g.items64 : P.g.items_tc;
@@ -959,11 +973,11 @@ __device__ bool y_ready(const ProbDev& P, const G2Task& t) {
     if (t.type == T_YD) {
         if (ld_acquire_s32(pot_at(P, k, P.g.ns - 1, P.g.ns - 1)) < P.g.ns) return false;
         for (int q = 0; q < cy; ++q)
-            if (ld_acquire_s32(P.ycnt + k * cy + q) < k) return false;
+            if (ld_acquire_s32(P.ycnt + k * cy + q) < steps_before(P, k, k)) return false;
         return true;
     }
     return ld_acquire_s32(P.ydone + k) >= 1 && ld_acquire_s32(P.tcnt + t.a * P.L.p + k) >= chunks_of(P, t.a, k) &&
-           ld_acquire_s32(P.ycnt + t.a * cy + t.b) >= k;
+           ld_acquire_s32(P.ycnt + t.a * cy + t.b) >= steps_before(P, t.a, k);
 }
 
 // Stop the whole launch (a wait timed out): the flag every wait polls, and in a
@@ -1049,40 +1063,40 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
             if (ok) switch (t.type) {
                 case T_PC:   // the tile's trailing updates; the chain waits for the rest as it goes
                 case T_PC2:
-                    ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 11);
+                    ok = wait_ge(A, L, P.upd + k * L.p + k, steps_before(P, k, k) * items_of(P, k, k), 11);
                     break;
                 case T_PT:
-                    if (t.b == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 13);
+                    if (t.b == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, steps_before(P, k, k) * items_of(P, k, k), 13);
                     ok = ok && wait_ge(A, L, pot_at(P, k, t.b, t.b), t.b + 1, 14) &&
                          wait_ge(A, L, pot_at(P, k, t.a, t.b), t.b, 15);
                     break;
                 case T_PU:
-                    if (t.c == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, k * items_of(P, k, k), 16);
+                    if (t.c == 0) ok = wait_ge(A, L, P.upd + k * L.p + k, steps_before(P, k, k) * items_of(P, k, k), 16);
                     ok = ok && wait_ge(A, L, pot_at(P, k, t.a, t.c), t.c + 1, 17) &&
                          wait_ge(A, L, pot_at(P, k, t.b, t.c), t.c + 1, 18) &&
                          wait_ge(A, L, pot_at(P, k, t.a, t.b), t.c, 19);
                     break;
                 case T_TRSM:   // the first sub-block of L_kk; the solve waits for later ones as it goes
                     ok = wait_ge(A, L, pot_at(P, k, 0, 0), 1, 20) &&
-                         wait_ge(A, L, P.upd + t.a * L.p + k, k * items_of(P, t.a, k), 21);
+                         wait_ge(A, L, P.upd + t.a * L.p + k, steps_before(P, t.a, k) * items_of(P, t.a, k), 21);
                     break;
                 case T_YD:   // L_kk final and every earlier block row's contribution applied
                     if (P.z) {
                         ok = wait_ge(A, L, pot_at(P, k, ns - 1, ns - 1), ns, 40);
                         for (int q = 0; ok && q < P.g.chunks_y; ++q)
-                            ok = wait_ge(A, L, P.ycnt + k * P.g.chunks_y + q, k, 41);
+                            ok = wait_ge(A, L, P.ycnt + k * P.g.chunks_y + q, steps_before(P, k, k), 41);
                     }
                     break;
                 case T_YG:   // y_k solved, tile (i,k) solved, contributions of steps < k applied
                     if (P.z)
                         ok = wait_ge(A, L, P.ydone + k, 1, 42) &&
                              wait_ge(A, L, P.tcnt + t.a * L.p + k, chunks_of(P, t.a, k), 43) &&
-                             wait_ge(A, L, P.ycnt + t.a * P.g.chunks_y + t.b, k, 44);
+                             wait_ge(A, L, P.ycnt + t.a * P.g.chunks_y + t.b, steps_before(P, t.a, k), 44);
                     break;
                 default:   // T_UPD: own sub-block's previous step only
                     ok = wait_ge(A, L, P.tcnt + t.a * L.p + k, chunks_of(P, t.a, k), 22) &&
                          wait_ge(A, L, P.tcnt + t.b * L.p + k, chunks_of(P, t.b, k), 23) &&
-                         wait_ge(A, L, sub_at(P, t.a, t.b, t.c), k, 24);
+                         wait_ge(A, L, sub_at(P, t.a, t.b, t.c), steps_before(P, t.a, k), 24);
                     break;
             }
             S.ok = ok ? 1 : 0;
@@ -1139,7 +1153,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                         ran = m >= 0.0f;
                         if (ran && L.planes && r < nb) g2_slice_row<double>(L, X, i, k, r, m);
                     } else {   // the host launches dag_kernel<true> for such tiles
-                        if (g == 0) abort_launch(A, 46);
+                        if (g == 0) abort_launch(A, 59);
                         ran = false;
                     }
                 } else {
@@ -1152,19 +1166,23 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 done = P.tcnt + i * L.p + k;
                 break;
             }
-            case T_YD: {   // y_k = L_kk^-1 r_k (block row 0: r_0 = Z_0); the last one sums the partials
+            case T_YD: {   // y_k = L_kk^-1 r_k (r_k = Z_k when no step reaches block row k); the last
+                           // one sums the partials
                 if (!P.z) break;
                 const int k = t.k;
                 double* yv = L.scal + 2 * L.p + 8;
-                if (k == 0)
-                    for (int r = g; r < nb; r += G2_THREADS) yv[r] = r < L.n ? P.z[r] : 0.0;
+                if (first_step(P, k) == k)
+                    for (int r = g; r < nb; r += G2_THREADS) {
+                        const size_t gi = (size_t)k * nb + r;
+                        yv[gi] = gi < (size_t)L.n ? P.z[gi] : 0.0;
+                    }
                 g2_sync();
                 ysolve_diag_tile(L, k, yv, L.scal, g, G2_THREADS, S.yd, G2Sync());
                 if (k == L.p - 1 && g == 0) ysolve_finish(L, L.scal, P.res, P.res + 1);
                 done = P.ydone + k;
                 break;
             }
-            case T_YG: {   // rows of r_i -= L(i,k) y_k (step 0 starts from Z_i)
+            case T_YG: {   // rows of r_i -= L(i,k) y_k (the first step reaching row i starts from Z_i)
                 if (!P.z) break;
                 const int i = t.a, k = t.k;
                 double* yv = L.scal + 2 * L.p + 8;
@@ -1174,7 +1192,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 if (r < nb) {
                     const double acc = yrow_update(L, i, k, r, S.yk);
                     const size_t gi = (size_t)i * nb + r;
-                    const double base = (k == 0) ? (gi < (size_t)L.n ? P.z[gi] : 0.0) : yv[gi];
+                    const double base = (k == first_step(P, i)) ? (gi < (size_t)L.n ? P.z[gi] : 0.0) : yv[gi];
                     yv[gi] = base - acc;
                 }
                 done = P.ycnt + i * P.g.chunks_y + t.b;
@@ -1526,7 +1544,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             long long te1 = te0;   // products done (off-band), for the trace
             if (threadIdx.x == 64) {
                 s_epi_skip = 0;
-                if (!wait_ge(A, L, sub_at(P, i, j, m.rem), k, 38)) {
+                if (!wait_ge(A, L, sub_at(P, i, j, m.rem), steps_before(P, i, k), 38)) {
                     if (single || aborted(A)) *abort_flag = 1;
                     else s_epi_skip = 1;
                 }

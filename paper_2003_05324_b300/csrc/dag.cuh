@@ -28,7 +28,7 @@ constexpr int DP_SPLIT_MIN_NB = 256;
 inline bool dag_small_dp(int nb, int band) { return nb < DP_SPLIT_MIN_NB && band > 1; }
 
 struct SchedGeom {
-    int p, ex, ns, nsb64, items64, items_tc, max_items, chunks_dp, chunks_sp, chunks_y;
+    int p, ex, dst, ns, nsb64, items64, items_tc, max_items, chunks_dp, chunks_sp, chunks_y;
     long long n_counters, n_g2, n_prio, n_bulk, n_tct, n_y;
 };
 
@@ -59,7 +59,9 @@ struct ProbDev {
 
 // ex: in-band (FP64) updates as FP64-accurate tensor-core items instead of
 // CUDA-core DMMA items
-SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex);
+// ex: in-band updates on the tensor cores; dst: the DST approximation (tiles
+// at i - j >= band are zero and get no tasks)
+SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex, bool dst = false);
 // yq: the forward-solve queue (claimed only when its head is ready)
 void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
                  std::vector<int>& trsm_end, std::vector<G2Task>& yq, std::vector<int4>& tct);

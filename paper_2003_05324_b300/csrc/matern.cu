@@ -138,6 +138,9 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
                 }
                 T[(size_t)(c0 + c) * nb + a] = v;
             }
+        } else if (L.flags & GEO_FLAG_DST) {   // the DST approximation: tiles beyond the band are zero
+            float* T = sp_tile(L, i, j);
+            for (int c = 0; c < cols; ++c) T[(size_t)(c0 + c) * nb + a] = 0.0f;
         } else if (L.flags & GEO_FLAG_FP64_OFFBAND_GEN) {
             float* T = sp_tile(L, i, j);
             for (int c = 0; c < cols; ++c) {

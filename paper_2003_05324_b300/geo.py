@@ -32,6 +32,7 @@ GEO_LP_FP32 = 1
 GEO_FLAG_FP64_OFFBAND_GEN = 1
 GEO_FLAG_STEPWISE = 2
 GEO_FLAG_FP64_DMMA = 4
+GEO_FLAG_DST = 8
 
 
 class GeoError(RuntimeError):

@@ -423,3 +423,64 @@ def test_nelder_mead_hand_traced_steps():
     u, f, evals, iters = O.nelder_mead(lambda u: float(u[0] ** 2), [0.2], step=1.0, max_evals=6)
     assert evals == 6 and iters == 2
     assert abs(u[0] + 0.05) <= 1e-15 and abs(f - 0.0025) <= 1e-16
+
+
+# ---- DST / IND approximation (Section III) ---------------------------------
+def _dst_problem(m=18, seed=31):
+    x, y = inputs.jittered_grid(m, seed=seed)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.white_noise(len(x), seed=seed + 1)
+    return x, y, z
+
+
+def test_dst_band1_is_independent_blocks():
+    # d = 1 keeps only the diagonal tiles: Eq. 2 then splits into the blocks'
+    # own Eq. 2 (log-det, quadratic form and the n/2 log 2 pi term are additive)
+    x, y, z = _dst_problem()
+    nb, th = 64, O.Theta(1.0, 0.1, 1.0, 0.0)
+    n = len(z)                                     # 324: five full tiles and one of 4 rows
+    got = O.loglik_dst(x, y, z, th, nb, 1)
+    parts = [O.loglik_dense(x[a:a + nb], y[a:a + nb], z[a:a + nb], th) for a in range(0, n, nb)]
+    assert got["logdet"] == pytest.approx(math.fsum(p["logdet"] for p in parts), rel=1e-12)
+    assert got["quad"] == pytest.approx(math.fsum(p["quad"] for p in parts), rel=1e-12)
+    assert got["loglik"] == pytest.approx(math.fsum(p["loglik"] for p in parts), rel=1e-12)
+
+
+def test_dst_band2_matches_block_tridiagonal_recursion():
+    # d = 2 leaves a block-tridiagonal matrix: block LDL' by the recursion
+    # D_k = A_kk - A_k,k-1 D_k-1^-1 A_k-1,k, w_k = z_k - A_k,k-1 D_k-1^-1 w_k-1,
+    # log|A| = sum log|D_k| and Z'A^-1 Z = sum w_k' D_k^-1 w_k
+    x, y, z = _dst_problem(m=16, seed=41)
+    nb, th = 48, O.Theta(1.3, 0.04, 0.5, 0.0)   # short range: the truncated matrix stays SPD
+    n = len(z)
+    S = O.covariance(x, y, theta=th)
+    cuts = list(range(0, n, nb)) + [n]
+    blk = [slice(cuts[t], cuts[t + 1]) for t in range(len(cuts) - 1)]
+    logdet, quad = 0.0, 0.0
+    D = w = None
+    for t, b in enumerate(blk):
+        A = S[b, b].copy()
+        v = z[b].copy()
+        if t > 0:
+            C = S[b, blk[t - 1]]
+            A -= C @ np.linalg.solve(D, C.T)
+            v -= C @ np.linalg.solve(D, w)
+        D, w = A, v
+        logdet += np.linalg.slogdet(D)[1]
+        quad += float(w @ np.linalg.solve(D, w))
+    got = O.loglik_dst(x, y, z, th, nb, 2)
+    assert got["info"] == 0
+    assert got["logdet"] == pytest.approx(logdet, rel=1e-11)
+    assert got["quad"] == pytest.approx(quad, rel=1e-10)
+
+
+def test_dst_full_reach_is_the_dense_likelihood():
+    x, y, z = _dst_problem(m=12, seed=51)
+    nb, th = 40, O.Theta(0.9, 0.2, 1.5, 0.0)
+    p = -(-len(z) // nb)
+    want = O.loglik_dense(x, y, z, th)["loglik"]
+    for d in (p, p + 3):
+        assert O.loglik_dst(x, y, z, th, nb, d)["loglik"] == want
+    # one tile diagonal fewer changes the value
+    assert O.loglik_dst(x, y, z, th, nb, p - 1)["loglik"] != want
