@@ -358,6 +358,17 @@ def loglik_flops(n: int) -> float:
 
 
 
+def loglik(x, y, z, theta: Theta, nb: int = 500, band: int = 1, lp_mode: int = GEO_LP_SPLIT_BF16,
+           flags: int = 0) -> float:
+    """geo.loglik(x, y, z, theta, nb, band): Eq. 2 on a fresh tile store (x, y, z:
+    Morton-ordered device tensors); raises NotSPDError when the factorization
+    meets a non-positive pivot."""
+    ts = TileStore(int(z.shape[0]), nb, band, lp_mode, device=z.device)
+    if flags:
+        ts.set_flags(flags)
+    return ts.loglik(x, y, z, theta)[0]
+
+
 def mle(x, y, z, theta0: Theta, nb: int, band: int, lp_mode: int = GEO_LP_SPLIT_BF16, flags: int = 0, **kw):
     """geo.mle(x, y, z, theta0, nb, band, ...): the estimator on a fresh tile store
     (x, y, z: Morton-ordered device tensors; keywords as TileStore.mle)."""
@@ -454,3 +465,11 @@ class Batch:
 
     def status(self):
         return [ts.status() for ts in self.stores]
+
+
+def __getattr__(name):
+    # geo.Server: the serving loop lives in serve.py, which builds on this module
+    if name == "Server":
+        from .serve import Server
+        return Server
+    raise AttributeError(name)

@@ -369,3 +369,18 @@ def test_krige_matches_oracle(G, nu):
     ts.potrf()
     got = ts.krige(dev(x), dev(y), dev(z), th, dev(xn), dev(yn)).cpu().numpy()
     np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-9)
+
+
+def test_module_level_api(G):
+    # geo.loglik on a fresh store equals the store's own evaluation bit for bit;
+    # geo.Server is the serving loop
+    x, y = inputs.jittered_grid(30, seed=3)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.white_noise(len(x), seed=4)
+    X, Y, Z = (torch.as_tensor(v, device="cuda") for v in (x, y, z))
+    th = G.Theta(1.0, 0.1, 0.5)
+    want = G.TileStore(len(z), 128, 2, G.GEO_LP_SPLIT_BF16).loglik(X, Y, Z, th)[0]
+    assert G.loglik(X, Y, Z, th, nb=128, band=2) == want
+    from paper_2003_05324_b300 import serve
+    assert G.Server is serve.Server
