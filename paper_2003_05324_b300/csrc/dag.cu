@@ -95,10 +95,10 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex, bool dst) {
     g.chunks_sp = ceil_div(nb, SP_TRSM_ROWS);
     g.chunks_y = ceil_div(nb, 128);
     // counters: grab counters, upd[p*p], tcnt[p*p], pot[p*ns*ns], sub[p*p*maxitems],
-    // ycnt[p*chunks_y], ydone[p]
+    // ycnt[p*chunks_y], ydone[p] + the number of finished YD tasks
     g.max_items = std::max(g.items64, g.items_tc);
     g.n_counters = 16 + 2 * (long long)p * p + (long long)p * g.ns * g.ns + (long long)p * p * g.max_items +
-                   (long long)p * g.chunks_y + p;
+                   (long long)p * g.chunks_y + p + 1;
     long long n_prio = 0, n_bulk = 0, n_tct = 0, n_y = 0;
     // with DST, panel tiles (i,k) at i - k >= band are zero: no solve, no
     // update reads them, no forward-solve contribution
@@ -974,7 +974,8 @@ __device__ bool y_ready(const ProbDev& P, const G2Task& t) {
         if (ld_acquire_s32(pot_at(P, k, P.g.ns - 1, P.g.ns - 1)) < P.g.ns) return false;
         for (int q = 0; q < cy; ++q)
             if (ld_acquire_s32(P.ycnt + k * cy + q) < steps_before(P, k, k)) return false;
-        return true;
+        // the last one sums every block row's partials: all other YD done
+        return k < P.L.p - 1 || ld_acquire_s32(P.ydone + P.L.p) >= P.L.p - 1;
     }
     return ld_acquire_s32(P.ydone + k) >= 1 && ld_acquire_s32(P.tcnt + t.a * P.L.p + k) >= chunks_of(P, t.a, k) &&
            ld_acquire_s32(P.ycnt + t.a * cy + t.b) >= steps_before(P, t.a, k);
@@ -1080,11 +1081,13 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                     ok = wait_ge(A, L, pot_at(P, k, 0, 0), 1, 20) &&
                          wait_ge(A, L, P.upd + t.a * L.p + k, steps_before(P, t.a, k) * items_of(P, t.a, k), 21);
                     break;
-                case T_YD:   // L_kk final and every earlier block row's contribution applied
+                case T_YD:   // L_kk final and every earlier block row's contribution applied; the
+                             // last one also every other YD (with DST nothing else orders them)
                     if (P.z) {
                         ok = wait_ge(A, L, pot_at(P, k, ns - 1, ns - 1), ns, 40);
                         for (int q = 0; ok && q < P.g.chunks_y; ++q)
                             ok = wait_ge(A, L, P.ycnt + k * P.g.chunks_y + q, steps_before(P, k, k), 41);
+                        if (ok && k == L.p - 1) ok = wait_ge(A, L, P.ydone + L.p, L.p - 1, 50);
                     }
                     break;
                 case T_YG:   // y_k solved, tile (i,k) solved, contributions of steps < k applied
@@ -1208,6 +1211,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
         if (g == 0) {
             if (ran && done) {   // (no counter: a solve task of a launch without Z)
                 if (t.type == T_UPD) red_release_add(sub_at(P, t.a, t.b, t.c), 1);
+                if (t.type == T_YD) red_release_add(P.ydone + L.p, 1);
                 red_release_add(done, 1);
             }
             if (kind == 0) atomicSub(inflight, 1);

@@ -129,3 +129,16 @@ def test_dst_in_a_batch_equals_the_single_problem(G):
     got = B.loglik(thetas)
     for g, w in zip(got, want):
         assert tuple(g) == tuple(w)
+
+
+def test_dst_fused_solve_sums_every_block_row(G):
+    # with independent blocks nothing but the finishing rule orders the last
+    # diagonal solve after the others: repeat a 20-block evaluation
+    x, y, z = grid(50, seed=7)              # n = 2,500, tile 128: 20 blocks, the last of 68 rows
+    th = G.Theta(1.0, 0.05, 0.5)
+    want = O.loglik_dst(x, y, z, O.Theta(1.0, 0.05, 0.5), 128, 1)["loglik"]
+    ts = dst_store(G, len(z), 128, 1)
+    X, Y, Z = dev(x), dev(y), dev(z)
+    for _ in range(10):
+        l, _, _ = ts.loglik(X, Y, Z, th)
+        assert abs(l - want) <= 1e-10 * abs(want)
