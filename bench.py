@@ -39,7 +39,7 @@ CPU_SAMPLE_M = 80            # oracle sample: 80 x 80 = 6,400 locations, tile 40
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--band", type=int, default=1)
@@ -241,6 +241,32 @@ def algorithmic_flops(p, nb, band):
                 else:
                     lp += 2.0 * nb ** 3
     return f64, f64u, f32, lp
+
+
+def measured_hbm_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)).get("hbm_gbs", 6400.0), "measured (MEASURED_PEAKS.json)"
+    return 6400.0, "fallback (6.4 TB/s of the profiling recipe)"
+
+
+def tile_mix_roofline(rows, ts, ms_step):
+    """The tile-mix-weighted lower bound of one evaluation, with the units taken
+    one after another: T* = sum over units of F_unit / P_unit (FP64 pipe, FP32
+    pipe, tensor cores, as in the kernel row) + B_gen / BW + B_solve / BW, where
+    B_gen = B_solve = the stored tile bytes (written once by the generation,
+    read once by the solve) and BW the measured HBM bandwidth.  The persistent
+    kernel overlaps the units, so the largest single term is also reported."""
+    dag = next((r for r in rows if r["kernel"].startswith("dag_kernel")), None)
+    if dag is None:
+        return None
+    bw, bw_src = measured_hbm_gbs()
+    stored = float(ts.lay.bytes_dp + ts.lay.bytes_sp)
+    units = dict(dag["unit_lower_bounds_ms"])
+    units["HBM (generation writes, solve reads the stored tiles)"] = 2.0 * stored / (bw * 1e9) * 1e3
+    t_star = sum(units.values())
+    return {"t_star_ms": t_star, "frac": t_star / ms_step, "terms_ms": units, "stored_tile_bytes": stored,
+            "largest_term_ms": max(units.values()), "hbm_source": bw_src}
 
 
 def measured_peaks():
@@ -679,6 +705,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": roofline,
+        "tile_mix_roofline": tile_mix_roofline(rows, ts, ms_step),
         "kernels": rows,
         "fp64_path": fp64,
         "e2e": e2e,
