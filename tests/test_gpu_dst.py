@@ -118,13 +118,18 @@ def test_dst_flag_combinations_are_refused(G):
 
 
 def test_dst_in_a_batch_equals_the_single_problem(G):
+    # DST problems next to an ordinary mixed-precision one in the same launch
     probs, thetas, want = [], [], []
-    for s, (m, nb, d) in enumerate([(30, 128, 1), (36, 128, 2), (20, 64, 3)]):
+    for s, (m, nb, d, flags) in enumerate([(30, 128, 1, G.GEO_FLAG_DST), (36, 128, 2, G.GEO_FLAG_DST),
+                                           (24, 128, 2, 0), (20, 64, 3, G.GEO_FLAG_DST)]):
         x, y, z = grid(m, seed=10 + s)
         th = G.Theta(1.0, 0.02, 0.5)
-        probs.append(dict(x=dev(x), y=dev(y), z=dev(z), nb=nb, band=d, flags=G.GEO_FLAG_DST))
+        probs.append(dict(x=dev(x), y=dev(y), z=dev(z), nb=nb, band=d, flags=flags))
         thetas.append(th)
-        want.append(dst_store(G, len(z), nb, d).loglik(dev(x), dev(y), dev(z), th))
+        ts = G.TileStore(len(z), nb, d, G.GEO_LP_SPLIT_BF16)
+        if flags:
+            ts.set_flags(flags)
+        want.append(ts.loglik(dev(x), dev(y), dev(z), th))
     B = G.Batch(probs)
     got = B.loglik(thetas)
     for g, w in zip(got, want):
