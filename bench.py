@@ -656,7 +656,7 @@ def main():
             sweep.append(ent)
             del tsb
 
-    # the DST / IND approximation (Section III): tiles at distance >= d zeroed,
+    # the DST / IND approximation (Section V-B): tiles at distance >= d zeroed,
     # the kept ones FP64; NOT_SPD when the truncation is indefinite
     dst = []
     if not args.no_dst:

@@ -127,7 +127,7 @@ typedef struct geo_trace_rec {
  * no larger than that of FP64 accumulation (measured against exact sums). */
 #define GEO_FLAG_FP64_DMMA 4
 /* Approximation option (tensor-core mode, default scheduler): the Diagonal
- * Super-Tile (DST) method of Section III, the tile form of the independent-
+ * Super-Tile (DST) method of Section V-B, the tile form of the independent-
  * blocks (IND) approximation.  Tile (i,j) of the covariance is kept, in FP64,
  * when i - j < band and set to zero otherwise; the factorization, log-
  * determinant and solve then follow Eq. 2 for that matrix.  Its Cholesky
@@ -138,7 +138,7 @@ typedef struct geo_trace_rec {
  * GEO_FLAG_STEPWISE or GEO_FLAG_FP64_DMMA (geo_tiles_set_flags returns -2). */
 #define GEO_FLAG_DST 8
 
-/* A1, "appropriate ordering" (Section IV): Z-order permutation of n locations.
+/* A1, "appropriate ordering" (Section VI): Z-order permutation of n locations.
  * Each coordinate c (expected in [0,1]) is quantised to q = clamp(floor(c*2^16),
  * 0, 2^16-1); the key interleaves qx (even bits) and qy (odd bits); perm[new] =
  * old index, sorted by (key, old index).  Host-only; x, y, perm are host arrays.
@@ -221,7 +221,7 @@ int geo_logdet_trsv_noalloc(const geo_tiles* t, const double* d_z, double* d_log
 int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream);
 
 /* A2-A11: generation, Algorithm 1, log-determinant and forward solve of Eq. 2
- * (Section III, Eq. 1-2; Algorithm 1), enqueued on `stream` without waiting.
+ * (Section IV, Eq. 1-2; Algorithm 1), enqueued on `stream` without waiting.
  * d_res (caller-owned device FP64[2]) receives log|Sigma| and Z' Sigma^-1 Z;
  * Eq. 2 is then -n/2 log(2 pi) - d_res[0]/2 - d_res[1]/2.  d_x, d_y, d_z:
  * device FP64[n], Morton-ordered, read only.  On the persistent tile-DAG path
@@ -239,7 +239,7 @@ int geo_loglik_async(geo_tiles* t, const double* d_x, const double* d_y, const d
 int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z,
                geo_theta theta, double* h_out, int* h_info, void* stream);
 
-/* Maximum likelihood estimation (Section III-A).  theta-hat maximises Eq. 2
+/* Maximum likelihood estimation (Section IV-C).  theta-hat maximises Eq. 2
  * over (sigma2, beta, nu), or, with profile = 1, Eq. 3 over (beta, nu) with
  * theta1 = Z' S~^-1 Z / n (S~ the covariance at unit variance, the nugget taken
  * relative to theta1).  The paper drives this with NLopt at tolerance 1e-3
@@ -312,7 +312,7 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
 int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_theta, void* d_work,
                      double* d_out, void* stream);
 
-/* A13, prediction (Section VI-B; simple kriging reading): with t holding the
+/* A13, prediction (Section VII-D; simple kriging reading): with t holding the
  * factor of Sigma(theta) over the observed locations (d_x, d_y, n = t->lay.n)
  * and observations d_z, write d_zhat[m] = Sigma_new,obs Sigma^-1 Z for the m
  * new locations (d_xnew, d_ynew).  d_work: device FP64 scratch of

@@ -15,7 +15,7 @@ Paper: Abdulah, Ltaief, Sun, Genton, Keyes, "Geostatistical Modeling and
 Prediction Using Mixed-Precision Tile Cholesky Factorization" (2019).
 
 Function -> paper passage -> what pins it (tests/test_oracle_pins.py):
-  morton_keys / morton_order   "appropriate ordering" (Section IV, mixed-
+  morton_keys / morton_order   "appropriate ordering" (Section VI, mixed-
                                precision Cholesky); Z-order reading    hand-worked
                                                                         keys, 2x2 grid
   matern                       Eq. 1                                    closed forms
@@ -34,14 +34,14 @@ Function -> paper passage -> what pins it (tests/test_oracle_pins.py):
                                                                         Fig. 2 op trace
   loglik_mp                    Eq. 2 on the Algorithm 1 factor          within FP32-level
                                                                         error of dense
-  dst_covariance / loglik_dst   DST / IND approximation (Section III)    d = 1: sum of the
+  dst_covariance / loglik_dst   DST / IND approximation (Section V-B)  d = 1: sum of the
                                                                         blocks' own Eq. 2;
                                                                         d >= p: dense Eq. 2
-  krige                        prediction (Section VI-B); simple        interpolation at
+  krige                        prediction (Section VII-D); simple       interpolation at
                                kriging reading                          observed points
   profile_sigma2               Eq. 3 and theta1_opt = Z'S~^-1 Z / n     argmax of Eq. 2
                                                                         over theta1
-  nelder_mead                  the MLE's optimizer (Section III-A: the  convex quadratic,
+  nelder_mead                  the MLE's optimizer (Section IV-C: the  convex quadratic,
                                paper uses NLopt with tolerance 1e-3;    Rosenbrock, 1D
                                reading: Nelder & Mead 1965 simplex)     Markov MLE vs a
                                                                         grid search
@@ -269,9 +269,9 @@ def loglik_mp(x, y, z, theta: Theta, nb, band):
     return dict(loglik=_assemble(n, logdet, quad), logdet=logdet, quad=quad, info=0)
 
 
-# ------------------------------------------- DST / IND (Section III-B) ---
+# -------------------------------------------- DST / IND (Section V-B) ---
 def dst_covariance(S, nb, d):
-    """Diagonal Super-Tile approximation (Section III): the covariance with
+    """Diagonal Super-Tile approximation (Section V-B): the covariance with
     every tile (i, j) whose tile distance |i - j| is d or more set to zero
     (tiles of nb rows and columns, the last one possibly short).  d = 1 keeps
     the diagonal tiles only: the independent-blocks (IND) method."""
@@ -331,7 +331,7 @@ def profile_sigma2(x, y, z, beta, nu, nugget_ratio=0.0):
     return s2, prof
 
 
-# ------------------------------------------------------ MLE (Section III-A) ---
+# ------------------------------------------------------- MLE (Section IV-C) ---
 # The estimator theta-hat maximises Eq. 2.  The paper drives it with NLopt at an
 # optimisation tolerance of 1e-3 without naming the method; the reading here is
 # the Nelder-Mead simplex (Nelder & Mead, 1965) over log-parameters with the

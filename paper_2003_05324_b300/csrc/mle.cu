@@ -1,4 +1,4 @@
-// Maximum likelihood estimation (Section III-A): the Nelder-Mead simplex over
+// Maximum likelihood estimation (Section IV-C): the Nelder-Mead simplex over
 // log-parameters driving full evaluations of Eq. 2 (or Eq. 3) through the
 // library's own geo_loglik.  Host code; every evaluation runs on the device.
 #include <math.h>

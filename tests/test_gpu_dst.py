@@ -1,4 +1,4 @@
-"""The DST / IND approximation (Section III) on the GPU against the oracle.
+"""The DST / IND approximation (Section V-B) on the GPU against the oracle.
 
 Tiles at tile distance >= d are zero and get no tasks; the kept tiles are
 FP64 and the in-band updates FP64-accurate, so the result is the oracle's

@@ -1,4 +1,4 @@
-"""Maximum likelihood estimation on the GPU (geo_mle, Section III-A).
+"""Maximum likelihood estimation on the GPU (geo_mle, Section IV-C).
 
 * The FP64 GPU path follows the oracle's simplex step for step: with the same
   theta0 and budget, the two objectives agree to ~1e-13, so the evaluation and

@@ -425,7 +425,7 @@ def test_nelder_mead_hand_traced_steps():
     assert abs(u[0] + 0.05) <= 1e-15 and abs(f - 0.0025) <= 1e-16
 
 
-# ---- DST / IND approximation (Section III) ---------------------------------
+# ---- DST / IND approximation (Section V-B) --------------------------------
 def _dst_problem(m=18, seed=31):
     x, y = inputs.jittered_grid(m, seed=seed)
     perm = O.morton_order(x, y)
