@@ -59,3 +59,28 @@ def test_single_rank_is_unchanged():
     assert bench.max_over_ranks(42.0, 1, "cpu") == 42.0
     evals, tflops = bench.replica_throughput(500.0, 1, 5, 2.0e13)
     assert abs(evals - 10.0) < 1e-12 and abs(tflops - 200.0) < 1e-9
+
+
+def test_tile_mix_roofline_sums_the_unit_terms():
+    # T* = sum of F_unit / P_unit over the kernel's units + 2 x stored bytes / BW
+    import types
+    import bench
+    rows = [{"kernel": "dag_kernel (test)", "unit_lower_bounds_ms": {"a": 3.0, "b": 5.0, "c": 90.0}},
+            {"kernel": "other", "unit_lower_bounds_ms": {"z": 1000.0}}]
+    ts = types.SimpleNamespace(lay=types.SimpleNamespace(bytes_dp=1_000_000_000, bytes_sp=2_000_000_000))
+    r = bench.tile_mix_roofline(rows, ts, 200.0)
+    bw = bench.measured_hbm_gbs()[0]
+    hbm_ms = 2 * 3e9 / (bw * 1e9) * 1e3
+    assert abs(r["t_star_ms"] - (98.0 + hbm_ms)) < 1e-9
+    assert abs(r["frac"] - r["t_star_ms"] / 200.0) < 1e-12
+    assert r["largest_term_ms"] == 90.0
+    assert bench.tile_mix_roofline([{"kernel": "other", "unit_lower_bounds_ms": {}}], ts, 1.0) is None
+
+
+def test_dag_traffic_is_keyed_by_the_kernel_sources():
+    import bench
+    h = bench.dag_source_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
+    assert h == bench.dag_source_hash()          # stable
+    for key, val in bench.DAG_TRAFFIC.items():
+        assert len(key) == 16 and val > 0
