@@ -47,12 +47,14 @@ extern "C" {
 #define GEO_ERR_UNSUPPORTED 4  /* a valid but unimplemented configuration */
 #define GEO_ERR_TOO_LARGE 5    /* the problem exceeds a fixed-size internal buffer */
 
-/* LP (off-band) arithmetic.  GEO_LP_SPLIT_BF16 runs the off-band updates on
- * the tcgen05 tensor cores: each FP32 panel row is scaled by a power of two and
- * cut into three 8-bit integer slices held exactly in BF16; six slice products
- * (those of weight >= 2^-16 of the leading one) are accumulated in FP32 tensor
- * memory, the leading product exactly.  GEO_LP_FP32 runs them as FP32 FMA on
- * the CUDA cores.  Both store off-band tiles in FP32. */
+/* LP (off-band) arithmetic.  GEO_LP_SPLIT_BF16 (the name of the tensor-core
+ * slice mode) runs the off-band updates on the tcgen05 tensor cores: each
+ * panel row is scaled by a power of two and cut exactly into an 8-bit and two
+ * 12-bit integer slices held in FP16 planes; six FP16 slice products (those of
+ * weight >= 2^-24 of the leading one) are accumulated in FP32 tensor memory,
+ * the leading product exactly.  In-band updates use seven 8-bit slices held in
+ * BF16.  GEO_LP_FP32 runs the off-band updates as FP32 FMA on the CUDA cores.
+ * Both store off-band tiles in FP32. */
 #define GEO_LP_SPLIT_BF16 0
 #define GEO_LP_FP32 1
 
@@ -88,6 +90,7 @@ typedef struct geo_tiles {
     int flags;                    /* GEO_FLAG_* options, set with geo_tiles_set_flags */
     void* trace;                  /* optional device trace buffer (geo_tiles_set_trace) */
     long long trace_cap;          /* its capacity in records */
+    long long timeout_ns;         /* bound of every device-side wait (geo_tiles_set_timeout_ns); 0 = default */
 } geo_tiles;
 
 /* One record of the device-side task trace (tensor-core mode scheduler):
@@ -137,6 +140,17 @@ typedef struct geo_trace_rec {
  * failing pivot reports GEO_ERR_NOT_SPD as for any other matrix.  Not with
  * GEO_FLAG_STEPWISE or GEO_FLAG_FP64_DMMA (geo_tiles_set_flags returns -2). */
 #define GEO_FLAG_DST 8
+/* Test hook (persistent scheduler only): the tensor-core update items of the
+ * first step wait for one more solved row chunk of their panel tile than the
+ * tile has, so that dependency can never be met.  The bounded wait then ends
+ * the launch: the status words record GEO_ERR_TIMEOUT with the wait's
+ * location code (31, read back by geo_status), every worker leaves, the
+ * tensor-core group returns its tensor memory, and the store can be evaluated
+ * again once the flag is cleared.  Used with a short geo_tiles_set_timeout_ns
+ * bound to exercise the failure path without faulting or hanging the device. */
+#define GEO_FLAG_TEST_STALL 16
+/* Default bound of a device-side wait of the persistent scheduler. */
+#define GEO_DEFAULT_TIMEOUT_NS 10000000000LL
 
 /* A1, "appropriate ordering" (Section VI): Z-order permutation of n locations.
  * Each coordinate c (expected in [0,1]) is quantised to q = clamp(floor(c*2^16),
@@ -158,6 +172,15 @@ int geo_tiles_bind(geo_tiles* t, const geo_layout* lay, void* d_dp, void* d_sp,
                    void* d_planes, void* d_meta, void* stream);
 int geo_tiles_release(geo_tiles* t);
 int geo_tiles_set_flags(geo_tiles* t, int flags);
+/* Bound, in nanoseconds of %globaltimer, of every wait inside the persistent
+ * factorization kernel on this store (a dependency counter, a queue claim, a
+ * copy or tensor-core hand-off): a wait that exceeds it abandons the launch
+ * with GEO_ERR_TIMEOUT and a location code in the status words (geo_status),
+ * and the store stays usable.  Batched launches use the bound of their first
+ * item's store.  ns = 0 restores the default GEO_DEFAULT_TIMEOUT_NS; otherwise
+ * 1e5 <= ns <= 1e12 (returns -2 outside).  Legitimate waits last at most as
+ * long as the factorization itself. */
+int geo_tiles_set_timeout_ns(geo_tiles* t, long long ns);
 /* Record every scheduler task of the following factorizations into d_trace
  * (device memory: one unsigned long long record counter, padded to 64 bytes,
  * then `capacity` geo_trace_rec).  The caller zeroes the counter; records past
@@ -192,7 +215,8 @@ int geo_potrf_mp(geo_tiles* t, void* stream);
 /* A10-A11, Eq. 2: from the factored store and Z (device FP64[n]), write
  * d_logdet[0] = log|Sigma| = 2 sum log L_ii and d_quad[0] = ||L^-1 Z||^2
  * (device FP64 scalars), and, if d_y != NULL, y = L^-1 Z (device FP64[p*nb]).
- * FP64 accumulation.  Asynchronous. */
+ * FP64 accumulation.  When the store's status records a failed factorization
+ * (not positive definite, timeout) both scalars are set to NaN.  Asynchronous. */
 int geo_logdet_trsv(const geo_tiles* t, const double* d_z, double* d_logdet, double* d_quad,
                     double* d_y, void* stream);
 
@@ -207,6 +231,8 @@ int geo_logdet_trsv(const geo_tiles* t, const double* d_z, double* d_logdet, dou
  * GEO_NOALLOC_MAX_P tiles per side; larger problems return GEO_ERR_TOO_LARGE
  * without launching anything.  The caller still passes the factored store, Z
  * and the two output scalars (device FP64), exactly as for geo_logdet_trsv.
+ * When the store's factorization failed both scalars are set to NaN (never a
+ * stale value left in the array by an earlier call).
  * The array is shared by every call in the process: calls whose work overlaps
  * on the GPU (different streams, no ordering between them) race on it.  The
  * first call on each device looks up the array's device address (no
@@ -217,18 +243,21 @@ int geo_logdet_trsv_noalloc(const geo_tiles* t, const double* d_z, double* d_log
                             void* stream);
 
 /* Copy the status words to the host (blocking on `stream`): *h_code = GEO_OK or
- * a GEO_ERR_* code, *h_info = 1-based failing row for GEO_ERR_NOT_SPD. */
+ * a GEO_ERR_* code; *h_info = the 1-based failing row for GEO_ERR_NOT_SPD, the
+ * location code of the wait that gave up for GEO_ERR_TIMEOUT. */
 int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream);
 
-/* A2-A11: generation, Algorithm 1, log-determinant and forward solve of Eq. 2
- * (Section IV, Eq. 1-2; Algorithm 1), enqueued on `stream` without waiting.
- * d_res (caller-owned device FP64[2]) receives log|Sigma| and Z' Sigma^-1 Z;
- * Eq. 2 is then -n/2 log(2 pi) - d_res[0]/2 - d_res[1]/2.  d_x, d_y, d_z:
- * device FP64[n], Morton-ordered, read only.  On the persistent tile-DAG path
- * (split-BF16 stores) the forward solve runs inside the factorization launch,
- * per element the same arithmetic as geo_logdet_trsv.  A failure (not positive
- * definite, timeout) is recorded in the status words (geo_status) and leaves
- * d_res undefined.  Returns GEO_OK or a negative argument index / GEO_ERR_CUDA. */
+/* A2-A12: generation, Algorithm 1, log-determinant, forward solve and
+ * assembly of Eq. 2 (Section IV, Eq. 1-2; Algorithm 1), enqueued on `stream`
+ * without waiting.  d_res (caller-owned device FP64[3]) receives
+ *   d_res[0] = log|Sigma|, d_res[1] = Z' Sigma^-1 Z,
+ *   d_res[2] = l(theta) = -n/2 log(2 pi) - d_res[0]/2 - d_res[1]/2,
+ * all computed on the device.  d_x, d_y, d_z: device FP64[n], Morton-ordered,
+ * read only.  On the persistent tile-DAG path (split-BF16 stores) the forward
+ * solve runs inside the factorization launch, per element the same arithmetic
+ * as geo_logdet_trsv.  A failure (not positive definite, timeout) is recorded
+ * in the status words (geo_status) and leaves NaN in all three entries.
+ * Returns GEO_OK or a negative argument index / GEO_ERR_CUDA. */
 int geo_loglik_async(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta,
                      double* d_res, void* stream);
 
@@ -312,7 +341,7 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
 int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_theta, void* d_work,
                      double* d_out, void* stream);
 
-/* A13, prediction (Section VII-D; simple kriging reading): with t holding the
+/* A13, prediction (Section VIII-D; simple kriging reading): with t holding the
  * factor of Sigma(theta) over the observed locations (d_x, d_y, n = t->lay.n)
  * and observations d_z, write d_zhat[m] = Sigma_new,obs Sigma^-1 Z for the m
  * new locations (d_xnew, d_ynew).  d_work: device FP64 scratch of
@@ -323,13 +352,14 @@ int geo_krige(const geo_tiles* t, const double* d_x, const double* d_y, const do
 
 /* Instrumentation.  geo_kernel_launches returns the number of kernel launches
  * this library has issued in the process (all entry points, all devices).
- * geo_profile_enable(1) makes geo_potrf_mp bracket each launch of its
- * factorization kernels with CUDA events on the stream it launches them on;
+ * geo_profile_enable(1) makes geo_potrf_mp (and the evaluation calls) bracket
+ * each launch of its kernels with CUDA events on the stream it launches them on;
  * geo_profile_read (blocking: synchronizes those events) returns, for
  * kind 0 = FP64 update (dsyrk/dgemm), 1 = off-band update (tensor-core or
  * FP32), 2 = diagonal-tile potrf, 3 = panel trsm (kinds 0-3: the step-by-step
  * driver), 4 = the persistent tile-DAG kernel (the whole factorization in one
- * launch), the summed event time in ms and the launch count since the last
+ * launch), 5 = the covariance generation of geo_loglik / geo_loglik_async, the
+ * summed event time in ms and the launch count since the last
  * geo_profile_reset.  An unknown kind returns -1. */
 unsigned long long geo_kernel_launches(void);
 int geo_profile_enable(int on);

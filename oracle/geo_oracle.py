@@ -37,7 +37,7 @@ Function -> paper passage -> what pins it (tests/test_oracle_pins.py):
   dst_covariance / loglik_dst   DST / IND approximation (Section V-B)  d = 1: sum of the
                                                                         blocks' own Eq. 2;
                                                                         d >= p: dense Eq. 2
-  krige                        prediction (Section VII-D); simple       interpolation at
+  krige                        prediction (Section VIII-D); simple       interpolation at
                                kriging reading                          observed points
   profile_sigma2               Eq. 3 and theta1_opt = Z'S~^-1 Z / n     argmax of Eq. 2
                                                                         over theta1

@@ -2,7 +2,7 @@
 
     python -m paper_2003_05324_b300.accuracy_study --m 100 --betas 0.03 0.1 0.3 --seeds 0 1
 
-A reduced form of the paper's Monte-Carlo study (Section VII-D): for each range
+A reduced form of the paper's Monte-Carlo study (Section VIII-D): for each range
 parameter theta2 (weak / medium / strong correlation) and seed,
 
 * locations: an m x m jittered grid (seed), Morton order;

@@ -78,7 +78,7 @@ struct ProfSlot {
     double ms = 0.0;
     long long launches = 0;
 };
-static ProfSlot g_slots[5];
+static ProfSlot g_slots[6];
 static std::mutex g_prof_mu;
 
 void count_launch(int n) { g_launches += (unsigned long long)n; }
@@ -299,11 +299,20 @@ int geo_tiles_release(geo_tiles* t) {
 
 int geo_tiles_set_flags(geo_tiles* t, int flags) {
     if (!t) return -1;
-    if (flags & ~(GEO_FLAG_FP64_OFFBAND_GEN | GEO_FLAG_STEPWISE | GEO_FLAG_FP64_DMMA | GEO_FLAG_DST)) return -2;
+    if (flags & ~(GEO_FLAG_FP64_OFFBAND_GEN | GEO_FLAG_STEPWISE | GEO_FLAG_FP64_DMMA | GEO_FLAG_DST |
+                  GEO_FLAG_TEST_STALL))
+        return -2;
     if ((flags & GEO_FLAG_DST) &&
         ((flags & (GEO_FLAG_STEPWISE | GEO_FLAG_FP64_DMMA)) || t->lay.lp_mode != GEO_LP_SPLIT_BF16))
         return -2;
     t->flags = flags;
+    return GEO_OK;
+}
+
+int geo_tiles_set_timeout_ns(geo_tiles* t, long long ns) {
+    if (!t) return -1;
+    if (ns != 0 && (ns < 100000LL || ns > 1000000000000LL)) return -2;
+    t->timeout_ns = ns;
     return GEO_OK;
 }
 
@@ -421,25 +430,32 @@ int geo_status(const geo_tiles* t, int* h_code, int* h_info, void* stream) {
     if (check_bound(t)) return -1;
     if (!h_code) return -2;
     Layout L = make_layout(t);
-    int st[2] = {0, 0};
+    int st[3] = {0, 0, 0};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(st, L.status, sizeof(st), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return GEO_ERR_CUDA;
-    *h_code = st[0];
-    if (h_info) *h_info = st[1];
+    *h_code = st[ST_CODE];
+    if (h_info) *h_info = st[ST_CODE] == GEO_ERR_TIMEOUT ? st[ST_TIMEOUT_WHERE] : st[ST_INFO];
     return GEO_OK;
 }
 
+// d_res[0..2] = (log|Sigma|, Z' Sigma^-1 Z, Eq. 2), all three NaN when the
+// factorization fails: they start as NaN (every byte 0xFF) and only the
+// solve's last step, which runs after every tile was factored, writes them.
 static int loglik_enqueue(geo_tiles* t, const double* d_x, const double* d_y, const double* d_z, geo_theta theta,
                           double* d_res, cudaStream_t s) {
     Layout L = make_layout(t);
     int rc = reset_status(L, s);
     if (rc) return rc;
-    if (launch_matern_tiles(L, d_x, d_y, theta, nullptr, 0, s)) return GEO_ERR_CUDA;
+    if (cudaMemsetAsync(d_res, 0xFF, 3 * sizeof(double), s)) return GEO_ERR_CUDA;
+    prof_begin(5, s);
+    const cudaError_t eg = launch_matern_tiles(L, d_x, d_y, theta, nullptr, 0, s);
+    prof_end(5, s);
+    if (eg) return GEO_ERR_CUDA;
     bool solved = false;
     if (factor(t, L, d_z, d_res, &solved, s)) return GEO_ERR_CUDA;
-    if (!solved && run_logdet_trsv(L, d_z, d_res, d_res + 1, nullptr, s)) return GEO_ERR_CUDA;
+    if (!solved && run_logdet_trsv(L, d_z, d_res, d_res + 1, nullptr, s, d_res + 2)) return GEO_ERR_CUDA;
     return GEO_OK;
 }
 
@@ -467,7 +483,7 @@ int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double*
     double* res = L.scal + 2 * L.p;
     const int rc = loglik_enqueue(t, d_x, d_y, d_z, theta, res, s);
     if (rc) return rc;
-    double hres[2];
+    double hres[3];
     int st[2];
     cudaError_t e = cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(st, L.status, sizeof(st), cudaMemcpyDeviceToHost, s);
@@ -475,7 +491,7 @@ int geo_loglik(geo_tiles* t, const double* d_x, const double* d_y, const double*
     if (e) return GEO_ERR_CUDA;
     if (h_info) *h_info = st[1];
     if (st[0] != 0) return st[0];
-    h_out[0] = assemble_loglik(L.n, hres[0], hres[1]);
+    h_out[0] = hres[2];   // Eq. 2, assembled on the device
     h_out[1] = hres[0];
     h_out[2] = hres[1];
     return GEO_OK;
@@ -516,7 +532,7 @@ int geo_profile_reset(void) {
 }
 
 int geo_profile_read(int kind, double* h_ms, long long* h_launches) {
-    if (kind < 0 || kind > 4) return -1;
+    if (kind < 0 || kind > 5) return -1;
     if (!h_ms) return -2;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     prof_collect(g_slots[kind]);
@@ -694,7 +710,8 @@ int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_
     if (run_potrf_dag_batch((const ProbDev*)(base + m.off_probs), nprob, (const G2Task*)(base + m.off_prio),
                             m.n_prio, (const G2Task*)(base + m.off_bulk), m.n_bulk,
                             (const int4*)(base + m.off_tct), m.n_tct, m.per, (int*)(base + m.off_ctr),
-                            m.counter_bytes, items[0].t->trace, items[0].t->trace_cap, small_dp, s))
+                            m.counter_bytes, items[0].t->trace, items[0].t->trace_cap, small_dp,
+                            items[0].t->timeout_ns, s))
         return GEO_ERR_CUDA;
     if (launch_trsv_batch((const SolveJob*)(base + m.off_jobs), nprob, m.pmax, d_out,
                           (unsigned*)(base + m.off_ctr) + 8, s))

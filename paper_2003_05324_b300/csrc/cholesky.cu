@@ -5,9 +5,11 @@
 //   trsm    every panel tile (i,k), i > k: X <- X L_kk^-T; FP64 for tiles
 //           within the band, FP32 arithmetic against the FP32 copy of L_kk
 //           (tmp_0k) for the others                                      (dtrsm / strsm)
-//   split   FP32 value of each panel tile -> three BF16 planes for the
-//           tensor-core off-band update (the SP copy of in-band panel tiles,
-//           Algorithm 1's dconv2s, is the FP32 rounding taken here)
+//   split   each solved panel tile -> its fixed-point slice planes (row scale
+//           exponent, 8-bit slices held in BF16) for the tensor-core updates;
+//           this step-by-step path's off-band update reads four of them (the
+//           SP copy of in-band panel tiles, Algorithm 1's dconv2s, is the
+//           FP32-level value these slices carry)
 //   update  trailing tiles (i,j), k < j <= i: FP64 for the diagonal (dsyrk,
 //           always FP64) and the band (dgemm), FP32-accurate for the rest
 //           (sgemm).  The FP64 and off-band updates run concurrently on two

@@ -203,7 +203,6 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
 // ----------------------------------------------------------- device side ---
 constexpr int G2_THREADS = 128;
 constexpr int DAG_THREADS = TC_THREADS + G2_THREADS;
-constexpr long long DAG_WAIT_NS = 10000000000LL;   // 10 s per wait (legitimate waits are ms)
 constexpr int RING = 8;
 constexpr size_t DAG_DYN_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ring*/;
 
@@ -225,6 +224,7 @@ struct DagArgs {
     unsigned long long* trace_ctr;   // optional task trace (nullptr: off)
     geo_trace_rec* trace;
     long long trace_cap;
+    long long wait_ns;       // bound of every wait of the launch (geo_tiles_set_timeout_ns)
 };
 
 __device__ __forceinline__ const ProbDev& prob_of(const DagArgs& A, int pid) {
@@ -268,7 +268,7 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" :::
 // launch: a timeout means the schedule itself went wrong).
 __device__ bool wait_ge(const DagArgs& A, const Layout& L, const int* p, int v, int where) {
     if (ld_acquire_s32(p) >= v) return true;
-    const long long dl = gtimer() + DAG_WAIT_NS;
+    const long long dl = gtimer() + A.wait_ns;
     for (unsigned it = 1;; ++it) {
         __nanosleep(64);
         if (ld_acquire_s32(p) >= v) return true;
@@ -1004,7 +1004,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
         // when none is available.
         if (g == 0) {
             int kind = -1, idx = -1;
-            const long long dl = gtimer() + DAG_WAIT_NS;
+            const long long dl = gtimer() + A.wait_ns;
             for (unsigned spin = 0; kind < 0; ++spin) {
                 if (aborted(A) || (!A.probs && failed(A.one.L))) break;
                 const int yh = A.n_y > 0 ? ld_volatile(y_head) : 0;
@@ -1181,7 +1181,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                     }
                 g2_sync();
                 ysolve_diag_tile(L, k, yv, L.scal, g, G2_THREADS, S.yd, G2Sync());
-                if (k == L.p - 1 && g == 0) ysolve_finish(L, L.scal, P.res, P.res + 1);
+                if (k == L.p - 1 && g == 0) ysolve_finish(L, L.scal, P.res, P.res + 1, P.res + 2);
                 done = P.ydone + k;
                 break;
             }
@@ -1222,10 +1222,10 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
 
 // ---- tensor group: the split-BF16 update with dynamic items and dependencies
 // bounded mbarrier wait for the scheduler: gives up when the launch is aborted
-// (or a single problem has failed), on an abort of this CTA, or after DAG_WAIT_NS
+// (or a single problem has failed), on an abort of this CTA, or after the launch's wait bound
 __device__ bool dwait(const DagArgs& A, uint32_t bar, uint32_t parity, volatile int* abort_flag) {
     if (mbar_try(bar, parity)) return true;
-    const long long dl = gtimer() + DAG_WAIT_NS;
+    const long long dl = gtimer() + A.wait_ns;
     for (unsigned it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 255u) == 0) {
@@ -1296,7 +1296,11 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                     red_release_add(P.upd + m.i * P.L.p + m.j, 1);
                     continue;
                 }
-                const bool ok = wait_ge(A, P.L, P.tcnt + m.i * P.L.p + m.k, chunks_of(P, m.i, m.k), 31) &&
+                // (the test hook GEO_FLAG_TEST_STALL asks the items of step 0
+                // for one solved row chunk more than the panel tile has: that
+                // wait can never be met and must end by its bound)
+                const int stall = (P.L.flags & GEO_FLAG_TEST_STALL) && m.k == 0;
+                const bool ok = wait_ge(A, P.L, P.tcnt + m.i * P.L.p + m.k, chunks_of(P, m.i, m.k) + stall, 31) &&
                                 wait_ge(A, P.L, P.tcnt + m.j * P.L.p + m.k, chunks_of(P, m.j, m.k), 32);
                 if (!ok) {
                     if (!single && !aborted(A)) continue;   // its problem failed meanwhile
@@ -1389,7 +1393,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
             }
         }
         for (int q = max(0, it - TC_STAGES); q < it; ++q)
-            mbar_wait(FULL(q % TC_STAGES), (q / TC_STAGES) & 1, gtimer() + TC_WAIT_NS);
+            mbar_wait(FULL(q % TC_STAGES), (q / TC_STAGES) & 1, gtimer() + min(A.wait_ns, TC_WAIT_NS));
     } else if (warp == 1) {
         if (lane != 0) return;
         int it = 0;
@@ -1520,7 +1524,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
         }
         if (it > 0) {
             const int q = it - 1;
-            mbar_wait(EMPTY(q % TC_STAGES), (q / TC_STAGES) & 1, gtimer() + TC_WAIT_NS);
+            mbar_wait(EMPTY(q % TC_STAGES), (q / TC_STAGES) & 1, gtimer() + min(A.wait_ns, TC_WAIT_NS));
         }
     } else {
         // epilogue warps 2..5: TMEM lane quadrant warp % 4
@@ -1801,6 +1805,7 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
     A.trace_ctr = (unsigned long long*)t->trace;
     A.trace = t->trace ? (geo_trace_rec*)((char*)t->trace + 64) : nullptr;
     A.trace_cap = t->trace_cap;
+    A.wait_ns = t->timeout_ns > 0 ? t->timeout_ns : GEO_DEFAULT_TIMEOUT_NS;
     CUtensorMap maps[3];
     memcpy(maps, t->tmap, sizeof(maps));
     void* args[] = {&A, &maps[0], &maps[1], &maps[2]};
@@ -1871,7 +1876,7 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
                                 const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
                                 int* counters, size_t counter_bytes, void* trace, long long trace_cap,
-                                bool small_dp, cudaStream_t s) {
+                                bool small_dp, long long wait_ns, cudaStream_t s) {
     int nsm = 0;
     cudaError_t e = small_dp ? dag_prepare<true>(nsm) : dag_prepare<false>(nsm);
     if (e) return e;
@@ -1890,6 +1895,7 @@ cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task*
     A.trace_ctr = (unsigned long long*)trace;
     A.trace = trace ? (geo_trace_rec*)((char*)trace + 64) : nullptr;
     A.trace_cap = trace_cap;
+    A.wait_ns = wait_ns > 0 ? wait_ns : GEO_DEFAULT_TIMEOUT_NS;
     (void)nprob;
     CUtensorMap maps[3];
     memset(maps, 0, sizeof(maps));   // unused: each problem's maps are in its view

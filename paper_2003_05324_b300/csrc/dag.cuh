@@ -52,7 +52,7 @@ struct ProbDev {
     SchedGeom g;
     int *upd, *tcnt, *pot, *sub, *ycnt, *ydone;
     const double* z;
-    double* res;   // (log|Sigma|, Z' Sigma^-1 Z) of the fused solve
+    double* res;   // (log|Sigma|, Z' Sigma^-1 Z, Eq. 2) of the fused solve
     const int* trsm_end;
     const CUtensorMap* tmap;
 };
@@ -65,8 +65,8 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex, bool dst = false)
 // yq: the forward-solve queue (claimed only when its head is ready)
 void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::vector<G2Task>& bulk,
                  std::vector<int>& trsm_end, std::vector<G2Task>& yq, std::vector<int4>& tct);
-// z: Z for the fused forward solve (log-det and quadratic form into res[0..1]),
-// or nullptr to factor only
+// z: Z for the fused forward solve (log-det, quadratic form and Eq. 2 into
+// res[0..2]), or nullptr to factor only
 cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, const double* z, double* res,
                           cudaStream_t s);
 
@@ -89,6 +89,6 @@ void bind_counters(ProbDev& P, int* base);
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
                                 const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
                                 int* counters, size_t counter_bytes, void* trace, long long trace_cap,
-                                bool small_dp, cudaStream_t s);
+                                bool small_dp, long long wait_ns, cudaStream_t s);
 
 }  // namespace geo

@@ -108,8 +108,9 @@ cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* 
 cudaError_t launch_load_dense(const Layout& L, const double* a, cudaStream_t s);
 cudaError_t launch_to_dense(const Layout& L, double* out, cudaStream_t s);
 cudaError_t run_potrf_mp(const geo_tiles* t, const Layout& L, cudaStream_t s);
+// loglik (optional): also Eq. 2 assembled on the device
 cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, double* quad, double* y,
-                            cudaStream_t s);
+                            cudaStream_t s, double* loglik = nullptr);
 cudaError_t run_logdet_trsv_noalloc(const Layout& L, const double* z, double* logdet, double* quad,
                                     cudaStream_t s);
 // bar: 4 unsigned of device scratch for the launch's grid barrier

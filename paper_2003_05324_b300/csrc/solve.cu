@@ -57,9 +57,18 @@ __global__ void trsv_load_kernel(Layout L, const double* __restrict__ z, double*
     if (g < L.p * L.nb) yv[g] = g < L.n ? z[g] : 0.0;
 }
 
-__global__ void trsv_finish_kernel(Layout L, const double* __restrict__ part, double* logdet, double* quad) {
+// The per-tile partials exist only when every diagonal solve ran: after a
+// failed factorization (the solves return early) the outputs are NaN, never
+// partials left over from an earlier solve in the same scratch.
+__global__ void trsv_finish_kernel(Layout L, const double* __restrict__ part, double* logdet, double* quad,
+                                   double* loglik) {
     if (threadIdx.x != 0) return;
-    ysolve_finish(L, part, logdet, quad);
+    if (failed(L)) {
+        *logdet = *quad = nan("");
+        if (loglik) *loglik = nan("");
+        return;
+    }
+    ysolve_finish(L, part, logdet, quad, loglik);
 }
 
 static cudaError_t forward_solve(const Layout& L, double* yv, double* part, cudaStream_t s) {
@@ -193,7 +202,7 @@ cudaError_t launch_trsv_batch(const SolveJob* d_jobs, int nprob, int pmax, doubl
 }
 
 cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, double* quad, double* y,
-                            cudaStream_t s) {
+                            cudaStream_t s, double* loglik) {
     double* yv = y ? y : L.scal + 2 * L.p + 8;
     double* part = L.scal;
     const int np = L.p * L.nb;
@@ -201,17 +210,19 @@ cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, do
     count_launch();
     cudaError_t e = forward_solve(L, yv, part, s);
     if (e) return e;
-    trsv_finish_kernel<<<1, 32, 0, s>>>(L, part, logdet, quad);
+    trsv_finish_kernel<<<1, 32, 0, s>>>(L, part, logdet, quad, loglik);
     count_launch();
     return cudaGetLastError();
 }
 
 // ------------------------------------------ allocation-free forward solve ---
 // Scratch of geo_logdet_trsv_noalloc: y (padded length) followed by the per-tile
-// partial sums.  Every entry the solve reads is written first in the same call
-// (the load kernel fills all of y, each tile writes its own partials), so
-// nothing needs clearing between calls.  The array is process-wide and shared
-// by all calls: calls that overlap on the GPU race on it.
+// partial sums.  On a store whose factorization succeeded every entry the
+// solve reads is written first in the same call (the load kernel fills all of
+// y, each tile writes its own partials), so nothing needs clearing between
+// calls; on a failed one the diagonal solves write nothing and the finish
+// kernel returns NaN instead of reading the partials.  The array is
+// process-wide and shared by all calls: calls that overlap on the GPU race on it.
 static __device__ __align__(256) double g_noalloc_scratch[GEO_NOALLOC_MAX_N + 2 * GEO_NOALLOC_MAX_P];
 
 // Device address of the array, looked up once per device (with that device
@@ -247,7 +258,7 @@ cudaError_t run_logdet_trsv_noalloc(const Layout& L, const double* z, double* lo
     count_launch();
     e = forward_solve(L, yv, part, s);
     if (e) return e;
-    trsv_finish_kernel<<<1, 32, 0, s>>>(L, part, logdet, quad);
+    trsv_finish_kernel<<<1, 32, 0, s>>>(L, part, logdet, quad, nullptr);
     count_launch();
     return cudaGetLastError();
 }

@@ -99,8 +99,10 @@ __device__ __forceinline__ double yrow_update(const Layout& L, int l, int i, int
     return acc;
 }
 
-// log|Sigma| and Z' Sigma^-1 Z from the per-tile partials, summed in tile order.
-__device__ __forceinline__ void ysolve_finish(const Layout& L, const double* part, double* logdet, double* quad) {
+// log|Sigma| and Z' Sigma^-1 Z from the per-tile partials, summed in tile
+// order, and (loglik != nullptr) Eq. 2 assembled from them.
+__device__ __forceinline__ void ysolve_finish(const Layout& L, const double* part, double* logdet, double* quad,
+                                              double* loglik = nullptr) {
     double s0 = 0.0, s1 = 0.0;
     for (int i = 0; i < L.p; ++i) {
         s0 += part[2 * i];
@@ -108,6 +110,7 @@ __device__ __forceinline__ void ysolve_finish(const Layout& L, const double* par
     }
     *logdet = s0;
     *quad = s1;
+    if (loglik) *loglik = assemble_loglik(L.n, s0, s1);
 }
 
 }  // namespace geo

@@ -8,7 +8,6 @@ no CPU fallback.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 from dataclasses import dataclass
 
@@ -16,8 +15,6 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgeo.so")
-
-LOG_2PI = math.log(2.0 * math.pi)
 
 GEO_OK = 0
 GEO_ERR_NOT_SPD = 1
@@ -33,6 +30,8 @@ GEO_FLAG_FP64_OFFBAND_GEN = 1
 GEO_FLAG_STEPWISE = 2
 GEO_FLAG_FP64_DMMA = 4
 GEO_FLAG_DST = 8
+GEO_FLAG_TEST_STALL = 16
+GEO_DEFAULT_TIMEOUT_NS = 10_000_000_000
 
 
 class GeoError(RuntimeError):
@@ -65,7 +64,8 @@ class geo_tiles(ctypes.Structure):
                 ("d_planes", ctypes.c_void_p), ("d_meta", ctypes.c_void_p),
                 ("aux_stream", ctypes.c_void_p), ("ev_fork", ctypes.c_void_p), ("ev_join", ctypes.c_void_p),
                 ("tmap", ctypes.c_uint64 * 48), ("flags", ctypes.c_int),
-                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_longlong)]
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_longlong),
+                ("timeout_ns", ctypes.c_longlong)]
 
 
 class geo_mle_opts(ctypes.Structure):
@@ -95,6 +95,7 @@ def _load():
         "geo_tiles_bind": [ctypes.POINTER(geo_tiles), ctypes.POINTER(geo_layout), P, P, P, P, P],
         "geo_tiles_release": [ctypes.POINTER(geo_tiles)],
         "geo_tiles_set_flags": [ctypes.POINTER(geo_tiles), I],
+        "geo_tiles_set_timeout_ns": [ctypes.POINTER(geo_tiles), ctypes.c_longlong],
         "geo_tiles_set_trace": [ctypes.POINTER(geo_tiles), P, ctypes.c_longlong],
         "geo_matern_tiles": [ctypes.POINTER(geo_tiles), P, P, geo_theta, P],
         "geo_tiles_load_dense": [ctypes.POINTER(geo_tiles), P, P],
@@ -198,6 +199,10 @@ class TileStore:
     def set_flags(self, flags: int):
         _check(lib.geo_tiles_set_flags(ctypes.byref(self.t), int(flags)), "geo_tiles_set_flags")
 
+    def set_timeout_ns(self, ns: int):
+        """Bound of every device-side wait of the persistent scheduler (0: default)."""
+        _check(lib.geo_tiles_set_timeout_ns(ctypes.byref(self.t), int(ns)), "geo_tiles_set_timeout_ns")
+
     def enable_trace(self, capacity: int = 1 << 20):
         """Record the scheduler's tasks of the following factorizations."""
         import torch
@@ -273,18 +278,16 @@ class TileStore:
                "geo_logdet_trsv")
         return ld, q, yv
 
-    def loglik_async(self, x, y, z, theta: Theta, stream=None):
-        """Generation, factorization, log-det and solve enqueued on the stream without
-        waiting (geo_loglik_async); returns device scalars (logdet, quad).  Assembly
-        of Eq. 2 from them is two scalar operations (`assemble`)."""
+    def loglik_async(self, x, y, z, theta: Theta, stream=None, out=None):
+        """Generation, factorization, log-det, solve and Eq. 2 enqueued on the
+        stream without waiting (geo_loglik_async).  Returns the device FP64[3]
+        tensor (log|Sigma|, Z' Sigma^-1 Z, l), written by the library's kernels
+        (NaN when the factorization fails); `out` may supply it."""
         import torch
-        res = torch.empty(2, dtype=torch.float64, device=self._dp.device)
+        res = out if out is not None else torch.empty(3, dtype=torch.float64, device=self._dp.device)
         _check(lib.geo_loglik_async(ctypes.byref(self.t), _ptr(x), _ptr(y), _ptr(z), theta.c(), _ptr(res),
                                     _stream(stream)), "geo_loglik_async")
-        return res[0:1], res[1:2]
-
-    def assemble(self, ld: float, q: float) -> float:
-        return -0.5 * self.n * LOG_2PI - 0.5 * ld - 0.5 * q
+        return res
 
     def loglik(self, x, y, z, theta: Theta, stream=None):
         """Eq. 2 (blocking): returns (loglik, logdet, quad)."""

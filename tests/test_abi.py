@@ -27,10 +27,35 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, nm), nm
 
 
-def test_struct_sizes_match_header():
-    # geo_theta: 4 doubles; geo_tiles = layout + 7 pointers + 32 u64 + int flags (padded) + trace ptr/cap
-    assert ctypes.sizeof(geo.geo_theta) == 32
-    assert ctypes.sizeof(geo.geo_tiles) == ctypes.sizeof(geo.geo_layout) + 7 * 8 + 384 + 8 + 16  # int+pad, trace
+def test_struct_sizes_match_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the sizes and field offsets a C
+    compiler gives the declarations in include/geo.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = {
+        "geo_theta": geo.geo_theta, "geo_layout": geo.geo_layout, "geo_tiles": geo.geo_tiles,
+        "geo_mle_opts": geo.geo_mle_opts, "geo_mle_result": geo.geo_mle_result,
+        "geo_batch_item": geo.geo_batch_item,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    for name, cls in checks.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-o", str(exe), str(src)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                    check=True).stdout.splitlines())
+    for name, cls in checks.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
 
 
 @pytest.mark.parametrize("n,nb,band", [(1600, 200, 8), (40000, 500, 1), (1000, 96, 2), (50, 64, 1), (1, 16, 1),
@@ -115,3 +140,14 @@ def test_morton_order_matches_oracle(seed):
     got = geo.morton_order(x, y)
     want = O.morton_order(x, y)
     assert np.array_equal(got, want)
+
+
+def test_timeout_and_flag_setters_validate_without_device_work():
+    t = geo.geo_tiles()
+    assert geo.lib.geo_tiles_set_timeout_ns(None, 0) == -1
+    for bad in (1, 99_999, 10 ** 13, -1):
+        assert geo.lib.geo_tiles_set_timeout_ns(ctypes.byref(t), bad) == -2
+    assert geo.lib.geo_tiles_set_timeout_ns(ctypes.byref(t), 50_000_000) == 0 and t.timeout_ns == 50_000_000
+    assert geo.lib.geo_tiles_set_timeout_ns(ctypes.byref(t), 0) == 0 and t.timeout_ns == 0
+    assert geo.lib.geo_tiles_set_flags(ctypes.byref(t), geo.GEO_FLAG_TEST_STALL) == 0
+    assert geo.lib.geo_tiles_set_flags(ctypes.byref(t), 1 << 10) == -2

@@ -333,16 +333,50 @@ def test_fused_solve_equals_standalone_solve(G, n, nb, band, flags):
     ts = G.TileStore(n, nb, band, G.GEO_LP_SPLIT_BF16)
     ts.set_flags(flags)
     l, ld, q = ts.loglik(X, Y, Z, th)
-    lda, qa = ts.loglik_async(X, Y, Z, th)
-    torch.cuda.synchronize()
+    lda, qa, la = ts.loglik_async(X, Y, Z, th).cpu().tolist()
     ts.matern(X, Y, th)
     ts.potrf()
     lds, qs, _ = ts.logdet_trsv(Z)
     torch.cuda.synchronize()
     assert ld == float(lds) and q == float(qs)
-    assert float(lda) == ld and float(qa) == q
+    assert lda == ld and qa == q and la == l
+    # Eq. 2 assembled on the device: the host's expression gives the same bits
+    assert la == -0.5 * n * math.log(2.0 * math.pi) - 0.5 * ld - 0.5 * q
     want = O.loglik_dense(x, y, z, oracle_theta(th))["loglik"]
     assert abs(l - want) <= 1e-6 * abs(want)
+
+
+def test_async_result_is_nan_when_not_spd(G):
+    """A factorization that meets a non-positive pivot leaves NaN in all three
+    device results of geo_loglik_async (never the values of an earlier call on
+    the same buffer), and the status words report it.  The failing case is the
+    DST truncation whose matrix is indefinite (smallest eigenvalue -0.35)."""
+    x, y = inputs.jittered_grid(40, seed=0)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.white_noise(len(x), seed=1)
+    X, Y, Z = dev(x), dev(y), dev(z)
+    ts = G.TileStore(len(z), 200, 3, G.GEO_LP_SPLIT_BF16)
+    ts.set_flags(G.GEO_FLAG_DST)
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    ts.loglik_async(X, Y, Z, G.Theta(1.0, 0.03, 0.5), out=out)
+    assert np.all(np.isfinite(out.cpu().numpy()))
+    ts.loglik_async(X, Y, Z, G.Theta(1.0, 0.03, 1.0), out=out)
+    code, _ = ts.status()
+    assert code == G.GEO_ERR_NOT_SPD
+    assert np.all(np.isnan(out.cpu().numpy()))
+
+
+def test_standalone_solve_is_nan_after_failed_factor(G):
+    """geo_logdet_trsv on a store whose factorization failed writes NaN."""
+    S = spd_matrix(300, seed=9)
+    S[211, 211] = -1.0
+    ts = G.TileStore(300, 64, 1, G.GEO_LP_FP32)
+    ts.load_dense(dev(S.T))
+    with pytest.raises(G.NotSPDError):
+        ts.potrf()
+    ld, q, _ = ts.logdet_trsv(dev(np.ones(300)))
+    assert math.isnan(float(ld)) and math.isnan(float(q))
 
 
 def test_loglik_deterministic(G):

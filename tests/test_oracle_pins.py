@@ -154,6 +154,61 @@ def _markov_loglik(x, z, sigma2, beta):
     return -0.5 * n * math.log(2 * math.pi) - 0.5 * logdet - 0.5 * quad, logdet, quad
 
 
+# --------------------------------------------- Eq. 1 on 2D locations ---
+def test_covariance_right_triangle_by_hand():
+    """Three points with hand-computed Euclidean distances 3/10, 4/10, 5/10 (a
+    3-4-5 right triangle, legs along x and along y): with nu = 1/2 Eq. 1 is
+    sigma2 exp(-r/beta).  A dropped or mis-signed dy term, or a distance taken
+    as |dx| + |dy|, changes the (1, 2) and (0, 2) entries."""
+    x = np.array([0.1, 0.4, 0.1])
+    y = np.array([0.2, 0.2, 0.6])
+    th = O.Theta(1.7, 0.25, 0.5, 0.0)
+    S = O.covariance(x, y, theta=th)
+    d01, d02, d12 = 0.3, 0.4, 0.5
+    want = np.array([[1.7, 1.7 * math.exp(-d01 / 0.25), 1.7 * math.exp(-d02 / 0.25)],
+                     [1.7 * math.exp(-d01 / 0.25), 1.7, 1.7 * math.exp(-d12 / 0.25)],
+                     [1.7 * math.exp(-d02 / 0.25), 1.7 * math.exp(-d12 / 0.25), 1.7]])
+    assert np.allclose(S, want, rtol=1e-14, atol=0.0)
+    # nu = 3/2 closed form on the same triangle
+    S32 = O.covariance(x, y, theta=O.Theta(1.0, 0.25, 1.5, 0.0))
+    assert S32[1, 2] == pytest.approx((1 + d12 / 0.25) * math.exp(-d12 / 0.25), rel=1e-14)
+    assert S32[0, 2] == pytest.approx((1 + d02 / 0.25) * math.exp(-d02 / 0.25), rel=1e-14)
+
+
+@pytest.mark.parametrize("angle,shift", [(0.7, (0.05, -0.02)), (math.pi / 2, (0.0, 0.0)), (2.2, (-0.1, 0.3))])
+def test_covariance_is_invariant_under_rigid_motion(angle, shift):
+    """Eq. 1 depends on the locations only through ||s_a - s_b||: rotating and
+    translating the point set leaves Sigma unchanged (to rounding).  A wrong
+    sign or weight of either coordinate difference breaks the invariance."""
+    x, y = inputs.uniform_points(40, seed=41)
+    c, s_ = math.cos(angle), math.sin(angle)
+    xr = c * x - s_ * y + shift[0]
+    yr = s_ * x + c * y + shift[1]
+    for th in (O.Theta(1.3, 0.2, 0.5, 0.01), O.Theta(0.8, 0.3, 1.0, 0.0), O.Theta(1.0, 0.1, 2.2, 0.0)):
+        a = O.covariance(x, y, theta=th)
+        b = O.covariance(xr, yr, theta=th)
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-15)
+    # and a reflection across the line y = x swaps the coordinates
+    th = O.Theta(1.0, 0.15, 1.5, 0.0)
+    assert np.allclose(O.covariance(x, y, theta=th), O.covariance(y, x, theta=th), rtol=1e-13, atol=0.0)
+
+
+def test_covariance_nugget_only_on_the_diagonal():
+    """Sigma(theta) - sigma2 R = tau2 I exactly, with R the unit-variance
+    correlation of the same points (sigma2 a power of two and tau2 exactly
+    representable, so every step is exact): the nugget sits on the diagonal
+    only and nowhere else (reading: Sigma + tau2 I)."""
+    x, y = inputs.jittered_grid(7, seed=43)
+    for nu in (0.5, 1.0, 1.5):
+        S = O.covariance(x, y, theta=O.Theta(2.0, 0.2, nu, 0.25))
+        R = O.covariance(x, y, theta=O.Theta(1.0, 0.2, nu, 0.0))
+        D = S - 2.0 * R
+        assert np.array_equal(D, 0.25 * np.eye(len(x))), nu
+    # a cross-covariance (two point sets) carries no nugget even where points coincide
+    C = O.covariance(x[:5], y[:5], x[:5], y[:5], theta=O.Theta(2.0, 0.2, 0.5, 0.25))
+    assert np.array_equal(np.diag(C), np.full(5, 2.0))
+
+
 def test_loglik_markov_1d_closed_form():
     n = 600
     x, y = inputs.line_points(n, seed=5, min_gap=0.05)

@@ -70,3 +70,27 @@ def test_noalloc_rejects_sizes_beyond_its_buffer(G):
     ld = torch.zeros(1, dtype=torch.float64, device="cuda")
     rc = G.lib.geo_logdet_trsv_noalloc(ctypes.byref(big), Z.data_ptr(), ld.data_ptr(), ld.data_ptr(), None)
     assert rc == G.GEO_ERR_TOO_LARGE
+
+
+def test_noalloc_after_failed_factor_is_nan_not_stale(G):
+    """A call on a store whose factorization failed must not return the partial
+    sums an earlier call left in the shared array: it returns NaN."""
+    X, Y, Z, n = _problem(G)
+    th = G.Theta(1.0, 0.1, 0.5)
+    good = G.TileStore(n, 200, 1, G.GEO_LP_FP32)
+    good.matern(X, Y, th)
+    good.potrf()
+    ld, q = _call(G, G.lib.geo_logdet_trsv_noalloc, good, Z)
+    assert math.isfinite(ld) and math.isfinite(q)
+    from oracle import geo_oracle as O
+    S = O.covariance(X.cpu().numpy(), Y.cpu().numpy(), theta=O.Theta(1.0, 0.1, 0.5))
+    S[700, 700] = -1.0                              # not positive definite at row 701
+    bad = G.TileStore(n, 200, 1, G.GEO_LP_FP32)
+    bad.load_dense(torch.as_tensor(np.ascontiguousarray(S.T), device="cuda"))
+    with pytest.raises(G.NotSPDError):
+        bad.potrf()
+    ld2, q2 = _call(G, G.lib.geo_logdet_trsv_noalloc, bad, Z)
+    assert math.isnan(ld2) and math.isnan(q2)
+    # the next good call is unaffected
+    ld3, q3 = _call(G, G.lib.geo_logdet_trsv_noalloc, good, Z)
+    assert ld3 == ld and q3 == q
