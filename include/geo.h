@@ -317,17 +317,33 @@ int geo_mle(geo_tiles* t, const double* d_x, const double* d_y, const double* d_
  * alone and in any batch.
  *
  * geo_batch_workspace: bytes of device workspace for these items (host only).
- * geo_batch_bind: write the merged task queues, the per-problem views and
- *   tensor maps into d_work (blocking).  The stores' flags are read here.
- * geo_loglik_batch: enqueue one evaluation (asynchronous, nprob + 2 kernel
- *   launches, no host synchronization, so it can be captured in a CUDA graph):
- *   generation of every problem from d_theta[b] (device memory: a replay of a
- *   captured graph may use new values), the batched factorization, and the
- *   batched log-det / solve / assembly into d_out[3b .. 3b+2] = (l, log|Sigma|,
- *   Z' Sigma^-1 Z); NaN for a problem that is not positive definite (its
- *   store's status says which row).  A launch-wide timeout marks every problem
- *   with GEO_ERR_TIMEOUT.  A trace enabled on the first item's store
- *   (geo_tiles_set_trace) records the tasks of all problems.
+ * geo_batch_bind: write the merged task queues (factorization and forward
+ *   solve), the per-problem views and tensor maps into d_work (blocking).  The
+ *   stores' flags are read here.
+ * geo_loglik_batch: enqueue one evaluation (asynchronous, nprob + 1 kernel
+ *   launches and three memsets, no host synchronization, so it can be captured
+ *   in a CUDA graph): generation of every problem from d_theta[b] (device
+ *   memory: a replay of a captured graph may use new values), then one
+ *   persistent launch that factors every problem and runs its forward solve,
+ *   log-determinant and assembly as soon as its own factor is ready, writing
+ *   d_out[3b .. 3b+2] = (l, log|Sigma|, Z' Sigma^-1 Z) (device FP64[3 nprob]);
+ *   NaN for a problem that is not positive definite (its store's status says
+ *   which row).  d_done_ns (optional, device int64[nprob + 1]): [0] = the
+ *   launch's start and [1 + b] = when problem b's result was written, in
+ *   %globaltimer nanoseconds (0 if it failed), for per-problem latency.  A
+ *   timeout ends the launch and marks every unfinished problem with
+ *   GEO_ERR_TIMEOUT.  A trace enabled on the first item's store
+ *   (geo_tiles_set_trace) records the tasks of all problems; the wait bound is
+ *   the first item's (geo_tiles_set_timeout_ns).
+ * geo_batch_set_ctas: run this workspace's factorization launches on `ctas`
+ *   CTAs (one per SM at most) instead of one per SM (ctas = 0, the default, a
+ *   cooperative launch of every SM).  With 1 <= ctas < SM count the launch is a
+ *   plain one: launches on other streams (another batch, kriging) run beside
+ *   it on the remaining SMs.  The schedule needs no co-residency (every wait
+ *   is on a task already taken by a running worker), so it completes with any
+ *   number of resident CTAs.
+ * geo_batch_release: forget the workspace's binding (host bookkeeping only;
+ *   the caller frees d_work).
  * All return 0, -k for a bad argument k, or GEO_ERR_CUDA. */
 typedef struct geo_batch_item {
     geo_tiles* t;
@@ -339,7 +355,9 @@ typedef struct geo_batch_item {
 int geo_batch_workspace(int nprob, const geo_batch_item* items, size_t* bytes);
 int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t bytes, void* stream);
 int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_theta, void* d_work,
-                     double* d_out, void* stream);
+                     double* d_out, long long* d_done_ns, void* stream);
+int geo_batch_set_ctas(const void* d_work, int ctas);
+int geo_batch_release(const void* d_work);
 
 /* A13, prediction (Section VIII-D; simple kriging reading): with t holding the
  * factor of Sigma(theta) over the observed locations (d_x, d_y, n = t->lay.n)

@@ -547,10 +547,11 @@ int geo_profile_read(int kind, double* h_ms, long long* h_launches) {
 namespace {
 struct BatchMeta {
     int nprob;
-    size_t off_probs, off_jobs, off_maps, off_tend, off_prio, off_bulk, off_tct, off_ctr, total;
-    long long n_prio, n_bulk, n_tct;
-    int per, pmax;
+    size_t off_probs, off_maps, off_tend, off_prio, off_bulk, off_tct, off_y, off_ctr, total;
+    long long n_prio, n_bulk, n_tct, n_y;
+    int per;
     size_t counter_bytes;
+    int ctas;   // CTAs of the factorization launch (0: one per SM, cooperative)
 };
 std::mutex g_batch_mu;
 std::vector<std::pair<const void*, BatchMeta>> g_batches;   // bound workspaces
@@ -563,9 +564,8 @@ int batch_meta(int nprob, const geo_batch_item* items, BatchMeta& m, std::vector
     m = BatchMeta();
     m.nprob = nprob;
     long long ptot = 0, ctot = 16;
-    m.n_prio = m.n_bulk = m.n_tct = 0;
+    m.n_prio = m.n_bulk = m.n_tct = m.n_y = 0;
     m.per = 1;
-    m.pmax = 0;
     for (int b = 0; b < nprob; ++b) {
         const geo_batch_item& it = items[b];
         if (!it.t || !it.t->d_meta || !it.d_x || !it.d_y || !it.d_z) return -2;
@@ -574,18 +574,16 @@ int batch_meta(int nprob, const geo_batch_item* items, BatchMeta& m, std::vector
         const SchedGeom& g = mo.geom[batch_variant(it.t)];
         if (geoms) geoms->push_back(g);
         ptot += g.p;
-        m.pmax = std::max(m.pmax, g.p);
         ctot += g.n_counters - 16;
         m.n_prio += g.n_prio;
         m.n_bulk += g.n_bulk;
         m.n_tct += g.n_tct;
+        m.n_y += g.n_y;
         m.per = std::max(m.per, g.items_tc);
     }
     size_t b = 0;
     m.off_probs = b;
     b = align256(b + sizeof(ProbDev) * (size_t)nprob);
-    m.off_jobs = b;
-    b = align256(b + sizeof(SolveJob) * (size_t)nprob);
     m.off_maps = b;
     b = align256(b + sizeof(CUtensorMap) * 3 * (size_t)nprob);
     m.off_tend = b;
@@ -596,6 +594,8 @@ int batch_meta(int nprob, const geo_batch_item* items, BatchMeta& m, std::vector
     b = align256(b + sizeof(G2Task) * (size_t)std::max(m.n_bulk, 1LL));
     m.off_tct = b;
     b = align256(b + sizeof(int4) * (size_t)std::max(m.n_tct, 1LL));
+    m.off_y = b;
+    b = align256(b + sizeof(G2Task) * (size_t)std::max(m.n_y, 1LL));
     m.off_ctr = b;
     m.counter_bytes = sizeof(int) * (size_t)ctot;
     b = align256(b + m.counter_bytes);
@@ -627,11 +627,10 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
     BatchPlan plan;
     sched_merge(geoms, bands, plan);
     if ((long long)plan.prio.size() != m.n_prio || (long long)plan.bulk.size() != m.n_bulk ||
-        (long long)plan.tct.size() != m.n_tct || plan.per != m.per)
+        (long long)plan.tct.size() != m.n_tct || (long long)plan.yq.size() != m.n_y || plan.per != m.per)
         return GEO_ERR_UNSUPPORTED;   // the merge must account for every task
     char* base = (char*)d_work;
     std::vector<ProbDev> probs((size_t)nprob);
-    std::vector<SolveJob> jobs((size_t)nprob);
     std::vector<CUtensorMap> maps(3 * (size_t)nprob);
     std::vector<int> tend;
     int* ctr = (int*)(base + m.off_ctr) + 16;
@@ -647,14 +646,11 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
         tend.insert(tend.end(), plan.trsm_end[(size_t)b].begin(), plan.trsm_end[(size_t)b].end());
         P.tmap = (const CUtensorMap*)(base + m.off_maps) + 3 * (size_t)b;
         memcpy(&maps[3 * (size_t)b], t->tmap, 3 * sizeof(CUtensorMap));
-        jobs[(size_t)b].L = P.L;
-        jobs[(size_t)b].z = items[b].d_z;
+        P.z = items[b].d_z;   // the forward solve runs inside the launch
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(base + m.off_probs, probs.data(), sizeof(ProbDev) * probs.size(),
                                     cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemcpyAsync(base + m.off_jobs, jobs.data(), sizeof(SolveJob) * jobs.size(),
-                                cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(base + m.off_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
                                 cudaMemcpyHostToDevice, s);
     if (!e && !tend.empty())
@@ -668,8 +664,12 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
     if (!e && !plan.tct.empty())
         e = cudaMemcpyAsync(base + m.off_tct, plan.tct.data(), sizeof(int4) * plan.tct.size(),
                             cudaMemcpyHostToDevice, s);
+    if (!e && !plan.yq.empty())
+        e = cudaMemcpyAsync(base + m.off_y, plan.yq.data(), sizeof(G2Task) * plan.yq.size(),
+                            cudaMemcpyHostToDevice, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return GEO_ERR_CUDA;
+    m.ctas = 0;
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto& kv : g_batches)
         if (kv.first == d_work) {
@@ -680,8 +680,31 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
     return GEO_OK;
 }
 
+int geo_batch_set_ctas(const void* d_work, int ctas) {
+    if (!d_work) return -1;
+    if (ctas < 0) return -2;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto& kv : g_batches)
+        if (kv.first == d_work) {
+            kv.second.ctas = ctas;
+            return GEO_OK;
+        }
+    return -1;   // not bound by geo_batch_bind
+}
+
+int geo_batch_release(const void* d_work) {
+    if (!d_work) return -1;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t q = 0; q < g_batches.size(); ++q)
+        if (g_batches[q].first == d_work) {
+            g_batches.erase(g_batches.begin() + (long)q);
+            return GEO_OK;
+        }
+    return -1;
+}
+
 int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_theta, void* d_work,
-                     double* d_out, void* stream) {
+                     double* d_out, long long* d_done_ns, void* stream) {
     if (nprob < 1) return -1;
     if (!items) return -2;
     if (!d_theta) return -3;
@@ -709,12 +732,9 @@ int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_
     }
     if (run_potrf_dag_batch((const ProbDev*)(base + m.off_probs), nprob, (const G2Task*)(base + m.off_prio),
                             m.n_prio, (const G2Task*)(base + m.off_bulk), m.n_bulk,
-                            (const int4*)(base + m.off_tct), m.n_tct, m.per, (int*)(base + m.off_ctr),
-                            m.counter_bytes, items[0].t->trace, items[0].t->trace_cap, small_dp,
-                            items[0].t->timeout_ns, s))
-        return GEO_ERR_CUDA;
-    if (launch_trsv_batch((const SolveJob*)(base + m.off_jobs), nprob, m.pmax, d_out,
-                          (unsigned*)(base + m.off_ctr) + 8, s))
+                            (const int4*)(base + m.off_tct), m.n_tct, m.per, (const G2Task*)(base + m.off_y),
+                            m.n_y, d_out, d_done_ns, (int*)(base + m.off_ctr), m.counter_bytes,
+                            items[0].t->trace, items[0].t->trace_cap, small_dp, items[0].t->timeout_ns, m.ctas, s))
         return GEO_ERR_CUDA;
     return GEO_OK;
 }

@@ -225,6 +225,9 @@ struct DagArgs {
     geo_trace_rec* trace;
     long long trace_cap;
     long long wait_ns;       // bound of every wait of the launch (geo_tiles_set_timeout_ns)
+    int nprob;               // batched launch: number of problems
+    double* out;             // batched launch: problem b's (l, log|Sigma|, Z' Sigma^-1 Z) at out[3b]
+    long long* done_ns;      // optional: [0] launch start, [1 + pid] when that problem's result was written
 };
 
 __device__ __forceinline__ const ProbDev& prob_of(const DagArgs& A, int pid) {
@@ -1008,7 +1011,9 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
             for (unsigned spin = 0; kind < 0; ++spin) {
                 if (aborted(A) || (!A.probs && failed(A.one.L))) break;
                 const int yh = A.n_y > 0 ? ld_volatile(y_head) : 0;
-                if (yh < A.n_y && y_ready(A.one, A.yq[yh]) && atomicCAS(y_head, yh, yh + 1) == yh) {
+                // (a solve task of a failed problem is taken at once and dropped below)
+                if (yh < A.n_y && (failed(prob_of(A, A.yq[yh].pid).L) || y_ready(prob_of(A, A.yq[yh].pid), A.yq[yh])) &&
+                    atomicCAS(y_head, yh, yh + 1) == yh) {
                     idx = yh;
                     kind = 2;
                     break;
@@ -1181,7 +1186,18 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                     }
                 g2_sync();
                 ysolve_diag_tile(L, k, yv, L.scal, g, G2_THREADS, S.yd, G2Sync());
-                if (k == L.p - 1 && g == 0) ysolve_finish(L, L.scal, P.res, P.res + 1, P.res + 2);
+                if (k == L.p - 1 && g == 0) {
+                    if (A.probs) {   // batched: (l, log|Sigma|, Z' Sigma^-1 Z) of problem pid
+                        double* o = A.out + 3 * (size_t)t.pid;
+                        ysolve_finish(L, L.scal, o + 1, o + 2, o);
+                    } else {
+                        ysolve_finish(L, L.scal, P.res, P.res + 1, P.res + 2);
+                    }
+                    if (A.done_ns) {
+                        __threadfence();
+                        A.done_ns[1 + t.pid] = gtimer();
+                    }
+                }
                 done = P.ydone + k;
                 break;
             }
@@ -1706,6 +1722,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 1)
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* ring = abort_flag + 1;
     const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0 && blockIdx.x == 0 && A.done_ns) A.done_ns[0] = gtimer();
     if (threadIdx.x == 0) {
         *abort_flag = 0;
         const uint32_t b0 = smem_u32(bars);
@@ -1741,6 +1758,13 @@ __global__ void __launch_bounds__(DAG_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
                      : "memory");
     }
+    // an aborted batched launch: every problem whose last solve task did not
+    // run is marked as timed out (its result stays NaN)
+    if (A.probs && blockIdx.x == 0 && threadIdx.x == 0 && aborted(A))
+        for (int b = 0; b < A.nprob; ++b) {
+            const ProbDev& P = A.probs[b];
+            if (ld_acquire_s32(P.ydone + P.L.p - 1) < 1) set_timeout(P.L, 9);
+        }
 }
 
 template <bool kSmallDP>
@@ -1826,11 +1850,11 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
     out.per = 1;
     std::vector<std::vector<G2Task>> prio((size_t)nprob), bulk((size_t)nprob);
     std::vector<std::vector<int>> tend((size_t)nprob);
-    std::vector<G2Task> yq_unused;
+    std::vector<std::vector<G2Task>> yq((size_t)nprob);
     std::vector<std::vector<int4>> tct((size_t)nprob);
     int pmax = 0;
     for (int b = 0; b < nprob; ++b) {
-        sched_build(g[(size_t)b], band[(size_t)b], prio[(size_t)b], bulk[(size_t)b], tend[(size_t)b], yq_unused,
+        sched_build(g[(size_t)b], band[(size_t)b], prio[(size_t)b], bulk[(size_t)b], tend[(size_t)b], yq[(size_t)b],
                     tct[(size_t)b]);
         out.trsm_end[(size_t)b].assign((size_t)g[(size_t)b].p, 0);
         out.per = std::max(out.per, g[(size_t)b].items_tc);
@@ -1838,9 +1862,11 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
     }
     // every queue of a problem is ordered by step; step k of all problems
     // precedes step k+1 of any (staggering the problems' steps against each
-    // other was measured to make no difference).  A batched launch solves after
-    // the factorization (its own kernel), so the forward-solve queue is unused.
-    std::vector<size_t> ip((size_t)nprob, 0), ib((size_t)nprob, 0), it((size_t)nprob, 0);
+    // other was measured to make no difference).  The forward-solve queues are
+    // merged the same way: each problem's solve runs inside the launch, and
+    // its result is written as soon as its own last block row is solved.
+    out.yq.clear();
+    std::vector<size_t> ip((size_t)nprob, 0), ib((size_t)nprob, 0), it((size_t)nprob, 0), iy((size_t)nprob, 0);
     for (int k = 0; k < pmax; ++k) {
         for (int b = 0; b < nprob; ++b) {
             const std::vector<G2Task>& q = prio[(size_t)b];
@@ -1870,17 +1896,30 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
                 out.tct.push_back(v);
             }
         }
+        for (int b = 0; b < nprob; ++b) {
+            const std::vector<G2Task>& q = yq[(size_t)b];
+            while (iy[(size_t)b] < q.size() && q[iy[(size_t)b]].k == k) {
+                G2Task tk = q[iy[(size_t)b]++];
+                tk.pid = b;
+                out.yq.push_back(tk);
+            }
+        }
     }
 }
 
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
                                 const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
+                                const G2Task* yq, long long n_y, double* out, long long* done_ns,
                                 int* counters, size_t counter_bytes, void* trace, long long trace_cap,
-                                bool small_dp, long long wait_ns, cudaStream_t s) {
+                                bool small_dp, long long wait_ns, int ctas, cudaStream_t s) {
     int nsm = 0;
     cudaError_t e = small_dp ? dag_prepare<true>(nsm) : dag_prepare<false>(nsm);
     if (e) return e;
     if ((e = cudaMemsetAsync(counters, 0, counter_bytes, s))) return e;
+    // results start as NaN (every byte 0xFF): a problem whose factorization
+    // fails never reaches its last solve task and keeps them
+    if ((e = cudaMemsetAsync(out, 0xFF, 3 * sizeof(double) * (size_t)nprob, s))) return e;
+    if (done_ns && (e = cudaMemsetAsync(done_ns, 0, sizeof(long long) * ((size_t)nprob + 1), s))) return e;
     DagArgs A;
     memset(&A, 0, sizeof(A));
     A.probs = d_probs;
@@ -1896,13 +1935,26 @@ cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task*
     A.trace = trace ? (geo_trace_rec*)((char*)trace + 64) : nullptr;
     A.trace_cap = trace_cap;
     A.wait_ns = wait_ns > 0 ? wait_ns : GEO_DEFAULT_TIMEOUT_NS;
-    (void)nprob;
+    A.yq = yq;
+    A.n_y = n_y;
+    A.nprob = nprob;
+    A.out = out;
+    A.done_ns = done_ns;
     CUtensorMap maps[3];
     memset(maps, 0, sizeof(maps));   // unused: each problem's maps are in its view
     void* args[] = {&A, &maps[0], &maps[1], &maps[2]};
+    const void* fn = small_dp ? (const void*)dag_kernel<true> : (const void*)dag_kernel<false>;
     prof_begin(4, s);
-    e = cudaLaunchCooperativeKernel(small_dp ? (const void*)dag_kernel<true> : (const void*)dag_kernel<false>,
-                                    dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
+    if (ctas > 0 && ctas < nsm) {
+        // a share of the SMs: a plain launch, so that launches on other streams
+        // run beside it.  The schedule needs no co-residency: a worker waits
+        // only on tasks already taken by running workers (the queues are in
+        // topological order and the solve queue is taken only when ready), so
+        // any number of resident CTAs >= 1 completes it.
+        e = cudaLaunchKernel(fn, dim3(ctas), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
+    } else {
+        e = cudaLaunchCooperativeKernel(fn, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
+    }
     prof_end(4, s);
     count_launch();
     return e;

@@ -74,7 +74,7 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
 // merges the problems' queues step by step (each problem keeps its own
 // topological order, so the merge is one too).
 struct BatchPlan {
-    std::vector<G2Task> prio, bulk;
+    std::vector<G2Task> prio, bulk, yq;   // yq: the problems' forward-solve queues, merged by step
     std::vector<int4> tct;            // (i, j, k, problem)
     std::vector<std::vector<int>> trsm_end;
     int per = 1;                      // tensor items per target (largest over the problems)
@@ -83,12 +83,18 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
 // point P's counters into a block of P.g.n_counters - 16 ints
 void bind_counters(ProbDev& P, int* base);
 // probs: nprob device views in global memory (their counters inside `counters`,
-// zeroed by this call), queues in device memory as laid out by the caller.
+// zeroed by this call), queues in device memory as laid out by the caller; the
+// forward solve of every problem runs inside the launch (yq) and writes its
+// (l, log|Sigma|, Z' Sigma^-1 Z) to out[3b] (NaN if it fails) and, with
+// done_ns, [0] the launch start and [1 + b] its completion (%globaltimer).
 // small_dp: some problem has FP64 panel tiles (band > 1) of fewer than
-// DP_SPLIT_MIN_NB rows (dag_small_dp), solved one row per thread
+// DP_SPLIT_MIN_NB rows (dag_small_dp), solved one row per thread.
+// ctas: 0 = one CTA per SM (cooperative launch), else a plain launch of that
+// many CTAs (a share of the SMs; launches on other streams run beside it).
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,
                                 const G2Task* bulk, long long n_bulk, const int4* tct, long long n_tct, int per,
+                                const G2Task* yq, long long n_y, double* out, long long* done_ns,
                                 int* counters, size_t counter_bytes, void* trace, long long trace_cap,
-                                bool small_dp, long long wait_ns, cudaStream_t s);
+                                bool small_dp, long long wait_ns, int ctas, cudaStream_t s);
 
 }  // namespace geo

@@ -87,12 +87,6 @@ __host__ __device__ inline double assemble_loglik(int n, double logdet, double q
 #endif
 }
 
-// One problem of a batched solve: its layout (the factored store) and Z.
-struct SolveJob {
-    Layout L;
-    const double* z;
-};
-
 Layout make_layout(const geo_tiles* t);
 
 // Instrumentation (api.cu): a launch counter and optional event timing of
@@ -113,9 +107,6 @@ cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, do
                             cudaStream_t s, double* loglik = nullptr);
 cudaError_t run_logdet_trsv_noalloc(const Layout& L, const double* z, double* logdet, double* quad,
                                     cudaStream_t s);
-// bar: 4 unsigned of device scratch for the launch's grid barrier
-cudaError_t launch_trsv_batch(const SolveJob* d_jobs, int nprob, int pmax, double* out, unsigned* bar,
-                              cudaStream_t s);
 cudaError_t run_krige(const Layout& L, const double* x, const double* y, const double* z, const MaternP& mp,
                       const double* xn, const double* yn, int m, double* zhat, double* work, cudaStream_t s);
 

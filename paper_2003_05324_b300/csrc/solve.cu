@@ -85,122 +85,6 @@ static cudaError_t forward_solve(const Layout& L, double* yv, double* part, cuda
     return cudaGetLastError();
 }
 
-// Batched A10-A12 as one cooperative launch over all problems.  Step i: every
-// problem with more than i tiles solves its diagonal tile i (one CTA per
-// problem), grid barrier, then the updates y_l -= L(l,i) y_i of all (problem,
-// block row l) pairs are spread over every CTA, grid barrier.  Per element the
-// arithmetic and its order are those of the per-tile kernels above, so a
-// problem's result is the same alone and in a batch.  Finally Eq. 2 is
-// assembled per problem: out = (l, log|Sigma|, Z' Sigma^-1 Z), NaN for a
-// problem whose factorization failed.  The grid barrier is a bounded counter
-// barrier on bar[0..1] (zeroed by the caller); on a timeout every problem's
-// status records GEO_ERR_TIMEOUT.
-__device__ bool sv_grid_barrier(unsigned* bar, volatile int* abort) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned* cnt = bar;
-        unsigned* gen = bar + 1;
-        unsigned g;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
-        __threadfence();
-        if (atomicAdd(cnt, 1u) == gridDim.x - 1) {
-            atomicExch(cnt, 0u);
-            __threadfence();
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(gen), "r"(g + 1) : "memory");
-        } else {
-            const long long deadline = gtimer() + 2000000000LL;
-            unsigned it = 0, cur = g;
-            for (;;) {
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
-                if (cur != g || *abort) break;
-                if ((++it & 1023u) == 0 && gtimer() > deadline) {
-                    *abort = 1;
-                    break;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    return *abort == 0;
-}
-
-__global__ void __launch_bounds__(SV_THREADS) trsv_batch_kernel(const SolveJob* __restrict__ jobs, int nprob,
-                                                                int pmax, double* __restrict__ out_all,
-                                                                unsigned* bar) {
-    volatile int* abort = (volatile int*)(bar + 2);
-    const int tid = threadIdx.x;
-    // y = Z (zero beyond n)
-    for (int b = blockIdx.x; b < nprob; b += gridDim.x) {
-        const Layout& L = jobs[b].L;
-        if (failed(L)) continue;
-        double* yv = L.scal + 2 * L.p + 8;
-        for (int g = tid; g < L.p * L.nb; g += SV_THREADS) yv[g] = g < L.n ? jobs[b].z[g] : 0.0;
-    }
-    bool ok = sv_grid_barrier(bar, abort);
-    for (int i = 0; i < pmax && ok; ++i) {
-        for (int b = blockIdx.x; b < nprob; b += gridDim.x) {
-            const Layout& L = jobs[b].L;
-            if (i >= L.p || failed(L)) continue;
-            trsv_diag_tile(L, i, L.scal + 2 * L.p + 8, L.scal);
-            __syncthreads();
-        }
-        ok = sv_grid_barrier(bar, abort);
-        if (!ok) break;
-        // work units (problem b, block row l > i), numbered problem by problem
-        int u0 = 0;
-        for (int b = 0; b < nprob; ++b) {
-            const Layout& L = jobs[b].L;
-            const int nl = (i + 1 < L.p && !failed(L)) ? L.p - i - 1 : 0;
-            for (int u = u0 + (int)((blockIdx.x + gridDim.x - (u0 % gridDim.x)) % gridDim.x); u < u0 + nl;
-                 u += gridDim.x) {
-                const int l = i + 1 + (u - u0);
-                double* yv = L.scal + 2 * L.p + 8;
-                const double* yi = yv + (size_t)i * L.nb;
-                for (int r = tid; r < L.nb; r += SV_THREADS)
-                    yv[(size_t)l * L.nb + r] -= yrow_update(L, l, i, r, yi);
-            }
-            u0 += nl;
-        }
-        ok = sv_grid_barrier(bar, abort);
-    }
-    for (int b = blockIdx.x; b < nprob; b += gridDim.x) {
-        const Layout& L = jobs[b].L;
-        double* out = out_all + 3 * (size_t)b;
-        if (!ok && tid == 0) set_timeout(L, 50);
-        if (!ok || failed(L)) {
-            if (tid < 3) out[tid] = nan("");
-            continue;
-        }
-        if (tid == 0) {
-            double s0 = 0.0, s1 = 0.0;
-            ysolve_finish(L, L.scal, &s0, &s1);
-            out[0] = assemble_loglik(L.n, s0, s1);
-            out[1] = s0;
-            out[2] = s1;
-        }
-    }
-}
-
-cudaError_t launch_trsv_batch(const SolveJob* d_jobs, int nprob, int pmax, double* out, unsigned* bar,
-                              cudaStream_t s) {
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsv_batch_kernel, SV_THREADS, 0);
-    if (e) return e;
-    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-    const int grid = std::min(nsm * std::min(per_sm, 2), std::max(nprob, 1) * 8);
-    if ((e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s))) return e;
-    void* args[] = {(void*)&d_jobs, &nprob, &pmax, &out, &bar};
-    e = cudaLaunchCooperativeKernel((const void*)trsv_batch_kernel, dim3(grid), dim3(SV_THREADS), args, 0, s);
-    count_launch();
-    return e;
-}
-
 cudaError_t run_logdet_trsv(const Layout& L, const double* z, double* logdet, double* quad, double* y,
                             cudaStream_t s, double* loglik) {
     double* yv = y ? y : L.scal + 2 * L.p + 8;

@@ -109,7 +109,9 @@ def _load():
         "geo_krige": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, P, P, I, P, P, P],
         "geo_batch_workspace": [I, ctypes.POINTER(geo_batch_item), ctypes.POINTER(ctypes.c_size_t)],
         "geo_batch_bind": [I, ctypes.POINTER(geo_batch_item), P, ctypes.c_size_t, P],
-        "geo_loglik_batch": [I, ctypes.POINTER(geo_batch_item), P, P, P, P],
+        "geo_loglik_batch": [I, ctypes.POINTER(geo_batch_item), P, P, P, P, P],
+        "geo_batch_set_ctas": [P, I],
+        "geo_batch_release": [P],
         "geo_mle_default_opts": [ctypes.POINTER(geo_mle_opts)],
         "geo_mle": [ctypes.POINTER(geo_tiles), P, P, P, geo_theta, ctypes.POINTER(geo_mle_opts),
                     ctypes.POINTER(geo_mle_result), P],
@@ -390,10 +392,12 @@ class Batch:
     `store` (TileStore of split-BF16 mode) to evaluate in.  The stores, the
     workspace and the per-problem theta buffer are allocated once; each
     evaluation only enqueues work, so `capture()` can record it in a CUDA graph
-    and `replay(thetas)` re-runs it with new parameters.
+    and `replay(thetas)` re-runs it with new parameters.  ctas: run the
+    factorization launch on that many SMs (0: all, cooperative), leaving the
+    others to launches on other streams.
     """
 
-    def __init__(self, problems, nb: int = 128, band: int = 1, device="cuda"):
+    def __init__(self, problems, nb: int = 128, band: int = 1, device="cuda", ctas: int = 0):
         import torch
         self.device = torch.device(device)
         self.stores, self._keep = [], []
@@ -416,9 +420,18 @@ class Batch:
         _check(lib.geo_batch_workspace(n, self.items, ctypes.byref(nbytes)), "geo_batch_workspace")
         self._work = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=self.device)
         _check(lib.geo_batch_bind(n, self.items, _ptr(self._work), int(nbytes.value), _stream()), "geo_batch_bind")
+        if ctas:
+            _check(lib.geo_batch_set_ctas(_ptr(self._work), int(ctas)), "geo_batch_set_ctas")
         self.theta = torch.zeros((n, 4), dtype=torch.float64, device=self.device)
         self.out = torch.zeros((n, 3), dtype=torch.float64, device=self.device)
+        self.done_ns = torch.zeros(n + 1, dtype=torch.int64, device=self.device)
         self.graph = None
+
+    def __del__(self):
+        try:
+            lib.geo_batch_release(_ptr(self._work))
+        except Exception:
+            pass
 
     def nbytes(self) -> int:
         """Device bytes of the batch workspace (the stores not included)."""
@@ -431,10 +444,19 @@ class Batch:
 
     def loglik_async(self, stream=None):
         """Enqueue one evaluation with the parameters in self.theta; results land
-        in self.out[b] = (l, log|Sigma|, Z' Sigma^-1 Z), NaN where not SPD."""
+        in self.out[b] = (l, log|Sigma|, Z' Sigma^-1 Z), NaN where not SPD, and
+        self.done_ns = (launch start, completion of each problem) in ns."""
         _check(lib.geo_loglik_batch(self.nprob, self.items, _ptr(self.theta), _ptr(self._work), _ptr(self.out),
-                                    _stream(stream)), "geo_loglik_batch")
+                                    _ptr(self.done_ns), _stream(stream)), "geo_loglik_batch")
         return self.out
+
+    def completion_ms(self):
+        """Per-problem completion time of the last evaluation, ms after the
+        factorization launch started (NaN for a problem that failed)."""
+        t = self.done_ns.cpu().numpy()
+        out = (t[1:] - t[0]).astype(np.float64) / 1e6
+        out[t[1:] == 0] = np.nan
+        return out
 
     def loglik(self, thetas):
         import torch

@@ -105,7 +105,9 @@ def test_entry_points_reject_null_arguments_without_device_work():
     items[0].t = ctypes.pointer(t)                 # unbound store: rejected before any device work
     assert L.geo_batch_workspace(1, items, ctypes.byref(nbytes)) == -2
     assert L.geo_batch_bind(1, items, None, 0, None) == -2
-    assert L.geo_loglik_batch(1, items, None, None, None, None) == -3
+    assert L.geo_loglik_batch(1, items, None, None, None, None, None) == -3
+    assert L.geo_batch_set_ctas(None, 4) == -1
+    assert L.geo_batch_release(None) == -1
     assert L.geo_mle_default_opts(None) == -1
 
 

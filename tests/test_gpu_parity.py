@@ -340,8 +340,10 @@ def test_fused_solve_equals_standalone_solve(G, n, nb, band, flags):
     torch.cuda.synchronize()
     assert ld == float(lds) and q == float(qs)
     assert lda == ld and qa == q and la == l
-    # Eq. 2 assembled on the device: the host's expression gives the same bits
-    assert la == -0.5 * n * math.log(2.0 * math.pi) - 0.5 * ld - 0.5 * q
+    # Eq. 2 assembled on the device: the host's expression with the correctly
+    # rounded log(2 pi) (one ulp above math.log(2 pi)) gives the same bits
+    log2pi = float("1.8378770664093454835606594728112")
+    assert la == -0.5 * n * log2pi - 0.5 * ld - 0.5 * q
     want = O.loglik_dense(x, y, z, oracle_theta(th))["loglik"]
     assert abs(l - want) <= 1e-6 * abs(want)
 

@@ -3,9 +3,14 @@
 * Every result served in a mix of concurrent requests equals the same request
   evaluated alone, bit for bit (log-likelihood: the single-problem path;
   kriging: a direct prediction from the resident factor).
-* HBM-budget admission: with room for one store at a time the requests are
-  served over several launches with the same results; a request whose store
-  alone exceeds the budget is rejected.
+* Continuous batching: a short request that arrives while a long one is on
+  the device is admitted into the other lane at once, runs beside it and
+  finishes first, and both results equal their values alone.
+* HBM-budget admission: the resident kriging factors count against the
+  budget; with room for one more store at a time the requests are served over
+  several launches with the same results; a request whose store can never fit
+  beside the resident factors is rejected, and with room for the resident
+  factors only every likelihood request is rejected while kriging is served.
 * Kriging from the mixed-precision resident factor: MSPE against the held-out
   truth within 1% of the FP64 path's (the stated gate), and the FP64 path's
   predictions match the oracle's to 1e-8.
@@ -56,9 +61,13 @@ def dss():
             dataset(1300, 3, (0.8, 0.08, 0.5)), dataset(2000, 4, (1.0, 0.1, 1.0), nb=256)]
 
 
-def server(geo, serve, dss, budget):
+def server(geo, serve, dss, budget, lanes=2):
     return serve.Server([dict(x=d["x"], y=d["y"], z=d["z"], theta=geo.Theta(*d["th"]), nb=d["nb"]) for d in dss],
-                        hbm_budget_bytes=budget)
+                        hbm_budget_bytes=budget, lanes=lanes)
+
+
+def resident(serve, dss):
+    return sum(serve.store_bytes(len(d["z"]), d["nb"], 1) for d in dss)
 
 
 def alone(geo, S, r):
@@ -71,11 +80,11 @@ def alone(geo, S, r):
     return d["krig"].krige(d["x"], d["y"], d["z"], d["theta"], xn, yn).cpu().numpy()
 
 
-@pytest.mark.parametrize("budget_stores", [100, 1])
-def test_served_results_equal_alone(G, dss, budget_stores):
+@pytest.mark.parametrize("budget_stores,lanes", [(100, 2), (1, 2), (100, 1)])
+def test_served_results_equal_alone(G, dss, budget_stores, lanes):
     geo, serve = G
     big = max(serve.store_bytes(len(d["z"]), d["nb"], 1) for d in dss)
-    S = server(geo, serve, dss, budget_stores * big)
+    S = server(geo, serve, dss, resident(serve, dss) + budget_stores * big, lanes)
     reqs = make_requests(geo, serve, dss, np.random.default_rng(5))
     results, stats = S.run(reqs)
     assert stats["completed"] == len(reqs) and stats["rejected"] == 0 and stats["queued"] == 0
@@ -94,7 +103,7 @@ def test_served_results_equal_alone(G, dss, budget_stores):
 def test_request_larger_than_budget_is_rejected(G, dss):
     geo, serve = G
     small = min(serve.store_bytes(len(d["z"]), d["nb"], 1) for d in dss)
-    S = server(geo, serve, dss, small)     # only the smallest dataset's store fits
+    S = server(geo, serve, dss, resident(serve, dss) + small)   # beside the resident factors: the smallest store
     th = geo.Theta(*dss[3]["th"])
     results, stats = S.run([serve.Request("loglik", 3, theta=th, id=0),
                             serve.Request("loglik", 0, theta=geo.Theta(*dss[0]["th"]), id=1)])
@@ -119,3 +128,48 @@ def test_kriging_mspe_mixed_precision_within_1pct(G, dss):
         m_mp = np.mean((pred[1] - d["zt"]) ** 2)
         m_dp = np.mean((pred[100] - d["zt"]) ** 2)
         assert abs(m_mp - m_dp) <= 0.01 * m_dp, (m_mp, m_dp)
+
+
+def test_budget_for_the_resident_factors_only(G, dss):
+    """The resident kriging factors count against the HBM budget: with room
+    for them and nothing else, likelihood requests are rejected (their stores
+    can never fit) while kriging requests on the resident factors are served."""
+    geo, serve = G
+    S = server(geo, serve, dss, resident(serve, dss))
+    assert S.allocated == S.resident_bytes
+    reqs = make_requests(geo, serve, dss, np.random.default_rng(6))
+    results, stats = S.run(reqs)
+    nlik = sum(1 for r in reqs if r.kind == "loglik")
+    assert stats["rejected"] == nlik and stats["loglik_completed"] == 0
+    assert stats["krige_completed"] == len(reqs) - nlik
+    assert S.allocated == S.resident_bytes       # nothing left allocated after the run
+
+
+def test_request_arriving_mid_flight_finishes_first(G):
+    """Continuous batching: a long likelihood request (n = 24,000) is on the
+    device on one lane; a short one (n = 800) arrives 10 ms later, is admitted
+    into the other lane while the long one runs, and completes first.  Both
+    results equal the single-problem path bit for bit."""
+    geo, serve = G
+    dsets = []
+    for n, nb, seed in ((24000, 500, 61), (800, 128, 62)):
+        x, y = inputs.uniform_points(n, seed=seed)
+        perm = O.morton_order(x, y)
+        dsets.append(dict(x=x[perm], y=y[perm], z=inputs.white_noise(n, seed=seed + 1), nb=nb,
+                          theta=geo.Theta(1.0, 0.1, 0.5, 1e-4), krige=False))
+    S = serve.Server(dsets, hbm_budget_bytes=64 << 30, lanes=2)
+    th = [geo.Theta(1.1, 0.09, 0.5, 1e-4), geo.Theta(0.9, 0.12, 0.5, 1e-4)]
+    S.run([serve.Request("loglik", 0, theta=th[0], id=0), serve.Request("loglik", 1, theta=th[1], id=1)])  # pool stores
+    results, stats = S.run([serve.Request("loglik", 0, theta=th[0], t_arrival=0.0, id=0),
+                            serve.Request("loglik", 1, theta=th[1], t_arrival=0.010, id=1)])
+    byid = {r.id: r for r in results}
+    long_, short = byid[0], byid[1]
+    assert short.lane != long_.lane
+    assert long_.t_admit < short.t_admit < long_.t_done          # admitted while the long one was on the device
+    assert short.t_done < long_.t_done                           # and finished first
+    assert stats["launches_overlapping"] >= 1
+    for r, q in ((long_, 0), (short, 1)):
+        d = S.ds[q]
+        ts = geo.TileStore(d["n"], d["nb"], 1, geo.GEO_LP_SPLIT_BF16)
+        want = ts.loglik(d["x"], d["y"], d["z"], th[q])
+        assert np.array_equal(np.asarray(r.value), np.asarray(want)), (q, r.value, want)
