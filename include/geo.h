@@ -91,6 +91,7 @@ typedef struct geo_tiles {
     void* trace;                  /* optional device trace buffer (geo_tiles_set_trace) */
     long long trace_cap;          /* its capacity in records */
     long long timeout_ns;         /* bound of every device-side wait (geo_tiles_set_timeout_ns); 0 = default */
+    int far_products;             /* far tier (geo_tiles_set_far): 0 = off, else 1 or 3 products */
 } geo_tiles;
 
 /* One record of the device-side task trace (tensor-core mode scheduler):
@@ -142,9 +143,10 @@ typedef struct geo_trace_rec {
 #define GEO_FLAG_DST 8
 /* Test hook (persistent scheduler only): the tensor-core update items of the
  * first step wait for one more solved row chunk of their panel tile than the
- * tile has, so that dependency can never be met.  The bounded wait then ends
- * the launch: the status words record GEO_ERR_TIMEOUT with the wait's
- * location code (31, read back by geo_status), every worker leaves, the
+ * tile has, so that dependency can never be met; that wait's bound is half the
+ * store's, so it gives up before the waits downstream of it.  The bounded wait
+ * then ends the launch: the status words record GEO_ERR_TIMEOUT with the
+ * wait's location code (31, read back by geo_status), every worker leaves, the
  * tensor-core group returns its tensor memory, and the store can be evaluated
  * again once the flag is cleared.  Used with a short geo_tiles_set_timeout_ns
  * bound to exercise the failure path without faulting or hanging the device. */
@@ -186,6 +188,27 @@ int geo_tiles_set_timeout_ns(geo_tiles* t, long long ns);
  * then `capacity` geo_trace_rec).  The caller zeroes the counter; records past
  * the capacity are dropped (the counter keeps counting).  NULL disables. */
 int geo_tiles_set_trace(geo_tiles* t, void* d_trace, long long capacity);
+
+/* Three-precision extension (the paper's future work, Section IX: a third,
+ * lower precision for the tiles farthest from the diagonal).  Off-band tiles
+ * marked far keep their FP32 storage and FP32 panel solve, but their
+ * trailing updates use fewer fixed-point slice products on the tensor cores:
+ * each panel row, scaled by its power of two, is cut into an 8-bit slice a0
+ * and a 12-bit slice a1 (the same planes the FP32-accurate tier reads), and
+ *   products = 3: a0 b0 + 2^-12 (a0 b1 + a1 b0)   (terms of weight >= 2^-12;
+ *                 relative error ~2^-16 per product term, half the MMAs),
+ *   products = 1: a0 b0                           (8-bit operands, 1/6 of the MMAs).
+ * A tile (i, j) is far when i - j >= far_band (far_band >= 1; 0: no band rule),
+ * or, with far_dist > 0, when the smallest distance between the bounding boxes
+ * of the two tiles' locations (d_x, d_y: device FP64[n], the locations the
+ * store is evaluated on, Morton-ordered) is at least far_dist; in-band (FP64)
+ * tiles are never far.  The tile map is computed once here (on `stream`,
+ * asynchronously) and kept in the store's meta buffer until the next call;
+ * far_band = 0 and far_dist <= 0 turn the tier off.  Tensor-core mode with the
+ * persistent scheduler only (the GEO_LP_FP32 mode and GEO_FLAG_STEPWISE return
+ * GEO_ERR_UNSUPPORTED).  Returns 0, -k for a bad argument k, or GEO_ERR_CUDA. */
+int geo_tiles_set_far(geo_tiles* t, int far_band, const double* d_x, const double* d_y, double far_dist,
+                      int products, void* stream);
 
 /* A2, Eq. 1: write Sigma_ab = C(||s_a - s_b||; theta) (+ nugget if a == b) into
  * every lower tile, each directly in its own precision (the FP64 -> FP32

@@ -32,6 +32,10 @@ Function -> paper passage -> what pins it (tests/test_oracle_pins.py):
   mp_tile_cholesky             Algorithm 1                              band=p equals the
                                                                         dense factor;
                                                                         Fig. 2 op trace
+  far_product / far_tile_mask  three-precision extension (Section IX,  exact integer
+                               future work): reduced products for far   slices (hand
+                               tiles (reading: 8/12-bit row-scaled      values), error
+                               slices, 1 or 3 products)                 bounds vs sgemm
   loglik_mp                    Eq. 2 on the Algorithm 1 factor          within FP32-level
                                                                         error of dense
   dst_covariance / loglik_dst   DST / IND approximation (Section V-B)  d = 1: sum of the
@@ -62,6 +66,7 @@ __all__ = [
     "morton_keys", "morton_order", "matern", "covariance", "loglik_dense",
     "dense_factor", "mp_tile_cholesky", "loglik_mp", "factor_logdet_quad",
     "krige", "profile_sigma2", "Theta", "tile_is_dp", "nelder_mead", "mle", "profile_loglik",
+    "far_tile_mask", "far_product",
 ]
 
 LOG_2PI = math.log(2.0 * math.pi)
@@ -182,7 +187,62 @@ def tile_is_dp(i, j, band):
     return abs(i - j) < band
 
 
-def mp_tile_cholesky(A, nb, band, trace=None):
+def far_tile_mask(x, y, nb, far_band=None, far_dist=None):
+    """Which lower tiles (i, j) fall in the far tier of the three-precision
+    extension (Section IX names it as future work; reading: a third tier beyond
+    the FP32 one).  A tile is far when i - j >= far_band, or, with far_dist, when
+    the smallest distance between the bounding boxes of the two tiles' locations
+    (nb consecutive locations each, the last tile possibly short) is at least
+    far_dist.  Returns a p x p boolean array (upper triangle False)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = len(x)
+    p = -(-n // nb)
+    far = np.zeros((p, p), dtype=bool)
+    box = []
+    for i in range(p):
+        sl = slice(i * nb, min(n, (i + 1) * nb))
+        box.append((x[sl].min(), x[sl].max(), y[sl].min(), y[sl].max()))
+    for j in range(p):
+        for i in range(j + 1, p):
+            if far_band is not None and i - j >= far_band:
+                far[i, j] = True
+            if far_dist is not None:
+                gx = max(0.0, box[j][0] - box[i][1], box[i][0] - box[j][1])
+                gy = max(0.0, box[j][2] - box[i][3], box[i][2] - box[j][3])
+                if math.hypot(gx, gy) >= far_dist:
+                    far[i, j] = True
+    return far
+
+
+def far_product(Ai, Aj, products=3):
+    """The far tier's reduced-precision product Ai Aj' (Section IX extension).
+
+    Each row of a panel tile is scaled by a power of two, 2^-e with e the
+    smallest integer such that max|v| 2^-e < 1/2 (the row maximum taken after
+    rounding |v| to float32), and cut into an 8-bit integer t0 = rint(t) and a
+    12-bit integer t1 = rint(2^12 (t - t0)), t = v 2^(8-e) (round half to
+    even).  The product keeps the terms of weight 1 and 2^-12:
+        products = 3:  2^(e_r + e_c - 16) [a0 b0' + 2^-12 (a0 b1' + a1 b0')]
+        products = 1:  2^(e_r + e_c - 16) a0 b0'
+    (every term an exact integer sum, formed here in float64)."""
+    def slices(X):
+        X = np.asarray(X)
+        m = np.max(np.abs(X.astype(np.float32)), axis=1).astype(np.float64)
+        e = np.where(m > 0, np.frexp(m)[1] + 1, 0).astype(np.int64)
+        t = np.ldexp(np.asarray(X, dtype=np.float64), (8 - e)[:, None])
+        s0 = np.rint(t)
+        s1 = np.rint((t - s0) * 4096.0)
+        return s0, s1, e
+    a0, a1, ea = slices(Ai)
+    b0, b1, eb = slices(Aj)
+    acc = a0 @ b0.T
+    if products == 3:
+        acc = acc + (a0 @ b1.T + a1 @ b0.T) / 4096.0
+    return acc * np.ldexp(1.0, (ea[:, None] + eb[None, :] - 16))
+
+
+def mp_tile_cholesky(A, nb, band, trace=None, far=None, far_products=3):
     """Algorithm 1 (mixed-precision tile Cholesky, lower case) on a dense SPD A.
 
     Readings of the printed algorithm: the undefined `m` in the two precision
@@ -198,6 +258,11 @@ def mp_tile_cholesky(A, nb, band, trace=None):
     tiles promoted exactly; info = 1-based global row of the first failing
     pivot, 0 on success.  `trace`, if a list, receives (op, i, j, k) tuples
     in execution order, op in {dpotrf, dtrsm, strsm, dsyrk, dconv2s, dgemm, sgemm}.
+
+    far (optional p x p boolean, far_tile_mask): the three-precision extension
+    -- an off-band target tile marked far is still stored in FP32 and solved
+    by strsm, but its updates use far_product (products = far_products)
+    instead of the FP32 sgemm; the rounded result is stored in FP32 as usual.
     """
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
@@ -247,6 +312,12 @@ def mp_tile_cholesky(A, nb, band, trace=None):
                     Aik = T[(i, k)].astype(np.float64)
                     T[(i, j)] = T[(i, j)] - Aik @ Ajk.T
                     rec("dgemm", i, j, k)
+                elif far is not None and far[i, j]:
+                    # far tier: the reduced product of the operands' own values
+                    # (an in-band A_jk is read in its FP64 value, as the slices are)
+                    T[(i, j)] = (T[(i, j)].astype(np.float64) -
+                                 far_product(T[(i, k)], T[(j, k)], far_products)).astype(np.float32)
+                    rec("far", i, j, k)
                 else:
                     Aik_s = T[(i, k)]  # off-band whenever (i, j) is off-band
                     Ajk_s = S[(j, k)] if tile_is_dp(j, k, band) else T[(j, k)]
@@ -258,11 +329,12 @@ def mp_tile_cholesky(A, nb, band, trace=None):
     return L[:n, :n], 0
 
 
-def loglik_mp(x, y, z, theta: Theta, nb, band):
-    """Eq. 2 with the covariance factored by Algorithm 1 (float64 log-det and solve)."""
+def loglik_mp(x, y, z, theta: Theta, nb, band, far=None, far_products=3):
+    """Eq. 2 with the covariance factored by Algorithm 1 (float64 log-det and
+    solve); far / far_products: the far tier of mp_tile_cholesky."""
     n = len(z)
     S = covariance(x, y, theta=theta)
-    L, info = mp_tile_cholesky(S, nb, band)
+    L, info = mp_tile_cholesky(S, nb, band, far=far, far_products=far_products)
     if info != 0:
         return dict(loglik=float("nan"), logdet=float("nan"), quad=float("nan"), info=info)
     logdet, quad = factor_logdet_quad(L, z)

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libgeo.so")
-SOURCES = ["api.cu", "matern.cu", "cholesky.cu", "lp_gemm.cu", "dag.cu", "solve.cu", "mle.cu"]
+SOURCES = ["api.cu", "matern.cu", "cholesky.cu", "lp_gemm.cu", "dag.cu", "solve.cu", "mle.cu", "far.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -23,7 +23,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // approximation): CUDA-core tasks, bulk tasks, solve ends, tensor targets
 constexpr int N_VARIANTS = 3;
 struct MetaOffsets {
-    size_t off, slot, status, scal, sched_ctr, total;
+    size_t off, slot, far, status, scal, sched_ctr, total;
     size_t sched_g2[N_VARIANTS], sched_bulk[N_VARIANTS], sched_end[N_VARIANTS], sched_tct[N_VARIANTS],
         sched_y[N_VARIANTS];
     SchedGeom geom[N_VARIANTS];
@@ -37,6 +37,8 @@ static MetaOffsets meta_offsets(int p, int nb, int band, int lp_mode, int pp) {
     b = align256(b + sizeof(long long) * (size_t)p * p);
     m.slot = b;
     b = align256(b + sizeof(int) * (size_t)p * p);
+    m.far = b;
+    b = align256(b + (size_t)p * p);
     m.status = b;
     b = align256(b + sizeof(int) * ((size_t)ST_WORDS + 2 * (size_t)p));
     m.scal = b;
@@ -143,6 +145,8 @@ Layout make_layout(const geo_tiles* t) {
     L.status = (int*)(base + mo.status);
     L.tickets = L.status + ST_WORDS;
     L.scal = (double*)(base + mo.scal);
+    L.far = t->far_products ? (const unsigned char*)(base + mo.far) : nullptr;
+    L.far_products = t->far_products;
     L.planes = (__nv_bfloat16*)t->d_planes;
     L.npl = planes_per_slot(g.band, g.p);
     L.rexp = t->d_planes ? (int*)((char*)t->d_planes + align256((size_t)L.npl * g.pp * g.pp *
@@ -305,6 +309,7 @@ int geo_tiles_set_flags(geo_tiles* t, int flags) {
     if ((flags & GEO_FLAG_DST) &&
         ((flags & (GEO_FLAG_STEPWISE | GEO_FLAG_FP64_DMMA)) || t->lay.lp_mode != GEO_LP_SPLIT_BF16))
         return -2;
+    if ((flags & GEO_FLAG_STEPWISE) && t->far_products) return -2;   // the far tier runs in the persistent scheduler
     t->flags = flags;
     return GEO_OK;
 }
@@ -313,6 +318,29 @@ int geo_tiles_set_timeout_ns(geo_tiles* t, long long ns) {
     if (!t) return -1;
     if (ns != 0 && (ns < 100000LL || ns > 1000000000000LL)) return -2;
     t->timeout_ns = ns;
+    return GEO_OK;
+}
+
+int geo_tiles_set_far(geo_tiles* t, int far_band, const double* d_x, const double* d_y, double far_dist,
+                      int products, void* stream) {
+    if (!t || !t->d_meta) return -1;
+    if (far_band < 0) return -2;
+    if (far_dist > 0.0 && !d_x) return -3;
+    if (far_dist > 0.0 && !d_y) return -4;
+    if (!(far_dist == far_dist)) return -5;
+    if (products != 1 && products != 3) return -6;
+    if (far_band == 0 && !(far_dist > 0.0)) {   // tier off
+        t->far_products = 0;
+        return GEO_OK;
+    }
+    if (t->lay.lp_mode != GEO_LP_SPLIT_BF16 || !t->d_planes || (t->flags & GEO_FLAG_STEPWISE))
+        return GEO_ERR_UNSUPPORTED;
+    Layout L = make_layout(t);
+    MetaOffsets mo = meta_offsets(t->lay);
+    unsigned char* far = (unsigned char*)t->d_meta + mo.far;
+    if (launch_far_map(L, far, far_band, d_x, d_y, far_dist, L.scal + 2 * L.p + 8, (cudaStream_t)stream))
+        return GEO_ERR_CUDA;
+    t->far_products = products;
     return GEO_OK;
 }
 

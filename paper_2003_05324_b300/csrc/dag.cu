@@ -266,12 +266,13 @@ struct G2Sync {
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Wait until *p >= v (acquire).  False once the problem's status records a
-// failure, the launch is aborted, or the wait exceeds its bound (then it
-// records GEO_ERR_TIMEOUT with `where` in the problem's status and aborts the
-// launch: a timeout means the schedule itself went wrong).
-__device__ bool wait_ge(const DagArgs& A, const Layout& L, const int* p, int v, int where) {
+// failure, the launch is aborted, or the wait exceeds its bound (the launch's,
+// or `bound` ns if > 0; then it records GEO_ERR_TIMEOUT with `where` in the
+// problem's status and aborts the launch: a timeout means the schedule itself
+// went wrong).
+__device__ bool wait_ge(const DagArgs& A, const Layout& L, const int* p, int v, int where, long long bound = 0) {
     if (ld_acquire_s32(p) >= v) return true;
-    const long long dl = gtimer() + A.wait_ns;
+    const long long dl = gtimer() + (bound > 0 ? bound : A.wait_ns);
     for (unsigned it = 1;; ++it) {
         __nanosleep(64);
         if (ld_acquire_s32(p) >= v) return true;
@@ -1263,6 +1264,7 @@ struct TcItem {
     int i, j, k, mb, nc, rem, pid;
     bool ex, skip, pad;
     int nh;   // in-band: 64-column halves holding columns < nb
+    int fp;   // off-band target of the far tier: its products (1 or 3); 0 = the six of the FP32-accurate tier
 };
 
 __device__ __forceinline__ TcItem tc_decode(const DagArgs& A, long long w) {
@@ -1281,6 +1283,7 @@ __device__ __forceinline__ TcItem tc_decode(const DagArgs& A, long long w) {
     t.ex = P.g.ex && is_dp(t.i, t.j, P.L.band);
     t.skip = t.ex && t.i == t.j && t.mb < t.nc;
     t.nh = (t.nc * TC_BN + EX_BN < P.L.nb) ? 2 : 1;
+    t.fp = (!t.ex && P.L.far && P.L.far[t.i * P.L.p + t.j]) ? P.L.far_products : 0;
     return t;
 }
 
@@ -1314,9 +1317,12 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                 }
                 // (the test hook GEO_FLAG_TEST_STALL asks the items of step 0
                 // for one solved row chunk more than the panel tile has: that
-                // wait can never be met and must end by its bound)
+                // wait can never be met and ends by half the launch's bound, so
+                // it gives up before any wait downstream of it and its location
+                // is the one recorded)
                 const int stall = (P.L.flags & GEO_FLAG_TEST_STALL) && m.k == 0;
-                const bool ok = wait_ge(A, P.L, P.tcnt + m.i * P.L.p + m.k, chunks_of(P, m.i, m.k) + stall, 31) &&
+                const bool ok = wait_ge(A, P.L, P.tcnt + m.i * P.L.p + m.k, chunks_of(P, m.i, m.k) + stall, 31,
+                                        stall ? A.wait_ns / 2 : 0) &&
                                 wait_ge(A, P.L, P.tcnt + m.j * P.L.p + m.k, chunks_of(P, m.j, m.k), 32);
                 if (!ok) {
                     if (!single && !aborted(A)) continue;   // its problem failed meanwhile
@@ -1349,20 +1355,21 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                 mbar_expect_tx(FULL(st), bytes);
                 return smem + st * TC_STAGE_BYTES;
             };
-            if (!m.ex) {   // FP16 planes NPL.. of the 8/12/12 split
+            if (!m.ex) {   // FP16 planes NPL.. of the 8/12/12 split (a far item: the first one or two of each)
+                const int na = m.fp == 1 ? 1 : m.fp == 3 ? 2 : TC_HA;
+                const int nbq = m.fp == 1 ? 1 : m.fp == 3 ? 2 : TC_HB;
+                const uint32_t bytes = (uint32_t)(na * TC_A_BYTES + nbq * TC_B_BYTES);
                 for (int kc = 0; kc < nk && ok; ++kc, ++it) {
-                    uint8_t* sbase = next_stage(TC_H_STAGE_BYTES);
+                    uint8_t* sbase = next_stage(bytes);
                     if (!sbase) {
                         ok = false;
                         break;
                     }
                     const uint32_t full = FULL(it % TC_STAGES);
-#pragma unroll
-                    for (int s = 0; s < TC_HA; ++s)
+                    for (int s = 0; s < na; ++s)
                         tma_load_3d(smem_u32(sbase + s * TC_A_BYTES), map_a, kc * TC_BK, m.mb * TC_BM, sa + NPL + s,
                                     full);
-#pragma unroll
-                    for (int s = 0; s < TC_HB; ++s)
+                    for (int s = 0; s < nbq; ++s)
                         tma_load_3d(smem_u32(sbase + TC_HA * TC_A_BYTES + s * TC_B_BYTES), map_b, kc * TC_BK,
                                     m.nc * TC_BN, sb + NPL + s, full);
                 }
@@ -1455,18 +1462,37 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                         ok = false;
                         break;
                     }
+                    if (m.fp == 0) {
 #pragma unroll
-                    for (int q = 0; q < TC_HPAIRS; ++q) {
-                        const uint32_t a_addr = sbase + c_hpair_a[q] * TC_A_BYTES;
-                        const uint32_t b_addr = sbase + TC_HA * TC_A_BYTES + c_hpair_b[q] * TC_B_BYTES;
+                        for (int q = 0; q < TC_HPAIRS; ++q) {
+                            const uint32_t a_addr = sbase + c_hpair_a[q] * TC_A_BYTES;
+                            const uint32_t b_addr = sbase + TC_HA * TC_A_BYTES + c_hpair_b[q] * TC_B_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                            if (q == 0)
-                                umma_bf16(dst0, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
-                                          (kc | kk) != 0, TC_IDESC_F16);
-                            else
-                                umma_bf16(dst1, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
-                                          (kc | (q - 1) | kk) != 0, TC_IDESC_F16);
+                            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                                if (q == 0)
+                                    umma_bf16(dst0, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
+                                              (kc | kk) != 0, TC_IDESC_F16);
+                                else
+                                    umma_bf16(dst1, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
+                                              (kc | (q - 1) | kk) != 0, TC_IDESC_F16);
+                            }
+                        }
+                    } else {
+                        // far tier: a0 b0 -> acc0; with three products a0 b1 + a1 b0 -> acc1
+                        const uint32_t a0 = sbase, a1 = sbase + TC_A_BYTES;
+                        const uint32_t b0 = sbase + TC_HA * TC_A_BYTES, b1 = b0 + TC_B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk)
+                            umma_bf16(dst0, sw64_desc(a0 + kk * 32), sw64_desc(b0 + kk * 32), (kc | kk) != 0,
+                                      TC_IDESC_F16);
+                        if (m.fp == 3) {
+#pragma unroll
+                            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                                umma_bf16(dst1, sw64_desc(a0 + kk * 32), sw64_desc(b1 + kk * 32), (kc | kk) != 0,
+                                          TC_IDESC_F16);
+#pragma unroll
+                            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                                umma_bf16(dst1, sw64_desc(a1 + kk * 32), sw64_desc(b0 + kk * 32), 1u, TC_IDESC_F16);
                         }
                     }
                     umma_commit(EMPTY(it % TC_STAGES));
@@ -1611,7 +1637,12 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                     for (int cc = 0; cc < BATCH; cc += 16) {
                         float v0[16], v1[16];
                         tmem_ld16(taddr + hb * BATCH + cc, v0);
-                        tmem_ld16(taddr + TC_BN + hb * BATCH + cc, v1);
+                        if (m.fp != 1) {
+                            tmem_ld16(taddr + TC_BN + hb * BATCH + cc, v1);
+                        } else {   // the one-product far tier writes no second accumulator
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) v1[e] = 0.0f;
+                        }
                         int ec[16];
                         const int cl0 = c_begin + hb * BATCH + cc;
                         if (cl0 + 16 <= pp) {

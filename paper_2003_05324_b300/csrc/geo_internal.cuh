@@ -35,6 +35,8 @@ struct Layout {
     int* status;
     int* tickets;   // [2p] work counters of the persistent update kernels (FP64: k, off-band: p + k)
     double* scal;   // scalar scratch: per-tile log-det and quad partials [2*p], results [2]
+    const unsigned char* far;   // [p*p] far-tier map of the tiles (nullptr: no far tier)
+    int far_products;           // products of a far update (1 or 3)
 };
 
 constexpr int NPL = 7;    // BF16 8-bit slice planes (in-band products)
@@ -97,6 +99,11 @@ void prof_begin(int kind, cudaStream_t s);
 void prof_end(int kind, cudaStream_t s);
 
 // Launchers (defined in their own .cu files; all asynchronous on `s`).
+// far-tier map of the store's tiles (geo_tiles_set_far): far[i*p + j] = 1 for
+// off-band tiles (i, j) with i - j >= far_band (if > 0) or whose bounding
+// boxes of locations lie far_dist or more apart (if > 0); scratch: 4p doubles
+cudaError_t launch_far_map(const Layout& L, unsigned char* far, int far_band, const double* x, const double* y,
+                           double far_dist, double* scratch, cudaStream_t s);
 cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* y, const geo_theta& th,
                                 const geo_theta* dth, int reset_status, cudaStream_t s);
 cudaError_t launch_load_dense(const Layout& L, const double* a, cudaStream_t s);

@@ -65,7 +65,7 @@ class geo_tiles(ctypes.Structure):
                 ("aux_stream", ctypes.c_void_p), ("ev_fork", ctypes.c_void_p), ("ev_join", ctypes.c_void_p),
                 ("tmap", ctypes.c_uint64 * 48), ("flags", ctypes.c_int),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_longlong),
-                ("timeout_ns", ctypes.c_longlong)]
+                ("timeout_ns", ctypes.c_longlong), ("far_products", ctypes.c_int)]
 
 
 class geo_mle_opts(ctypes.Structure):
@@ -97,6 +97,7 @@ def _load():
         "geo_tiles_set_flags": [ctypes.POINTER(geo_tiles), I],
         "geo_tiles_set_timeout_ns": [ctypes.POINTER(geo_tiles), ctypes.c_longlong],
         "geo_tiles_set_trace": [ctypes.POINTER(geo_tiles), P, ctypes.c_longlong],
+        "geo_tiles_set_far": [ctypes.POINTER(geo_tiles), I, P, P, D, I, P],
         "geo_matern_tiles": [ctypes.POINTER(geo_tiles), P, P, geo_theta, P],
         "geo_tiles_load_dense": [ctypes.POINTER(geo_tiles), P, P],
         "geo_tiles_to_dense": [ctypes.POINTER(geo_tiles), P, P],
@@ -200,6 +201,14 @@ class TileStore:
 
     def set_flags(self, flags: int):
         _check(lib.geo_tiles_set_flags(ctypes.byref(self.t), int(flags)), "geo_tiles_set_flags")
+
+    def set_far(self, far_band: int = 0, x=None, y=None, far_dist: float = 0.0, products: int = 3, stream=None):
+        """The far tier of the three-precision extension (geo_tiles_set_far):
+        off-band tiles with i - j >= far_band, or whose locations' bounding
+        boxes lie far_dist or more apart, are updated with `products` (1 or 3)
+        slice products.  far_band = 0 and far_dist = 0 turn it off."""
+        _check(lib.geo_tiles_set_far(ctypes.byref(self.t), int(far_band), _ptr(x), _ptr(y), float(far_dist),
+                                     int(products), _stream(stream)), "geo_tiles_set_far")
 
     def set_timeout_ns(self, ns: int):
         """Bound of every device-side wait of the persistent scheduler (0: default)."""

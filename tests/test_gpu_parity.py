@@ -420,3 +420,68 @@ def test_module_level_api(G):
     assert G.loglik(X, Y, Z, th, nb=128, band=2) == want
     from paper_2003_05324_b300 import serve
     assert G.Server is serve.Server
+
+
+# ------------------------------ far tier (three-precision extension) ---
+@pytest.mark.parametrize("products,far_band,far_dist", [(3, 3, 0.0), (1, 4, 0.0), (3, 0, 0.25)])
+def test_far_tier_factor_matches_oracle_emulation(G, products, far_band, far_dist):
+    """Off-band tiles of the far tier are updated with 3 or 1 slice products.
+    The oracle's Algorithm 1 with the same far-tile map and its exact-integer
+    emulation of those products (far_product) is the reference: the GPU factor
+    stays within three times the FP32 tier's own error of it everywhere, while
+    the far tier itself moves the factor away from FP64 by more than that (so
+    the comparison sees the reduced products, not FP32 rounding).  The map
+    is the oracle's own (band rule, or bounding-box distance)."""
+    n, nb = 1536, 128   # p = 12
+    x, y = inputs.uniform_points(n, seed=5)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    S = O.covariance(x, y, theta=O.Theta(1.0, 0.1, 0.5, 1e-3))
+    far = O.far_tile_mask(x, y, nb, far_band=far_band or None, far_dist=far_dist or None)
+    far &= ~np.eye(far.shape[0], dtype=bool)
+    assert far.any()
+    ts = G.TileStore(n, nb, 1, G.GEO_LP_SPLIT_BF16)
+    ts.load_dense(dev(S.T))
+    ts.set_far(far_band, dev(x), dev(y), far_dist, products)
+    ts.potrf()
+    got = ts.to_dense().cpu().numpy()
+    Lfar, info = O.mp_tile_cholesky(S, nb, 1, far=far, far_products=products)
+    assert info == 0
+    Lmp, _ = O.mp_tile_cholesky(S, nb, 1)
+    Ldp, _ = O.dense_factor(S)
+    ref_err = np.max(np.abs(Lmp - Ldp))                # the FP32 tier's rounding
+    far_err = np.max(np.abs(Lfar - Ldp))
+    assert far_err > 3.0 * ref_err                     # the far tier is visible
+    assert np.max(np.abs(got - Lfar)) <= 3.0 * ref_err
+    # tiles that are not far and see no far input before step 1 are untouched by the tier
+    assert np.max(np.abs(got[:, :nb] - Lmp[:, :nb])) <= 3.0 * ref_err
+    # off again: the store gives the FP32-accurate tier's factor
+    ts.set_far(0, None, None, 0.0, 3)
+    ts.load_dense(dev(S.T))
+    ts.potrf()
+    assert np.max(np.abs(ts.to_dense().cpu().numpy() - Lmp)) <= 3.0 * ref_err
+
+
+def test_far_tier_loglik_and_refusals(G):
+    """geo_loglik on a store with a far tier, against the oracle's Algorithm 1
+    with the same far map (Eq. 2 within 4x the FP32 tier's error of it plus
+    1e-9), and the modes that cannot run it refuse it."""
+    m, nb = 40, 200
+    x, y = inputs.jittered_grid(m, seed=11)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.matern_field_rff(x, y, 1.0, 0.1, 0.5, seed=12)
+    th = G.Theta(1.0, 0.1, 0.5)
+    ts = G.TileStore(len(z), nb, 1, G.GEO_LP_SPLIT_BF16)
+    ts.set_far(3, None, None, 0.0, 3)
+    l = ts.loglik(dev(x), dev(y), dev(z), th)[0]
+    far = O.far_tile_mask(x, y, nb, far_band=3)
+    want = O.loglik_mp(x, y, z, oracle_theta(th), nb, 1, far=far, far_products=3)["loglik"]
+    mp = O.loglik_mp(x, y, z, oracle_theta(th), nb, 1)["loglik"]
+    dp = O.loglik_dense(x, y, z, oracle_theta(th))["loglik"]
+    assert abs(l - want) <= 4.0 * abs(mp - dp) + 1e-9 * abs(dp)
+    t32 = G.TileStore(len(z), nb, 1, G.GEO_LP_FP32)
+    with pytest.raises(G.GeoError):
+        t32.set_far(3, None, None, 0.0, 3)
+    with pytest.raises(G.GeoError):
+        ts.set_far(3, None, None, 0.0, 2)

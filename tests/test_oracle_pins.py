@@ -539,3 +539,89 @@ def test_dst_full_reach_is_the_dense_likelihood():
         assert O.loglik_dst(x, y, z, th, nb, d)["loglik"] == want
     # one tile diagonal fewer changes the value
     assert O.loglik_dst(x, y, z, th, nb, p - 1)["loglik"] != want
+
+
+# ----------------------------------- far tier (Section IX extension) pins ---
+def test_far_product_hand_values():
+    """Slices by hand: row a = (0.3, -0.1): max 0.3 = 0.6 2^-1 -> e = 0,
+    t = (76.8, -25.6), a0 = (77, -26), a1 = rint(4096 (-0.2, 0.4)) =
+    (-819, 1638).  Row b = (0.75, 0.5): max 0.75 = 0.75 2^0 -> e = 1,
+    t = (96, 64) exactly, b0 = (96, 64), b1 = (0, 0)."""
+    A = np.array([[0.3, -0.1]])
+    B = np.array([[0.75, 0.5]])
+    a0, a1 = np.array([77.0, -26.0]), np.array([-819.0, 1638.0])
+    b0 = np.array([96.0, 64.0])
+    scale = 2.0 ** (0 + 1 - 16)
+    want3 = scale * (a0 @ b0 + (a1 @ b0) / 4096.0)
+    want1 = scale * (a0 @ b0)
+    assert O.far_product(A, B, 3)[0, 0] == want3
+    assert O.far_product(A, B, 1)[0, 0] == want1
+    # the exact product here differs from the 3-product form only by the
+    # rounding of a1 (b1 = 0): |0.3*0.75 - 0.1*0.5 - want3| <= 2 * 2^-13 * 96 * scale
+    assert abs((0.3 * 0.75 - 0.1 * 0.5) - want3) <= 2 * 2 ** -13 * 96 * scale
+
+
+@pytest.mark.parametrize("products,bound_units", [(3, 0.25 + 2 * 128.5 * 2 ** -13 + 2 ** -26),
+                                                  (1, 2 * 128.5 * 0.5 + 0.25 + 2 * 128.5 * 2 ** -13)])
+def test_far_product_error_bound(products, bound_units):
+    """With t = t0 + t1 2^-12 + d, |d| <= 2^-13, and |t0| <= 128, |t1| <= 2048,
+    each dropped term is bounded: per contraction index the error of the
+    3-product form is at most |t1 2^-12||u1 2^-12| + |t||d_u| + |u||d_t|
+    <= 1/4 + 2 (128.5) 2^-13 (+ d d) in units of 2^(e_r + e_c - 16); the
+    1-product form also drops t0 u1 2^-12 + t1 2^-12 u0 (<= 128.5 each).  The
+    bound holds element by element and is reached to within a factor of a few."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((20, 64)) * np.exp(rng.uniform(-3, 3, size=(20, 1)))
+    B = rng.standard_normal((17, 64)).astype(np.float32).astype(np.float64)
+    P = O.far_product(A, B, products)
+    exact = A @ B.T
+
+    def ex(X):
+        m = np.max(np.abs(X.astype(np.float32)), axis=1).astype(np.float64)
+        return np.frexp(m)[1] + 1
+    unit = np.ldexp(1.0, ex(A)[:, None] + ex(B)[None, :] - 16)
+    err = np.abs(P - exact) / unit
+    assert np.all(err <= 64 * bound_units)
+    assert err.max() >= bound_units / 8          # the dropped terms are really there
+
+
+def test_far_product_full_tier_would_be_exact_to_fp32_level():
+    """Keeping every slice pair makes the product the exact one up to the
+    second rounding only: a check that the slices carry the value (the a1
+    slice is the next 12 bits, not a lost term)."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((8, 32))
+    a = O.far_product(A, np.eye(32), 3)                 # B = I: b0 = 128 on its unit, b1 = 0
+    assert np.allclose(a, A, rtol=0, atol=np.max(np.abs(A)) * 2 ** -18)
+
+
+def test_far_tile_mask_band_and_distance():
+    # 3 tiles of 2 points on a line: boxes [0, .1], [.5, .6], [.9, 1.0]
+    x = np.array([0.0, 0.1, 0.5, 0.6, 0.9, 1.0])
+    y = np.zeros(6)
+    m = O.far_tile_mask(x, y, 2, far_band=2)
+    assert m.tolist() == [[False, False, False], [False, False, False], [True, False, False]]
+    d = O.far_tile_mask(x, y, 2, far_dist=0.35)        # gaps: (1,0) 0.4, (2,1) 0.3, (2,0) 0.8
+    assert d.tolist() == [[False, False, False], [True, False, False], [True, False, False]]
+    assert not O.far_tile_mask(x, y, 2, far_dist=0.9).any()
+
+
+def test_far_tier_in_algorithm1():
+    """Algorithm 1 with far tiles: no far tile leaves the factor unchanged bit
+    for bit; a far tier moves it by more than the FP32 tier's rounding but
+    stays within its own per-product bound (3 products: ~2^-16 relative)."""
+    x, y = inputs.jittered_grid(16, seed=5)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    S = O.covariance(x, y, theta=O.Theta(1.0, 0.1, 0.5, 1e-3))
+    L64, _ = O.dense_factor(S)
+    L1, _ = O.mp_tile_cholesky(S, 32, 1)
+    none = np.zeros((8, 8), dtype=bool)
+    L1b, _ = O.mp_tile_cholesky(S, 32, 1, far=none)
+    assert np.array_equal(L1, L1b)
+    far = O.far_tile_mask(x, y, 32, far_band=3)
+    L3, info = O.mp_tile_cholesky(S, 32, 1, far=far, far_products=3)
+    assert info == 0
+    e1 = np.max(np.abs(L1 - L64))
+    e3 = np.max(np.abs(L3 - L64))
+    assert e1 < e3 < 2 ** -10
