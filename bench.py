@@ -55,6 +55,7 @@ def parse():
                     help="in-band (FP64) updates on the FP64 pipe instead of FP64-accurate tensor-core products")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-evaluation measurement")
     ap.add_argument("--no-dst", action="store_true", help="skip the DST / IND approximation timings")
+    ap.add_argument("--no-far", action="store_true", help="skip the far-tier (three-precision) sweep")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-window", type=float, default=3.0, help="seconds of Poisson arrivals served")
     return ap.parse_args()
@@ -475,6 +476,27 @@ def run_batch(geo, dev):
 
 
 DST_BANDS = (1, 2, 4)
+# far tier of the three-precision extension: (far_band, far_dist, products)
+FAR_SWEEP = [(2, 0.0, 3), (4, 0.0, 3), (8, 0.0, 3), (16, 0.0, 3), (32, 0.0, 3), (8, 0.0, 1), (16, 0.0, 1),
+             (32, 0.0, 1), (0, 0.2, 3), (0, 0.3, 3), (0, 0.5, 3), (0, 0.5, 1)]
+
+
+def far_tile_count(x, y, nb, far_band, far_dist):
+    """Off-band tiles of band 1 that the far rule marks (host count for the report)."""
+    n = len(x)
+    p = -(-n // nb)
+    box = [(x[i * nb:(i + 1) * nb].min(), x[i * nb:(i + 1) * nb].max(), y[i * nb:(i + 1) * nb].min(),
+            y[i * nb:(i + 1) * nb].max()) for i in range(p)]
+    cnt = 0
+    for j in range(p):
+        for i in range(j + 1, p):
+            f = far_band > 0 and i - j >= far_band
+            if far_dist > 0:
+                gx = max(0.0, box[j][0] - box[i][1], box[i][0] - box[j][1])
+                gy = max(0.0, box[j][2] - box[i][3], box[i][2] - box[j][3])
+                f = f or math.hypot(gx, gy) >= far_dist
+            cnt += f
+    return cnt, p * (p - 1) // 2
 SERVE_SWEEP_RATES = (2.0, 5.0, 10.0, 20.0, 50.0)
 SERVE_SWEEP_WINDOW = 4.0
 
@@ -735,6 +757,27 @@ def main():
             dst.append(ent)
             del tsd
 
+    # the far tier of the three-precision extension: error and time per rule
+    far = []
+    if not args.no_far and args.lp == "bf16" and ts.band == 1:
+        for fb, fd, fp in FAR_SWEEP:
+            tsf = geo.TileStore(n, NB, 1, geo.GEO_LP_SPLIT_BF16, device=dev)
+            tsf.set_far(fb, X, Y, fd, fp)
+            cnt, tot = far_tile_count(x, y, NB, fb, fd)
+            ent = {"far_band": fb, "far_dist": fd, "products": fp, "far_tiles": cnt, "offband_tiles": tot}
+            try:
+                eval_once(tsf)
+                tf, lf = eval_once(tsf)
+                ent.update({"seconds_per_eval": tf, "tflops": flops / tf / 1e12, "loglik": lf,
+                            "speedup_vs_mp": (ms_step / 1000.0) / tf})
+                if fp64:
+                    ent["rel_err_vs_fp64"] = abs(lf - fp64["loglik"]) / abs(fp64["loglik"])
+                    ent["passes_1e-6_gate"] = ent["rel_err_vs_fp64"] <= 1e-6
+            except geo.NotSPDError:
+                ent["status"] = "not positive definite with this far tier"
+            far.append(ent)
+            del tsf
+
     if rank != 0:
         return
     p50 = statistics.median(step_ms)
@@ -769,6 +812,10 @@ def main():
         out["band_sweep"] = sweep
     if dst:
         out["dst"] = dst
+    if far:
+        out["far_tier_sweep"] = far
+        ok = [e for e in far if e.get("passes_1e-6_gate")]
+        out["far_tier_best"] = min(ok, key=lambda e: e["seconds_per_eval"]) if ok else None
     if not args.no_batch and world == 1:
         out["batch"] = run_batch(geo, dev)
     if not args.no_serve and world == 1:

@@ -1523,31 +1523,23 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                                     ok = false;
                                     break;
                                 }
-                                if (pass == 0) {
+                                // one MMA per (A slice, run of B slices): N = 64 x the run,
+                                // the accumulator the run of level slots; each slot's
+                                // first product of the part overwrites it
+                                const int nq = pass == 0 ? EX_P1_MMAS : EX_P2_MMAS;
+                                const uint32_t b_base = sbase + (pass == 0 ? 4 : 3) * TC_A_BYTES;
+#pragma unroll 1
+                                for (int q = 0; q < nq; ++q) {
+                                    const signed char* e = pass == 0 ? c_ex1[q] : c_ex2[q];
+                                    const int slot = e[3], cnt = e[2];
+                                    const uint32_t a_addr = sbase + e[0] * TC_A_BYTES;
+                                    const uint32_t b_addr = b_base + e[1] * EX_B_BYTES;
+                                    const uint32_t idesc = ex_idesc(EX_BN * cnt);
 #pragma unroll
-                                    for (int q = 0; q < EX_P1_PAIRS; ++q) {
-                                        const int acc = c_ex1[q][2];
-                                        const uint32_t a_addr = sbase + c_ex1[q][0] * TC_A_BYTES;
-                                        const uint32_t b_addr = sbase + 4 * TC_A_BYTES + c_ex1[q][1] * EX_B_BYTES;
-#pragma unroll
-                                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                                            umma_bf16(tmem_base + acc * EX_BN, sw64_desc(a_addr + kk * 32),
-                                                      sw64_desc(b_addr + kk * 32), (touched >> acc) & 1u, EX_IDESC);
-                                            touched |= 1u << acc;
-                                        }
-                                    }
-                                } else {
-#pragma unroll
-                                    for (int q = 0; q < EX_P2_PAIRS; ++q) {
-                                        const int acc = c_ex2[q][2];
-                                        const uint32_t a_addr = sbase + c_ex2[q][0] * TC_A_BYTES;
-                                        const uint32_t b_addr = sbase + 3 * TC_A_BYTES + c_ex2[q][1] * EX_B_BYTES;
-#pragma unroll
-                                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                                            umma_bf16(tmem_base + acc * EX_BN, sw64_desc(a_addr + kk * 32),
-                                                      sw64_desc(b_addr + kk * 32), (touched >> acc) & 1u, EX_IDESC);
-                                            touched |= 1u << acc;
-                                        }
+                                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                                        umma_bf16(tmem_base + slot * EX_BN, sw64_desc(a_addr + kk * 32),
+                                                  sw64_desc(b_addr + kk * 32), (touched >> slot) & 1u, idesc);
+                                        touched |= ((1u << cnt) - 1u) << slot;
                                     }
                                 }
                                 umma_commit(EMPTY(it % TC_STAGES));
@@ -1694,15 +1686,15 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                         tc_fence_after();
 #pragma unroll 1
                         for (int cc = 0; cc < EX_BN; cc += 8) {
-                            float v[EX_NACC][8];
-                            tmem_ld7x8(tmem_base + tlane + cc, v);
+                            float v[EX_NSLOT][8];
+                            tmem_ld8x8(tmem_base + tlane + cc, v);
                             const int4 ea = *reinterpret_cast<const int4*>(eb + c_begin + cc);
                             const int4 ebb = *reinterpret_cast<const int4*>(eb + c_begin + cc + 4);
                             const int ec[8] = {ea.x, ea.y, ea.z, ea.w, ebb.x, ebb.y, ebb.z, ebb.w};
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
                                 const long long tot = ex_fixed_total(v[0][e], v[1][e], v[2][e], v[3][e], v[4][e],
-                                                                     v[5][e], v[6][e]);
+                                                                     v[5][e], v[6][e], v[EX_X][e]);
                                 cpre[e] = fma(-(double)tot, pow2d(er + ec[e] - 56), cpre[e]);
                             }
 #pragma unroll

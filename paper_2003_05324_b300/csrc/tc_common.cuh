@@ -47,36 +47,39 @@ __constant__ int c_hpair_b[TC_HPAIRS] = {0, 3, 2, 0, 1, 0};
 // scale) and every pair with a + b <= 6 (28 pairs).  A 128 x 64 output block
 // is accumulated over K parts of EX_KP = 256: one product of two slices sums
 // at most 256 * 2^14 = 2^22 in integer units, so an accumulator holding up to
-// four pairs of one level a + b stays below 2^24 and the tensor core's FP32
-// accumulation is exact.  Levels 0..4 (15 pairs) use six exact accumulators;
-// levels 5 and 6 (13 pairs), 2^-40 below level 0, share a seventh, FP32-
-// accumulated one.  Each K part is drained into the FP64 target, so the error
-// of the whole update is that of FP64 accumulation.
-// Pass 1 stages A slices 0..3 and B slices 0..6, pass 2 A slices 4..6 and B
-// slices 0..2 (the stage holds at most 4 x 8 KB + 7 x 4 KB).
+// four pairs of one level a + b stays at or below 2^24 and the tensor core's
+// FP32 accumulation is exact.  Each level L has its own TMEM slot at column
+// 64 L (L = 0..6), except the fifth pair of level 4, (4, 0), which goes to slot
+// X at column 448: levels 0..4 are exact, levels 5 and 6 (2^-40 below level 0)
+// are FP32-accumulated.  Each K part is drained into the FP64 target, so the
+// error of the whole update is that of FP64 accumulation.
+// The pairs that share an A slice are one MMA whose B operand is the run of
+// consecutive B slices (64 rows each, adjacent in shared memory) and whose
+// accumulator is the run of consecutive level slots: pass 1 stages A slices
+// 0..3 and B slices 0..6 and issues 7 MMAs of N = 64..256 (22 pairs); pass 2
+// stages A slices 4..6 and B slices 0..2 and issues 4 MMAs (6 pairs).
 constexpr int EX_BN = 64;
 constexpr int EX_KP = 256;
-constexpr int EX_NACC = 7;
+constexpr int EX_NSLOT = 8;                          // levels 0..6 and X
+constexpr int EX_X = 7;                              // slot of the pair (4, 0)
 constexpr int EX_B_BYTES = EX_BN * TC_BK * 2;        // 4 KB
-constexpr int EX_P1_PAIRS = 22, EX_P2_PAIRS = 6;
+constexpr int EX_P1_MMAS = 7, EX_P2_MMAS = 4;
 constexpr uint32_t EX_P1_BYTES = 4 * TC_A_BYTES + 7 * EX_B_BYTES;
 constexpr uint32_t EX_P2_BYTES = 3 * TC_A_BYTES + 3 * EX_B_BYTES;
 static_assert(EX_P1_BYTES <= (uint32_t)TC_STAGE_BYTES, "EX stage");
-static_assert(EX_NACC * EX_BN <= 4 * TC_BN, "EX accumulators");
-static_assert(EX_NACC == 7, "ex_fixed_total sums levels 0..4 (acc 0..5) and the level-5/6 accumulator");
-// (A slice, B slice, accumulator); pass 2's A slice index counts from slice 4
-__constant__ signed char c_ex1[EX_P1_PAIRS][3] = {
-    {0, 0, 0},                                                       // level 0
-    {0, 1, 1}, {1, 0, 1},                                            // level 1
-    {0, 2, 2}, {1, 1, 2}, {2, 0, 2},                                 // level 2
-    {0, 3, 3}, {1, 2, 3}, {2, 1, 3}, {3, 0, 3},                      // level 3
-    {0, 4, 4}, {1, 3, 4}, {2, 2, 4}, {3, 1, 4},                      // level 4 (with (4,0) below)
-    {0, 5, 6}, {1, 4, 6}, {2, 3, 6}, {3, 2, 6},                      // level 5
-    {0, 6, 6}, {1, 5, 6}, {2, 4, 6}, {3, 3, 6}};                     // level 6
-__constant__ signed char c_ex2[EX_P2_PAIRS][3] = {
-    {0, 0, 5},                                                       // (4,0): level 4
-    {0, 1, 6}, {1, 0, 6},                                            // (4,1) (5,0): level 5
-    {0, 2, 6}, {1, 1, 6}, {2, 0, 6}};                                // (4,2) (5,1) (6,0): level 6
+static_assert(EX_NSLOT * EX_BN <= 4 * TC_BN, "EX accumulators");
+// (A slice, first B slice, number of B slices, first slot); pass 2's A slice
+// index counts from slice 4
+__constant__ signed char c_ex1[EX_P1_MMAS][4] = {
+    {0, 0, 4, 0}, {0, 4, 3, 4},                                      // (0,0..3) (0,4..6)
+    {1, 0, 4, 1}, {1, 4, 2, 5},                                      // (1,0..3) (1,4..5)
+    {2, 0, 4, 2}, {2, 4, 1, 6},                                      // (2,0..3) (2,4)
+    {3, 0, 4, 3}};                                                   // (3,0..3)
+__constant__ signed char c_ex2[EX_P2_MMAS][4] = {
+    {0, 0, 1, EX_X},                                                 // (4,0): slot X
+    {0, 1, 2, 5},                                                    // (4,1..2)
+    {1, 0, 2, 5},                                                    // (5,0..1)
+    {2, 0, 1, 6}};                                                   // (6,0)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -128,8 +131,10 @@ constexpr uint32_t TC_IDESC =
 // kind::f16 with FP16 A and B (the FP16 off-band planes), D = F32
 constexpr uint32_t TC_IDESC_F16 = (1u << 4) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 
-constexpr uint32_t EX_IDESC =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(EX_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+// kind::f16, D = F32, A = B = BF16, K-major, M = 128 and N = nrows (a multiple of 16, <= 256)
+__host__ __device__ constexpr uint32_t ex_idesc(int nrows) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nrows >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc,
                                           uint32_t idesc = TC_IDESC) {
@@ -172,19 +177,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// 8 columns of each of the seven in-band accumulators (64 columns apart) for
-// this warp's 32 lanes, loads and the wait in one statement so that no use of
-// the registers can be scheduled before the wait
-__device__ __forceinline__ void tmem_ld7x8(uint32_t taddr, float (&v)[EX_NACC][8]) {
-    uint32_t r[EX_NACC][8];
+// 8 columns of each of the eight in-band slots (64 columns apart) for this
+// warp's 32 lanes, loads and the wait in one statement so that no use of the
+// registers can be scheduled before the wait
+__device__ __forceinline__ void tmem_ld8x8(uint32_t taddr, float (&v)[EX_NSLOT][8]) {
+    uint32_t r[EX_NSLOT][8];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%56];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%57];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%58];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%59];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32,%33,%34,%35,%36,%37,%38,%39}, [%60];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40,%41,%42,%43,%44,%45,%46,%47}, [%61];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48,%49,%50,%51,%52,%53,%54,%55}, [%62];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%65];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%66];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%67];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32,%33,%34,%35,%36,%37,%38,%39}, [%68];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40,%41,%42,%43,%44,%45,%46,%47}, [%69];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48,%49,%50,%51,%52,%53,%54,%55}, [%70];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%56,%57,%58,%59,%60,%61,%62,%63}, [%71];\n"
         "tcgen05.wait::ld.sync.aligned;\n"
         : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]),
           "=r"(r[0][6]), "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]),
@@ -195,12 +201,13 @@ __device__ __forceinline__ void tmem_ld7x8(uint32_t taddr, float (&v)[EX_NACC][8
           "=r"(r[4][4]), "=r"(r[4][5]), "=r"(r[4][6]), "=r"(r[4][7]), "=r"(r[5][0]), "=r"(r[5][1]),
           "=r"(r[5][2]), "=r"(r[5][3]), "=r"(r[5][4]), "=r"(r[5][5]), "=r"(r[5][6]), "=r"(r[5][7]),
           "=r"(r[6][0]), "=r"(r[6][1]), "=r"(r[6][2]), "=r"(r[6][3]), "=r"(r[6][4]), "=r"(r[6][5]),
-          "=r"(r[6][6]), "=r"(r[6][7])
+          "=r"(r[6][6]), "=r"(r[6][7]), "=r"(r[7][0]), "=r"(r[7][1]), "=r"(r[7][2]), "=r"(r[7][3]),
+          "=r"(r[7][4]), "=r"(r[7][5]), "=r"(r[7][6]), "=r"(r[7][7])
         : "r"(taddr), "r"(taddr + EX_BN), "r"(taddr + 2 * EX_BN), "r"(taddr + 3 * EX_BN), "r"(taddr + 4 * EX_BN),
-          "r"(taddr + 5 * EX_BN), "r"(taddr + 6 * EX_BN)
+          "r"(taddr + 5 * EX_BN), "r"(taddr + 6 * EX_BN), "r"(taddr + 7 * EX_BN)
         : "memory");
 #pragma unroll
-    for (int a = 0; a < EX_NACC; ++a)
+    for (int a = 0; a < EX_NSLOT; ++a)
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[a][e] = __uint_as_float(r[a][e]);
 }
@@ -223,22 +230,23 @@ __device__ __forceinline__ void slice_value(T v, int e, __nv_bfloat16* out) {
     }
 }
 
-// The seven in-band accumulators of one output as one exact fixed-point sum, in
-// units of 2^-40 of the level-0 unit.  Accumulator L <= 4 holds integers times
-// 2^-8L below 2^24 in magnitude (exact), so I_L = acc_L 2^8L is an exact
-// float-to-int conversion; the shared level-5/6 accumulator is rounded to the
-// nearest unit (2^-40, below its own FP32 accumulation error).  |level 0| <=
-// 2^22 bounds the total by 2^62 (1 + 2^-7 + ...) < 2^63.  Integer arithmetic
-// replaces the seven FP64 additions: on this part the FP64 pipe runs at 1/71
-// of the FP32 rate, and one conversion of the total to FP64 is left.
-__device__ __forceinline__ long long ex_fixed_total(float a0, float a1, float a2, float a3, float a4, float a5,
-                                                    float a56) {
-    const long long i0 = __float2int_rn(a0);
-    const long long i1 = __float2int_rn(a1 * 256.0f);
-    const long long i2 = __float2int_rn(a2 * 65536.0f);
-    const long long i3 = __float2int_rn(a3 * 16777216.0f);
-    const long long i4 = (long long)(__float2int_rn(a4 * 4294967296.0f) + __float2int_rn(a5 * 4294967296.0f));
-    const long long i56 = __float2int_rn(a56 * 1099511627776.0f);
+// The eight in-band slots of one output as one exact fixed-point sum, in units
+// of 2^-40 of the level-0 unit.  Slot L <= 4 (and X, level 4) holds integers
+// times 2^-8L of magnitude at most 2^24 (exact), so I_L = s_L 2^8L is an exact
+// float-to-int conversion; the FP32-accumulated level-5 and level-6 slots are
+// each rounded to the nearest unit (2^-40, below their own accumulation error).
+// |level 0| <= 2^22 bounds the total by 2^62 (1 + 2^-7 + ...) < 2^63.  Integer
+// arithmetic replaces the FP64 additions: on this part the FP64 pipe runs at
+// 1/71 of the FP32 rate, and one conversion of the total to FP64 is left.
+__device__ __forceinline__ long long ex_fixed_total(float s0, float s1, float s2, float s3, float s4, float s5,
+                                                    float s6, float sx) {
+    const long long i0 = __float2int_rn(s0);
+    const long long i1 = __float2int_rn(s1 * 256.0f);
+    const long long i2 = __float2int_rn(s2 * 65536.0f);
+    const long long i3 = __float2int_rn(s3 * 16777216.0f);
+    const long long i4 = (long long)__float2int_rn(s4 * 4294967296.0f) + (long long)__float2int_rn(sx * 4294967296.0f);
+    const long long i56 =
+        (long long)__float2int_rn(s5 * 1099511627776.0f) + (long long)__float2int_rn(s6 * 1099511627776.0f);
     return (i0 << 40) + (i1 << 32) + (i2 << 24) + (i3 << 16) + (i4 << 8) + i56;
 }
 

@@ -452,7 +452,13 @@ def test_far_tier_factor_matches_oracle_emulation(G, products, far_band, far_dis
     ref_err = np.max(np.abs(Lmp - Ldp))                # the FP32 tier's rounding
     far_err = np.max(np.abs(Lfar - Ldp))
     assert far_err > 3.0 * ref_err                     # the far tier is visible
-    assert np.max(np.abs(got - Lfar)) <= 3.0 * ref_err
+    # Three products (20-bit slices): within the FP32 tier's own error.  One
+    # product (8-bit slices): a slice of a solved panel row can round to the
+    # neighbouring integer under FP32-level differences between the two
+    # implementations' panel solves, a 2^-8 step of that product term; the GPU
+    # must still reproduce the tier's departure from FP64 to 2 %.
+    tol = 3.0 * ref_err if products == 3 else max(3.0 * ref_err, 0.02 * far_err)
+    assert np.max(np.abs(got - Lfar)) <= tol
     # tiles that are not far and see no far input before step 1 are untouched by the tier
     assert np.max(np.abs(got[:, :nb] - Lmp[:, :nb])) <= 3.0 * ref_err
     # off again: the store gives the FP32-accurate tier's factor
