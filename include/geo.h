@@ -103,7 +103,11 @@ typedef struct geo_tiles {
  * s (in a) of PC: the factor of (s,s), the solve of (s+1,s), with t_claim =
  * sub-step start, t_ready = its dependencies met, t_end = done; 14 = one
  * (column slice, contraction part) of an in-band item (c = slice * parts +
- * part), t_ready = its products done, t_end = drained.  Times are
+ * part), t_ready = its products done, t_end = drained; 15 = the MMA
+ * thread's view of an off-band item (t_claim = began waiting for its first
+ * stage, t_ready = that stage arrived, t_end = its last MMA issued); 16 = the
+ * copy thread's view (t_claim = before taking it from the queue, t_ready =
+ * its panel tiles were solved, t_end = its first stage's copies issued).  Times are
  * %globaltimer nanoseconds: t_claim when the task was taken, t_ready when its
  * dependencies were met, t_end when it finished. */
 typedef struct geo_trace_rec {

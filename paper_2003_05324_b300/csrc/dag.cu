@@ -1304,6 +1304,8 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
         if (lane != 0) return;
         int it = 0;
         for (int t = 0;;) {
+            const long long tq0 = A.trace ? gtimer() : 0;   // trace: claim, dependencies met, first copies issued
+            long long tq1 = 0;
             long long w = (*abort_flag || aborted(A) || (single && failed(A.one.L))) ? -1 : atomicAdd(A.ctr + 1, 1);
             if (w >= A.n_tc_items) w = -1;
             TcItem m;
@@ -1330,6 +1332,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                 } else {
                     fence_proxy_async_global();
                 }
+                if (A.trace) tq1 = gtimer();
             }
             ring[t % RING] = (int)w;
             mbar_arrive(RFULL(t % RING));
@@ -1372,6 +1375,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                     for (int s = 0; s < nbq; ++s)
                         tma_load_3d(smem_u32(sbase + TC_HA * TC_A_BYTES + s * TC_B_BYTES), map_b, kc * TC_BK,
                                     m.nc * TC_BN, sb + NPL + s, full);
+                    if (A.trace && kc == 0) trace_put(A, 16, m.k, m.i, m.j, m.rem, tq0, tq1, gtimer());
                 }
             } else {
                 for (int h = 0; h < m.nh && ok; ++h) {
@@ -1430,10 +1434,12 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
         for (int tc = 0;; ++tc) {
             // the first stage of the item carries the item id (or the end marker)
             const int st0 = it % TC_STAGES;
+            const long long tm0 = A.trace ? gtimer() : 0;   // trace: waiting for the item, first stage in
             if (!dwait(A, FULL(st0), (it / TC_STAGES) & 1, abort_flag)) {
                 bail(34);
                 break;
             }
+            const long long tm1 = A.trace ? gtimer() : 0;
             const int w = ring[tc % RING];
             if (w < 0) break;   // end marker (the epilogue reads it from the ring)
             const TcItem m = tc_decode(A, w);
@@ -1505,6 +1511,7 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                 if (b) ++use1;
                 else ++use0;
                 nxt ^= 1;
+                if (A.trace) trace_put(A, 15, m.k, m.i, m.j, m.rem, tm0, tm1, gtimer());
             } else {
                 for (int h = 0; h < m.nh && ok; ++h)
                     for (int kp = 0; kp < nkp && ok; ++kp) {
