@@ -1469,20 +1469,21 @@ __device__ void tc_worker(const DagArgs& A, const CUtensorMap* tmap_a, const CUt
                         break;
                     }
                     if (m.fp == 0) {
+                        // descriptors from the stage's one: a shared-memory offset of
+                        // o bytes adds o / 16 to it (addresses stay below 2^18 bytes)
+                        constexpr int PA[TC_HPAIRS] = {0, 1, 0, 2, 0, 1};   // the six pairs (tc_common.cuh)
+                        constexpr int PB[TC_HPAIRS] = {0, 3, 2, 0, 1, 0};
+                        const uint64_t da = sw64_desc(sbase);
+                        const uint64_t db = da + (uint64_t)((TC_HA * TC_A_BYTES) >> 4);
+                        const uint32_t later = kc != 0;
 #pragma unroll
-                        for (int q = 0; q < TC_HPAIRS; ++q) {
-                            const uint32_t a_addr = sbase + c_hpair_a[q] * TC_A_BYTES;
-                            const uint32_t b_addr = sbase + TC_HA * TC_A_BYTES + c_hpair_b[q] * TC_B_BYTES;
+                        for (int q = 0; q < TC_HPAIRS; ++q)
 #pragma unroll
-                            for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                                if (q == 0)
-                                    umma_bf16(dst0, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
-                                              (kc | kk) != 0, TC_IDESC_F16);
-                                else
-                                    umma_bf16(dst1, sw64_desc(a_addr + kk * 32), sw64_desc(b_addr + kk * 32),
-                                              (kc | (q - 1) | kk) != 0, TC_IDESC_F16);
-                            }
-                        }
+                            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                                umma_bf16(q == 0 ? dst0 : dst1,
+                                          da + (uint64_t)((PA[q] * TC_A_BYTES + kk * 32) >> 4),
+                                          db + (uint64_t)((PB[q] * TC_B_BYTES + kk * 32) >> 4),
+                                          later | (uint32_t)((q > 1) | (kk > 0)), TC_IDESC_F16);
                     } else {
                         // far tier: a0 b0 -> acc0; with three products a0 b1 + a1 b0 -> acc1
                         const uint32_t a0 = sbase, a1 = sbase + TC_A_BYTES;

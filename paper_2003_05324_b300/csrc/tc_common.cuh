@@ -36,11 +36,12 @@ __constant__ int c_pair_b[TC_NPAIRS] = {0, 3, 2, 1, 0, 2, 1, 0, 1, 0};
 // (|a0|, |b0| <= 128) sums exactly in FP32 for K <= 1024 (below 2^24); the
 // bracket, 2^-12 below it, goes to the second accumulator, smallest weights
 // first.  The epilogue forms acc0 + 2^-12 acc1.
+// The six (A plane, B plane) pairs, in issue order: (0,0) -> acc0; (1,3),
+// (0,2), (2,0), (0,1), (1,0) -> acc1 (the MMA thread spells them out with
+// compile-time shared-memory offsets).
 constexpr int TC_HA = 3, TC_HB = 4, TC_HPAIRS = 6;
 constexpr uint32_t TC_H_STAGE_BYTES = TC_HA * TC_A_BYTES + TC_HB * TC_B_BYTES;
 static_assert(TC_H_STAGE_BYTES <= (uint32_t)TC_STAGE_BYTES, "FP16 stage");
-__constant__ int c_hpair_a[TC_HPAIRS] = {0, 1, 0, 2, 0, 1};
-__constant__ int c_hpair_b[TC_HPAIRS] = {0, 3, 2, 0, 1, 0};
 
 // ---- FP64-accurate products for in-band (FP64) targets ("EX" items).
 // Seven slices a_0..a_6 per operand (|a_s| <= 128, 56 bits below the row
