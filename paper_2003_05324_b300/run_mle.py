@@ -1,14 +1,21 @@
 """Maximum likelihood estimation on a synthetic dataset from the command line.
 
     python -m paper_2003_05324_b300.run_mle --m 360 --nb 720 --band 3 --nu 1.0 \
-        --beta 0.03 --nugget 1e-8 --evals 60
+        --beta 0.03 --nugget 1e-8 --evals 60 --fp64-mle
 
 m x m jittered grid (seed 0) in Morton order; measurements simulated from the
 Matern field with the given (sigma2, beta, nu) and nugget by random Fourier
 features (seed 1); the Nelder-Mead estimator (geo_mle) from
 theta0 = (0.5, 0.05, 0.5) with the given evaluation budget.  Prints one JSON
-line: theta-hat, l(theta-hat), evaluations, wall time per evaluation, and the
-arithmetic (band, tile, in-band updates on the tensor cores or the FP64 pipe).
+line per estimate as soon as it is done: theta-hat, l(theta-hat), evaluations,
+wall time per evaluation, and the arithmetic (band, tile, in-band updates on
+the tensor cores or the FP64 pipe).
+
+--fp64-mle then runs the same estimator, same start and budget, with every tile
+FP64 (the all-FP64 GPU path, FP64-accurate tensor-core updates) and prints the
+relative distance of the mixed-precision theta-hat to it, parameter by
+parameter (Section IV-C's comparison of the two estimates at a matched
+evaluation budget).  --out appends every JSON line to a file.
 """
 import argparse
 import json
@@ -33,45 +40,77 @@ def main():
     ap.add_argument("--dmma", action="store_true")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="after the estimate, evaluate l at theta-hat and theta-true with every tile FP64")
+    ap.add_argument("--fp64-mle", action="store_true",
+                    help="also run the estimator with every tile FP64 and compare the two estimates")
+    ap.add_argument("--out", default=None, help="append the JSON lines to this file")
     a = ap.parse_args()
+
+    def emit(rec):
+        line = json.dumps(rec)
+        print(line, flush=True)
+        if a.out:
+            with open(a.out, "a") as fh:
+                fh.write(line + "\n")
+
     x, y = inputs.jittered_grid(a.m, seed=0)
     perm = geo.morton_order(x, y)
     x, y = x[perm], y[perm]
     z = inputs.matern_field_rff(x, y, a.sigma2, a.beta, a.nu, seed=1, nugget=a.nugget)
     X, Y, Z = (torch.as_tensor(v, device="cuda") for v in (x, y, z))
     n = len(z)
-    ts = geo.TileStore(n, a.nb, a.band, geo.GEO_LP_SPLIT_BF16)
-    if a.dmma:
-        ts.set_flags(geo.GEO_FLAG_FP64_DMMA)
     th0 = geo.Theta(0.5, 0.05, 0.5, a.nugget)
     th_true = geo.Theta(a.sigma2, a.beta, a.nu, a.nugget)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    l_mp_true = ts.loglik(X, Y, Z, th_true)[0]
-    t_eval = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    r = ts.mle(X, Y, Z, th0, max_evals=a.evals, profile=a.profile)
-    wall = time.perf_counter() - t0
-    th = r["theta"]
-    extra = {"seconds_first_eval": t_eval, "loglik_mp_theta_true": l_mp_true,
-             "tflops_per_eval": n ** 3 / 3.0 / (wall / max(r["evals"], 1)) / 1e12}
+
+    def estimate(band, label):
+        ts = geo.TileStore(n, a.nb, band, geo.GEO_LP_SPLIT_BF16)
+        if a.dmma:
+            ts.set_flags(geo.GEO_FLAG_FP64_DMMA)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        l_true = ts.loglik(X, Y, Z, th_true)[0]
+        t_eval = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        r = ts.mle(X, Y, Z, th0, max_evals=a.evals, profile=a.profile)
+        wall = time.perf_counter() - t0
+        th = r["theta"]
+        rec = {"estimate": label, "n": n, "nb": a.nb, "band": ts.band, "seconds_first_eval": t_eval,
+               "loglik_theta_true": l_true, "theta_true": [a.sigma2, a.beta, a.nu, a.nugget],
+               "theta_hat": [th.sigma2, th.beta, th.nu], "loglik": r["loglik"], "evals": r["evals"],
+               "iterations": r["iterations"], "not_spd": r["not_spd"], "seconds": wall,
+               "seconds_per_eval": wall / max(r["evals"], 1),
+               "tflops_per_eval": n ** 3 / 3.0 / (wall / max(r["evals"], 1)) / 1e12, "profile": a.profile,
+               "inband_updates": "fp64 pipe" if a.dmma else "tensor cores (FP64-accurate)"}
+        return ts, rec
+
+    ts, mp = estimate(a.band, "mixed precision")
+    emit(mp)
+    th = mp["theta_hat"]
     if a.compare_fp64:
-        l_mp_hat = r["loglik"]
+        l_mp_hat = mp["loglik"]
         del ts
         torch.cuda.empty_cache()
         t64 = geo.TileStore(n, a.nb, 10 ** 6, geo.GEO_LP_SPLIT_BF16)
         t0 = time.perf_counter()
         l64_true = t64.loglik(X, Y, Z, th_true)[0]
-        extra["seconds_fp64_eval"] = time.perf_counter() - t0
-        l64_hat = t64.loglik(X, Y, Z, geo.Theta(th.sigma2, th.beta, th.nu, a.nugget))[0]
-        extra.update({"loglik_fp64_theta_true": l64_true, "loglik_fp64_theta_hat": l64_hat,
-                      "rel_err_theta_true": abs(l_mp_true - l64_true) / abs(l64_true),
-                      "rel_err_theta_hat": abs(l_mp_hat - l64_hat) / abs(l64_hat)})
-    print(json.dumps({**extra, "n": n, "nb": a.nb, "band": a.band, "theta_true": [a.sigma2, a.beta, a.nu, a.nugget],
-                      "theta_hat": [th.sigma2, th.beta, th.nu], "loglik": r["loglik"], "evals": r["evals"],
-                      "iterations": r["iterations"], "not_spd": r["not_spd"], "seconds": wall,
-                      "seconds_per_eval": wall / max(r["evals"], 1), "profile": a.profile,
-                      "inband_updates": "fp64 pipe" if a.dmma else "tensor cores (FP64-accurate)"}), flush=True)
+        sec64 = time.perf_counter() - t0
+        l64_hat = t64.loglik(X, Y, Z, geo.Theta(th[0], th[1], th[2], a.nugget))[0]
+        emit({"compare": "FP64 likelihood at the mixed-precision estimate", "seconds_fp64_eval": sec64,
+              "loglik_fp64_theta_true": l64_true, "loglik_fp64_theta_hat": l64_hat,
+              "rel_err_theta_true": abs(mp["loglik_theta_true"] - l64_true) / abs(l64_true),
+              "rel_err_theta_hat": abs(l_mp_hat - l64_hat) / abs(l64_hat)})
+        del t64
+    else:
+        del ts
+    torch.cuda.empty_cache()
+    if a.fp64_mle:
+        t64, dp = estimate(10 ** 6, "all tiles FP64")
+        emit(dp)
+        names = ("sigma2", "beta", "nu")
+        emit({"compare": "mixed-precision theta-hat against the all-FP64 theta-hat (same start and budget)",
+              "rel_err": {nm: abs(th[q] - dp["theta_hat"][q]) / abs(dp["theta_hat"][q]) for q, nm in enumerate(names)},
+              "max_rel_err": max(abs(th[q] - dp["theta_hat"][q]) / abs(dp["theta_hat"][q]) for q in range(3)),
+              "same_path": mp["evals"] == dp["evals"] and mp["iterations"] == dp["iterations"],
+              "mp_speedup_per_eval": dp["seconds_per_eval"] / mp["seconds_per_eval"]})
 
 
 if __name__ == "__main__":
