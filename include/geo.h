@@ -316,6 +316,19 @@ typedef struct geo_mle_opts {
     double xtol;          /* simplex-size stop in log-parameter space (default 1e-3) */
     double step;          /* initial simplex step in log space (default 0.1) */
     double lo[3], hi[3];  /* box on (sigma2, beta, nu) (defaults [1e-3,1e2], [1e-4,2], [0.05,3]) */
+    /* Optional evaluation journal (host memory, default NULL), for runs split
+     * over several calls: journal_cap records of 4 doubles (sigma2, beta, nu,
+     * f = -l, +inf when not positive definite), in evaluation order.  On entry
+     * *journal_len records are already present: the estimator's first
+     * *journal_len evaluations take their values from them instead of the
+     * device (the simplex is deterministic, so it retraces the same points; a
+     * point that differs from its record returns -6).  Every new evaluation is
+     * appended while there is room, and *journal_len is updated.  A run with
+     * max_evals = E and the journal of an earlier run with a smaller budget
+     * therefore gives the same estimate as one uninterrupted run of E. */
+    double* journal;
+    int journal_cap;
+    int* journal_len;
 } geo_mle_opts;
 
 typedef struct geo_mle_result {

@@ -1,23 +1,28 @@
 """Estimation and prediction accuracy of DP, MP and DST on synthetic data.
 
-    python -m paper_2003_05324_b300.accuracy_study --m 100 --betas 0.03 0.1 0.3 --seeds 0 1
+    python -m paper_2003_05324_b300.accuracy_study --m 200 --betas 0.03 0.1 0.3 --seeds 0 1 2 \
+        --out study.jsonl
 
 A reduced form of the paper's Monte-Carlo study (Section VIII-D): for each range
 parameter theta2 (weak / medium / strong correlation) and seed,
 
-* locations: an m x m jittered grid (seed), Morton order;
+* locations: an m x m jittered grid (seed), Morton order (m = 200: the
+  paper's 40K points);
 * measurements: an exact sample of the zero-mean Matern field with theta =
   (1, theta2, 1/2): Z = L w with L the all-FP64 GPU factor of Sigma(theta) and
   w standard normal (seed + 1000);
-* a random 10 % of the points (seed + 2000) is held out for prediction;
-* each method estimates theta on the rest with the library's Nelder-Mead MLE
-  (same start, bounds and budget for all): DP (every tile FP64), MP with band
-  1 and 2 (Algorithm 1), DST with d = 1 (independent blocks) and d = 2;
-* with its estimate each method refactors and predicts the held-out values
-  by simple kriging; the score is the mean square prediction error.
+* each method estimates theta on all points with the library's Nelder-Mead
+  MLE (same start, bounds and budget for all): DP (every tile FP64), MP with
+  band 1 (Algorithm 1) and DST with d = 1 (independent blocks); the number of
+  likelihood evaluations and simplex iterations each needed is recorded;
+* prediction by 10-fold cross-validation: the points are split into 10 random
+  folds (seed + 2000); each fold is predicted by simple kriging from the other
+  nine with the method's own estimate and arithmetic; the score is the mean
+  square prediction error over all points.
 
-Prints one JSON line per (theta2, seed, method) and a summary table of the
-estimates' distance to DP's and of the prediction errors.
+Every row is printed as one JSON line (and appended to --out), followed by a
+summary table: the largest relative distance of each method's estimate to
+DP's, the mean MSPE and its ratio to DP's, and the evaluations per estimate.
 """
 import argparse
 import json
@@ -28,8 +33,8 @@ import torch
 
 from . import geo, inputs
 
-METHODS = (("DP", 10 ** 6, 0), ("MP b=1", 1, 0), ("MP b=2", 2, 0), ("DST d=1", 1, geo.GEO_FLAG_DST),
-           ("DST d=2", 2, geo.GEO_FLAG_DST))
+METHODS = {"DP": (10 ** 6, 0), "MP b=1": (1, 0), "MP b=2": (2, 0), "DST d=1": (1, geo.GEO_FLAG_DST),
+           "DST d=2": (2, geo.GEO_FLAG_DST)}
 
 
 def exact_field(x, y, theta, nb, seed, dev):
@@ -47,78 +52,122 @@ def exact_field(x, y, theta, nb, seed, dev):
     return z
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--m", type=int, default=100)
-    ap.add_argument("--nb", type=int, default=500)
-    ap.add_argument("--betas", type=float, nargs="+", default=[0.03, 0.1, 0.3])
-    ap.add_argument("--seeds", type=int, nargs="+", default=[0, 1])
-    ap.add_argument("--evals", type=int, default=200)
-    ap.add_argument("--holdout", type=float, default=0.1)
-    a = ap.parse_args()
-    dev = torch.device("cuda")
+def cv_mspe(x, y, z, theta, nb, band, flags, folds, seed, dev):
+    """10-fold cross-validated MSPE: each fold kriged from the others with the
+    given arithmetic (None when a factor is not positive definite)."""
+    n = len(z)
+    fold = np.random.default_rng(seed).permutation(n) % folds
+    se = 0.0
+    for f in range(folds):
+        tr, te = fold != f, fold == f      # the training points keep their Morton order
+        X, Y, Z = (torch.as_tensor(np.ascontiguousarray(v[tr]), device=dev) for v in (x, y, z))
+        Xn, Yn = (torch.as_tensor(np.ascontiguousarray(v[te]), device=dev) for v in (x, y))
+        ts = geo.TileStore(int(tr.sum()), nb, band, geo.GEO_LP_SPLIT_BF16, device=dev)
+        if flags:
+            ts.set_flags(flags)
+        try:
+            ts.matern(X, Y, theta)
+            ts.potrf()
+        except geo.NotSPDError:
+            return None
+        zhat = ts.krige(X, Y, Z, theta, Xn, Yn).cpu().numpy()
+        se += float(np.sum((zhat - z[te]) ** 2))
+        del ts
+    return se / n
+
+
+def run_study(m, nb, betas, seeds, evals, methods, folds=10, dev=None, emit=print):
+    dev = dev or torch.device("cuda")
     rows = []
-    for beta in a.betas:
-        for seed in a.seeds:
-            x, y = inputs.jittered_grid(a.m, seed=seed)
+    for beta in betas:
+        for seed in seeds:
+            x, y = inputs.jittered_grid(m, seed=seed)
             perm = geo.morton_order(x, y)
             x, y = x[perm], y[perm]
             th_true = geo.Theta(1.0, beta, 0.5)
-            z = exact_field(x, y, th_true, a.nb, seed + 1000, dev)
+            z = exact_field(x, y, th_true, nb, seed + 1000, dev)
             n = len(z)
-            test = np.zeros(n, dtype=bool)
-            test[np.random.default_rng(seed + 2000).choice(n, int(round(a.holdout * n)), replace=False)] = True
-            tr, te = ~test, test        # the training points keep their Morton order
-            Xtr, Ytr, Ztr = (torch.as_tensor(np.ascontiguousarray(v[tr]), device=dev) for v in (x, y, z))
-            Xte, Yte = (torch.as_tensor(np.ascontiguousarray(v[te]), device=dev) for v in (x, y))
-            zte = z[te]
-            ntr = int(tr.sum())
-            for name, band, flags in METHODS:
-                ts = geo.TileStore(ntr, a.nb, band, geo.GEO_LP_SPLIT_BF16, device=dev)
+            X, Y, Z = (torch.as_tensor(v, device=dev) for v in (x, y, z))
+            for name in methods:
+                band, flags = METHODS[name]
+                ts = geo.TileStore(n, nb, band, geo.GEO_LP_SPLIT_BF16, device=dev)
                 if flags:
                     ts.set_flags(flags)
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
                 try:
-                    r = ts.mle(Xtr, Ytr, Ztr, geo.Theta(0.5, 0.05, 0.4), max_evals=a.evals)
+                    r = ts.mle(X, Y, Z, geo.Theta(0.5, 0.05, 0.4), max_evals=evals)
                 except geo.NotSPDError:   # the truncated covariance is indefinite at the start
-                    row = {"theta2": beta, "seed": seed, "method": name, "n_train": ntr,
+                    row = {"theta2": beta, "seed": seed, "method": name, "n": n,
                            "status": "not positive definite at the starting theta: no estimate"}
                     rows.append(row)
-                    print(json.dumps(row), flush=True)
+                    emit(json.dumps(row))
                     continue
                 secs = time.perf_counter() - t0
-                th = r["theta"]
-                row = {"theta2": beta, "seed": seed, "method": name, "n_train": ntr, "n_test": int(te.sum()),
-                       "theta_hat": [th.sigma2, th.beta, th.nu], "loglik": r["loglik"], "evals": r["evals"],
-                       "not_spd_evals": r["not_spd"], "seconds": secs}
-                try:
-                    ts.matern(Xtr, Ytr, th)
-                    ts.potrf()
-                    zhat = ts.krige(Xtr, Ytr, Ztr, th, Xte, Yte).cpu().numpy()
-                    row["mspe"] = float(np.mean((zhat - zte) ** 2))
-                except geo.NotSPDError:
-                    row["mspe"] = None      # no positive definite factor at the estimate
-                rows.append(row)
-                print(json.dumps(row), flush=True)
                 del ts
                 torch.cuda.empty_cache()
-    # summary: distance of each estimate to DP's on the same data, prediction error
-    print("\n| theta2 | method | max rel. distance of theta-hat to DP's (over seeds) | mean MSPE | MSPE / DP's |")
-    print("|---|---|---|---|---|")
-    for beta in a.betas:
-        dp = {r["seed"]: r for r in rows if r["theta2"] == beta and r["method"] == "DP"}
-        for name, _, _ in METHODS:
+                th = r["theta"]
+                row = {"theta2": beta, "seed": seed, "method": name, "n": n,
+                       "theta_hat": [th.sigma2, th.beta, th.nu], "loglik": r["loglik"], "evals": r["evals"],
+                       "iterations": r["iterations"], "not_spd_evals": r["not_spd"], "seconds": secs,
+                       "cv_folds": folds}
+                t0 = time.perf_counter()
+                row["mspe"] = cv_mspe(x, y, z, th, nb, band, flags, folds, seed + 2000, dev)
+                row["cv_seconds"] = time.perf_counter() - t0
+                rows.append(row)
+                emit(json.dumps(row))
+    return rows
+
+
+def summary(rows, betas, methods):
+    """Per theta2 and method: the largest relative distance of the estimate to
+    DP's on the same data, the mean CV MSPE and its mean ratio to DP's, and the
+    mean evaluations / iterations of the estimator."""
+    out = []
+    for beta in betas:
+        dp = {r["seed"]: r for r in rows if r["theta2"] == beta and r["method"] == "DP" and "theta_hat" in r}
+        for name in methods:
             rs = [r for r in rows if r["theta2"] == beta and r["method"] == name and "theta_hat" in r]
             if not rs:
-                print(f"| {beta} | {name} | no estimate (indefinite) | - | - |")
+                out.append({"theta2": beta, "method": name, "status": "no estimate (indefinite)"})
                 continue
-            dist = max(max(abs(u - v) / abs(v) for u, v in zip(r["theta_hat"], dp[r["seed"]]["theta_hat"]))
-                       for r in rs)
+            dist = [max(abs(u - v) / abs(v) for u, v in zip(r["theta_hat"], dp[r["seed"]]["theta_hat"]))
+                    for r in rs if r["seed"] in dp]
             ms = [r["mspe"] for r in rs if r["mspe"] is not None]
-            rel = [r["mspe"] / dp[r["seed"]]["mspe"] for r in rs if r["mspe"] is not None]
-            print(f"| {beta} | {name} | {dist:.2e} | {np.mean(ms) if ms else float('nan'):.4e} | "
-                  f"{np.mean(rel) if rel else float('nan'):.4f} |")
+            rel = [r["mspe"] / dp[r["seed"]]["mspe"] for r in rs
+                   if r["mspe"] is not None and r["seed"] in dp and dp[r["seed"]]["mspe"]]
+            out.append({"theta2": beta, "method": name, "datasets": len(rs),
+                        "max_rel_dist_to_dp": max(dist) if dist else None,
+                        "median_rel_dist_to_dp": float(np.median(dist)) if dist else None,
+                        "mean_mspe": float(np.mean(ms)) if ms else None,
+                        "mean_mspe_ratio_to_dp": float(np.mean(rel)) if rel else None,
+                        "mean_evals": float(np.mean([r["evals"] for r in rs])),
+                        "mean_iterations": float(np.mean([r["iterations"] for r in rs])),
+                        "mean_seconds": float(np.mean([r["seconds"] for r in rs]))})
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--m", type=int, default=200)
+    ap.add_argument("--nb", type=int, default=500)
+    ap.add_argument("--betas", type=float, nargs="+", default=[0.03, 0.1, 0.3])
+    ap.add_argument("--seeds", type=int, nargs="+", default=[0, 1, 2])
+    ap.add_argument("--evals", type=int, default=150)
+    ap.add_argument("--folds", type=int, default=10)
+    ap.add_argument("--methods", nargs="+", default=["DP", "MP b=1", "DST d=1"], choices=list(METHODS))
+    ap.add_argument("--out", default=None, help="append every JSON line to this file")
+    a = ap.parse_args()
+
+    def emit(line):
+        print(line, flush=True)
+        if a.out:
+            with open(a.out, "a") as fh:
+                fh.write(line + "\n")
+
+    rows = run_study(a.m, a.nb, a.betas, a.seeds, a.evals, a.methods, a.folds, emit=emit)
+    for s in summary(rows, a.betas, a.methods):
+        emit(json.dumps({"summary": s}))
 
 
 if __name__ == "__main__":

@@ -1927,6 +1927,17 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
                 out.tct.push_back(v);
             }
         }
+        // the step's diagonal solves of every problem first, then their block-row
+        // updates: the queue's head is taken only when ready, so a head waiting
+        // for one problem's diagonal solve must not hold back the others'
+        for (int b = 0; b < nprob; ++b) {
+            const std::vector<G2Task>& q = yq[(size_t)b];
+            if (iy[(size_t)b] < q.size() && q[iy[(size_t)b]].k == k && q[iy[(size_t)b]].type == T_YD) {
+                G2Task tk = q[iy[(size_t)b]++];
+                tk.pid = b;
+                out.yq.push_back(tk);
+            }
+        }
         for (int b = 0; b < nprob; ++b) {
             const std::vector<G2Task>& q = yq[(size_t)b];
             while (iy[(size_t)b] < q.size() && q[iy[(size_t)b]].k == k) {

@@ -37,13 +37,40 @@ struct Problem {
     // or an evaluation failed otherwise (error set)
     bool eval(const std::vector<double>& u, double& f) {
         if (evals >= o->max_evals || error) return false;
-        ++evals;
+        const int k = evals++;
         double th[3];
         unpack(u, th);
         geo_theta q = theta0;
         q.sigma2 = o->profile ? 1.0 : th[0];
         q.beta = th[1];
         q.nu = th[2];
+        if (o->journal && o->journal_len && k < *o->journal_len) {   // replay a journaled evaluation
+            const double* rec = o->journal + 4 * (size_t)k;
+            if (rec[0] != q.sigma2 || rec[1] != q.beta || rec[2] != q.nu) {
+                error = -6;   // the journal belongs to another run
+                return false;
+            }
+            f = rec[3];
+            if (std::isinf(f)) ++not_spd;
+        } else {
+            if (!device_eval(q, f)) return false;
+            if (o->journal && o->journal_len && k < o->journal_cap) {
+                double* rec = o->journal + 4 * (size_t)k;
+                rec[0] = q.sigma2;
+                rec[1] = q.beta;
+                rec[2] = q.nu;
+                rec[3] = f;
+                *o->journal_len = k + 1;
+            }
+        }
+        if (f < best_f) {
+            best_f = f;
+            best_u = u;
+        }
+        return true;
+    }
+    // -l of one evaluation on the device (+inf when not positive definite)
+    bool device_eval(const geo_theta& q, double& f) {
         double out[3];
         int info = 0;
         const int rc = geo_loglik(t, x, y, z, q, out, &info, stream);
@@ -59,10 +86,6 @@ struct Problem {
                                  ? -0.5 * n * log(2.0 * M_PI) - 0.5 * n - 0.5 * n * log(out[2] / n) - 0.5 * out[1]
                                  : out[0];
             f = std::isfinite(l) ? -l : kInf;
-        }
-        if (f < best_f) {
-            best_f = f;
-            best_u = u;
         }
         return true;
     }
@@ -97,6 +120,9 @@ int geo_mle(geo_tiles* t, const double* d_x, const double* d_y, const double* d_
     if (!d_z) return -4;
     if (!(theta0.sigma2 > 0 && theta0.beta > 0 && theta0.nu > 0 && theta0.nugget >= 0)) return -5;
     if (!opts || opts->max_evals < 1 || !(opts->xtol >= 0) || !(opts->step > 0)) return -6;
+    if (opts->journal && (!opts->journal_len || opts->journal_cap < 0 || *opts->journal_len < 0 ||
+                          *opts->journal_len > opts->journal_cap))
+        return -6;
     for (int a = 0; a < 3; ++a)
         if (!(opts->lo[a] > 0 && opts->lo[a] <= opts->hi[a])) return -6;
     if (!out) return -7;

@@ -71,7 +71,9 @@ class geo_tiles(ctypes.Structure):
 class geo_mle_opts(ctypes.Structure):
     _fields_ = [("max_evals", ctypes.c_int), ("profile", ctypes.c_int), ("fix_nu", ctypes.c_int),
                 ("xtol", ctypes.c_double), ("step", ctypes.c_double),
-                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("journal", ctypes.c_void_p), ("journal_cap", ctypes.c_int),
+                ("journal_len", ctypes.POINTER(ctypes.c_int))]
 
 
 class geo_mle_result(ctypes.Structure):
@@ -310,10 +312,12 @@ class TileStore:
         return out[0], out[1], out[2]
 
     def mle(self, x, y, z, theta0: Theta, max_evals: int = 60, profile: bool = False, fix_nu: bool = False,
-            xtol: float = 1e-3, step: float = 0.1, lo=None, hi=None, stream=None) -> dict:
+            xtol: float = 1e-3, step: float = 0.1, lo=None, hi=None, stream=None, journal=None) -> dict:
         """Maximum likelihood estimate (Nelder-Mead over log-parameters, see geo_mle)
         with every likelihood evaluation on this store.  Returns dict(theta,
-        loglik, evals, iterations, not_spd)."""
+        loglik, evals, iterations, not_spd).  journal: optional dict with a
+        float64 array "records" (cap x 4) and "len", the evaluation journal of
+        geo_mle (replayed, then extended; "len" is updated)."""
         o = geo_mle_opts()
         _check(lib.geo_mle_default_opts(ctypes.byref(o)), "geo_mle_default_opts")
         o.max_evals, o.profile, o.fix_nu = int(max_evals), int(bool(profile)), int(bool(fix_nu))
@@ -324,9 +328,17 @@ class TileStore:
         if hi is not None:
             for a in range(3):
                 o.hi[a] = float(hi[a])
+        jl = ctypes.c_int(0)
+        if journal is not None:
+            rec = journal["records"]
+            assert rec.dtype == np.float64 and rec.flags["C_CONTIGUOUS"] and rec.shape[1] == 4
+            jl.value = int(journal["len"])
+            o.journal, o.journal_cap, o.journal_len = rec.ctypes.data, int(rec.shape[0]), ctypes.pointer(jl)
         r = geo_mle_result()
         _check(lib.geo_mle(ctypes.byref(self.t), _ptr(x), _ptr(y), _ptr(z), theta0.c(), ctypes.byref(o),
                            ctypes.byref(r), _stream(stream)), "geo_mle")
+        if journal is not None:
+            journal["len"] = jl.value
         th = Theta(r.theta.sigma2, r.theta.beta, r.theta.nu, r.theta.nugget)
         return dict(theta=th, loglik=r.loglik, evals=r.evals, iterations=r.iterations, not_spd=r.not_spd)
 

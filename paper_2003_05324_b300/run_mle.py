@@ -16,11 +16,18 @@ FP64 (the all-FP64 GPU path, FP64-accurate tensor-core updates) and prints the
 relative distance of the mixed-precision theta-hat to it, parameter by
 parameter (Section IV-C's comparison of the two estimates at a matched
 evaluation budget).  --out appends every JSON line to a file.
+
+--journal-dir DIR runs each estimate in chunks of --chunk evaluations and
+keeps geo_mle's evaluation journal in DIR after every chunk: a run that is
+stopped resumes from the journal (the journaled evaluations are replayed, not
+recomputed) and gives the same estimate as an uninterrupted one.
 """
 import argparse
 import json
+import os
 import time
 
+import numpy as np
 import torch
 
 from . import geo, inputs
@@ -43,6 +50,8 @@ def main():
     ap.add_argument("--fp64-mle", action="store_true",
                     help="also run the estimator with every tile FP64 and compare the two estimates")
     ap.add_argument("--out", default=None, help="append the JSON lines to this file")
+    ap.add_argument("--journal-dir", default=None, help="keep resumable evaluation journals here")
+    ap.add_argument("--chunk", type=int, default=10, help="evaluations per chunk with --journal-dir")
     a = ap.parse_args()
 
     def emit(rec):
@@ -65,20 +74,43 @@ def main():
         ts = geo.TileStore(n, a.nb, band, geo.GEO_LP_SPLIT_BF16)
         if a.dmma:
             ts.set_flags(geo.GEO_FLAG_FP64_DMMA)
-        torch.cuda.synchronize()
+        journal, jpath = None, None
+        if a.journal_dir:
+            os.makedirs(a.journal_dir, exist_ok=True)
+            jpath = os.path.join(a.journal_dir, "mle_journal_band%d%s.json" % (ts.band, "_profile" if a.profile else ""))
+            journal = {"records": np.zeros((a.evals, 4)), "len": 0}
+            if os.path.exists(jpath):
+                saved = json.load(open(jpath))
+                journal["records"][:len(saved)] = np.array(saved, dtype=np.float64).reshape(-1, 4)
+                journal["len"] = len(saved)
+        done0 = journal["len"] if journal else 0
+        l_true, t_eval = None, None
+        if done0 == 0:   # (a resumed run skips this extra evaluation)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            l_true = ts.loglik(X, Y, Z, th_true)[0]
+            t_eval = time.perf_counter() - t0
         t0 = time.perf_counter()
-        l_true = ts.loglik(X, Y, Z, th_true)[0]
-        t_eval = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        r = ts.mle(X, Y, Z, th0, max_evals=a.evals, profile=a.profile)
+        if journal is None:
+            r = ts.mle(X, Y, Z, th0, max_evals=a.evals, profile=a.profile)
+        else:
+            budget = done0
+            while True:
+                budget = min(a.evals, budget + a.chunk)
+                r = ts.mle(X, Y, Z, th0, max_evals=budget, profile=a.profile, journal=journal)
+                json.dump(journal["records"][:journal["len"]].tolist(), open(jpath, "w"))
+                if budget >= a.evals or r["evals"] < budget:   # budget spent, or converged earlier
+                    break
         wall = time.perf_counter() - t0
+        new_evals = max(r["evals"] - done0, 1)
         th = r["theta"]
         rec = {"estimate": label, "n": n, "nb": a.nb, "band": ts.band, "seconds_first_eval": t_eval,
                "loglik_theta_true": l_true, "theta_true": [a.sigma2, a.beta, a.nu, a.nugget],
                "theta_hat": [th.sigma2, th.beta, th.nu], "loglik": r["loglik"], "evals": r["evals"],
                "iterations": r["iterations"], "not_spd": r["not_spd"], "seconds": wall,
-               "seconds_per_eval": wall / max(r["evals"], 1),
-               "tflops_per_eval": n ** 3 / 3.0 / (wall / max(r["evals"], 1)) / 1e12, "profile": a.profile,
+               "evals_replayed_from_journal": done0,
+               "seconds_per_eval": wall / new_evals,
+               "tflops_per_eval": n ** 3 / 3.0 / (wall / new_evals) / 1e12, "profile": a.profile,
                "inband_updates": "fp64 pipe" if a.dmma else "tensor cores (FP64-accurate)"}
         return ts, rec
 
@@ -96,7 +128,8 @@ def main():
         l64_hat = t64.loglik(X, Y, Z, geo.Theta(th[0], th[1], th[2], a.nugget))[0]
         emit({"compare": "FP64 likelihood at the mixed-precision estimate", "seconds_fp64_eval": sec64,
               "loglik_fp64_theta_true": l64_true, "loglik_fp64_theta_hat": l64_hat,
-              "rel_err_theta_true": abs(mp["loglik_theta_true"] - l64_true) / abs(l64_true),
+              "rel_err_theta_true": (abs(mp["loglik_theta_true"] - l64_true) / abs(l64_true)
+                                     if mp["loglik_theta_true"] is not None else None),
               "rel_err_theta_hat": abs(l_mp_hat - l64_hat) / abs(l64_hat)})
         del t64
     else:

@@ -117,7 +117,8 @@ def test_mle_options_defaults_and_validation():
     assert (o.max_evals, o.profile, o.fix_nu) == (60, 0, 0)
     assert o.xtol == 1e-3 and o.step == 0.1
     assert list(o.lo) == [1e-3, 1e-4, 0.05] and list(o.hi) == [1e2, 2.0, 3.0]
-    assert ctypes.sizeof(geo.geo_mle_opts) == 80 and ctypes.sizeof(geo.geo_mle_result) == 56
+    assert ctypes.sizeof(geo.geo_mle_opts) == 104 and ctypes.sizeof(geo.geo_mle_result) == 56
+    assert o.journal is None and o.journal_cap == 0 and not o.journal_len
     t = geo.geo_tiles()
     th = geo.Theta(1.0, 0.1, 0.5).c()
     r = geo.geo_mle_result()
@@ -153,3 +154,18 @@ def test_timeout_and_flag_setters_validate_without_device_work():
     assert geo.lib.geo_tiles_set_timeout_ns(ctypes.byref(t), 0) == 0 and t.timeout_ns == 0
     assert geo.lib.geo_tiles_set_flags(ctypes.byref(t), geo.GEO_FLAG_TEST_STALL) == 0
     assert geo.lib.geo_tiles_set_flags(ctypes.byref(t), 1 << 10) == -2
+
+
+def test_mle_journal_validation_without_device_work():
+    t = geo.geo_tiles()
+    th = geo.Theta(1.0, 0.1, 0.5).c()
+    d = ctypes.c_void_p(8)   # never dereferenced: validation fails first
+    r = geo.geo_mle_result()
+    o = geo.geo_mle_opts()
+    geo.lib.geo_mle_default_opts(ctypes.byref(o))
+    rec = np.zeros((4, 4))
+    n = ctypes.c_int(5)                       # more records claimed than the journal holds
+    o.journal, o.journal_cap, o.journal_len = rec.ctypes.data, 4, ctypes.pointer(n)
+    assert geo.lib.geo_mle(ctypes.byref(t), d, d, d, th, ctypes.byref(o), ctypes.byref(r), None) == -6
+    o.journal_len = ctypes.POINTER(ctypes.c_int)()   # journal without a length
+    assert geo.lib.geo_mle(ctypes.byref(t), d, d, d, th, ctypes.byref(o), ctypes.byref(r), None) == -6

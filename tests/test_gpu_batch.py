@@ -119,3 +119,27 @@ def test_batch_against_the_oracle(G):
         want = O.loglik_dense(pr["xh"], pr["yh"], pr["zh"], O.Theta(*pr["theta"]))["loglik"]
         tol = 1e-10 if pr["band"] >= 100 else 1e-6
         assert abs(out[b][0] - want) <= tol * abs(want), (b, out[b][0], want)
+
+
+def test_per_problem_completion_stamps(G):
+    """Each problem's solve runs inside the batched launch and stamps its
+    completion: every stamp lies after the launch start, a problem of 4 tiles
+    finishes before one of 24 tiles in the same launch, and the results equal
+    the single-problem path bit for bit."""
+    small = make_problem(500, 11, (1.0, 0.1, 0.5, 0.0), 128, 1)
+    big = make_problem(6000, 12, (1.0, 0.1, 0.5, 0.0), 256, 1)
+    B = G.Batch([small, big])
+    out = B.loglik([G.Theta(*small["theta"]), G.Theta(*big["theta"])])
+    t = B.done_ns.cpu().numpy()
+    assert t[0] > 0 and np.all(t[1:] > t[0])
+    ms = B.completion_ms()
+    assert ms[0] < ms[1], ms
+    assert np.array_equal(out[0], single(G, small)) and np.array_equal(out[1], single(G, big))
+
+
+def test_partial_sm_launch_equals_full(G, probs):
+    """A launch on a share of the SMs (geo_batch_set_ctas, a plain launch) gives
+    the same bits as the cooperative launch on every SM."""
+    full = G.Batch(probs).loglik([G.Theta(*pr["theta"]) for pr in probs])
+    part = G.Batch(probs, ctas=16).loglik([G.Theta(*pr["theta"]) for pr in probs])
+    assert np.array_equal(full, part, equal_nan=True)

@@ -4,14 +4,16 @@
   theta0 and budget, the two objectives agree to ~1e-13, so the evaluation and
   iteration counts are equal and theta-hat agrees to 1e-9 (full and profiled
   likelihood; FP64 pipe and tensor-core FP64 updates).
-* The mixed-precision estimate is within 1e-3 (relative, every parameter) of
-  the FP64 estimate at n = 1,600, both run to convergence (the stated MLE
-  gate), as the median over five datasets: on any one dataset the FP32
-  rounding noise of the likelihood surface moves the optimum along the
-  sigma2-beta ridge by a random amount of about that size.  At n = 6,400 the
-  noise moves it by up to ~1e-2 (measured 2e-3 .. 1e-2 for every band <= 4,
-  full and profiled), so there the check is 1e-2: the gate is a property of
-  the method at the smaller size only.
+* The mixed-precision estimate against the FP64 estimate, both run to
+  convergence, dataset by dataset against the oracle's own Algorithm 1
+  (tests/golden/mle_alg1.json, oracle calls only).  The FP32 storage of the
+  off-band tiles leaves the likelihood surface with rounding noise that moves
+  the optimum along the sigma2-beta ridge: the oracle's Algorithm 1 moves it by
+  up to 2.3e-3 on single datasets at n = 1,600 (median 8e-4) and by up to 5e-3
+  at n = 6,400 (median 2.2e-3).  So each dataset's GPU deviation must stay
+  within three times the oracle's deviation on the same dataset (plus 1e-3),
+  and the median over datasets within the stated 1e-3 gate at n = 1,600 and
+  within twice the oracle's median at n = 6,400.
 * 1D Markov data: the FP64 GPU estimate equals the closed-form argmax.
 """
 import math
@@ -65,16 +67,19 @@ def test_fp64_mle_follows_the_oracle(G, profile, updates):
     assert rel(got["loglik"], want["loglik"]) <= 1e-11
 
 
-@pytest.mark.parametrize("m,nb,profile,tol,seeds", [(40, 200, False, 1e-3, (5, 6, 7, 8, 9)),
-                                                     (40, 200, True, 1e-3, (5, 6, 7, 8, 9)),
-                                                     (80, 400, False, 1e-2, (5, 6, 7))])
-def test_mixed_precision_mle_matches_fp64(G, m, nb, profile, tol, seeds):
-    """The FP32 storage of the off-band tiles leaves the likelihood surface with
-    rounding noise, and the optimum moves along the sigma2-beta ridge by a
-    random amount of the order of the gate on any one dataset (the oracle's own
-    Algorithm 1 behaves the same way): the median deviation over several
-    datasets is checked."""
-    devs = []
+def _golden_mle():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "mle_alg1.json")))
+    return {(c["m"], c["profile"], c["seed"]): max(c["rel_dev"]) for c in g["cases"]}
+
+
+@pytest.mark.parametrize("m,nb,profile,seeds", [(40, 200, False, (5, 6, 7, 8, 9)),
+                                                (40, 200, True, (5, 6, 7, 8, 9)),
+                                                (80, 400, False, (5, 6, 7))])
+def test_mixed_precision_mle_matches_fp64(G, m, nb, profile, seeds):
+    golden = _golden_mle()
+    devs, alg1 = [], []
     for seed in seeds:
         x, y, z = grid_problem(m, seed, (1.0, 0.1, 0.5))
         X, Y, Z = dev(x), dev(y), dev(z)
@@ -82,9 +87,17 @@ def test_mixed_precision_mle_matches_fp64(G, m, nb, profile, tol, seeds):
         kw = dict(max_evals=500, xtol=1e-7, profile=profile)
         ref = G.TileStore(m * m, nb, 100, G.GEO_LP_SPLIT_BF16).mle(X, Y, Z, th0, **kw)   # all tiles FP64
         mp = G.TileStore(m * m, nb, 1, G.GEO_LP_SPLIT_BF16).mle(X, Y, Z, th0, **kw)
-        devs.append([rel(getattr(mp["theta"], a), getattr(ref["theta"], a)) for a in ("sigma2", "beta", "nu")])
-    med = np.median(np.array(devs), axis=0)
-    assert np.all(med <= tol), (med, devs)
+        d = max(rel(getattr(mp["theta"], a), getattr(ref["theta"], a)) for a in ("sigma2", "beta", "nu"))
+        a1 = golden[(m, profile, seed)]
+        devs.append(d)
+        alg1.append(a1)
+        assert d <= 3.0 * a1 + 1e-3, (seed, d, a1)
+    med = float(np.median(devs))
+    if m == 40:
+        assert med <= 1e-3, (devs, alg1)
+    else:
+        assert med <= 2.0 * float(np.median(alg1)), (devs, alg1)
+    print(f"n={m * m} profile={profile}: GPU deviations {devs}, oracle Algorithm 1 deviations {alg1}")
 
 
 def _ar1_field(x, sigma2, beta, seed):
@@ -126,3 +139,31 @@ def test_fp64_mle_markov_1d_closed_form(G):
                  fix_nu=True)
     assert rel(got["theta"].beta, b_hat) <= 1e-6
     assert rel(got["theta"].sigma2, s2_hat) <= 1e-6
+
+
+def test_mle_journal_resume_equals_one_run(G):
+    """geo_mle's evaluation journal: the estimate run in chunks of 15
+    evaluations, each chunk replaying the journal of the previous ones, ends at
+    the same theta-hat (bit for bit), with the same evaluation and iteration
+    counts, as one uninterrupted run; a journal from another run is refused."""
+    x, y, z = grid_problem(20, 3, (1.0, 0.1, 0.5))       # n = 400
+    X, Y, Z = dev(x), dev(y), dev(z)
+    th0 = G.Theta(0.5, 0.05, 0.5)
+    ts = G.TileStore(400, 96, 1, G.GEO_LP_SPLIT_BF16)
+    whole = ts.mle(X, Y, Z, th0, max_evals=60)
+    journal = {"records": np.zeros((60, 4)), "len": 0}
+    budget, calls = 0, 0
+    while True:
+        budget = min(60, budget + 15)
+        part = ts.mle(X, Y, Z, th0, max_evals=budget, journal=journal)
+        calls += 1
+        assert journal["len"] == part["evals"]
+        if budget >= 60 or part["evals"] < budget:
+            break
+    assert calls >= 2
+    assert part["theta"] == whole["theta"] and part["loglik"] == whole["loglik"]
+    assert part["evals"] == whole["evals"] and part["iterations"] == whole["iterations"]
+    # a journal of another start point does not match the simplex
+    with pytest.raises(G.GeoError) as ei:
+        ts.mle(X, Y, Z, G.Theta(0.7, 0.05, 0.5), max_evals=60, journal=dict(journal))
+    assert ei.value.code == -6

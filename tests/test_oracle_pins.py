@@ -625,3 +625,38 @@ def test_far_tier_in_algorithm1():
     e1 = np.max(np.abs(L1 - L64))
     e3 = np.max(np.abs(L3 - L64))
     assert e1 < e3 < 2 ** -10
+
+
+# --------------------------- the mixed-precision MLE tolerance (Section IV-C) ---
+def test_algorithm1_mle_deviation_golden():
+    """tests/golden/mle_alg1.json (written by make_mle_alg1.py from oracle calls
+    only) holds, for the datasets of the GPU MLE test, the FP64 estimate and the
+    estimate on the oracle's own Algorithm 1 likelihood (band 1).  Checked here:
+    each stored optimum is an optimum of its own objective against the other's
+    point (recomputed at n = 1,600 for two datasets), and the oracle's
+    Algorithm 1 itself moves theta-hat along the sigma2-beta ridge by more than
+    1e-3 on single datasets (the median stays near 1e-3 at n = 1,600 and grows at
+    n = 6,400): the reason the GPU test compares its deviation dataset by
+    dataset with the oracle's."""
+    import json
+    g = json.load(open(os.path.join(GOLDEN, "mle_alg1.json")))
+    cases = g["cases"]
+    assert {(c["n"], c["profile"]) for c in cases} == {(1600, False), (1600, True), (6400, False)}
+    dev = {(c["n"], c["profile"], c["seed"]): max(c["rel_dev"]) for c in cases}
+    assert max(v for k, v in dev.items() if k[0] == 1600) > 1e-3
+    assert np.median([v for k, v in dev.items() if k[:2] == (1600, False)]) <= 1e-3
+    assert np.median([v for k, v in dev.items() if k[0] == 6400]) > 1e-3
+    for c in cases:   # the deviation lies along the ridge: sigma2 and beta move together, nu much less
+        s2, b, nu = c["rel_dev"]
+        assert nu <= max(s2, b)
+    for seed in (5, 8):
+        c = next(c for c in cases if c["n"] == 1600 and not c["profile"] and c["seed"] == seed)
+        x, y = inputs.jittered_grid(40, seed=seed)
+        perm = O.morton_order(x, y)
+        x, y = x[perm], y[perm]
+        z = inputs.matern_field_rff(x, y, 1.0, 0.1, 0.5, seed=seed + 1)
+        t64, t1 = O.Theta(*c["fp64"]["theta"]), O.Theta(*c["alg1"]["theta"])
+        assert O.loglik_dense(x, y, z, t64)["loglik"] == pytest.approx(c["fp64"]["loglik"], rel=1e-12)
+        assert O.loglik_dense(x, y, z, t64)["loglik"] >= O.loglik_dense(x, y, z, t1)["loglik"]
+        assert O.loglik_mp(x, y, z, t1, 200, 1)["loglik"] == pytest.approx(c["alg1"]["loglik"], rel=1e-12)
+        assert O.loglik_mp(x, y, z, t1, 200, 1)["loglik"] >= O.loglik_mp(x, y, z, t64, 200, 1)["loglik"]
