@@ -79,6 +79,32 @@ def replica_throughput(ms, world, steps, flops_per_eval):
     return world * steps / sec, world * flops_per_eval * steps / sec / 1e12
 
 
+def shard_problems(costs, rank, world):
+    """Indices of the independent problems this rank evaluates: greedy by cost
+    (largest first, to the least loaded rank, ties to the lower rank), so the
+    ranks' shares are disjoint, cover every problem and have near-equal work."""
+    load = [0.0] * world
+    mine = []
+    for b in sorted(range(len(costs)), key=lambda q: (-costs[q], q)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += costs[b]
+        if r == rank:
+            mine.append(b)
+    return sorted(mine)
+
+
+def gather_shards(local, world):
+    """The per-rank batch results of a sharded run, gathered on every rank:
+    (ms of the slowest rank, every problem's completion ms, problems done)."""
+    if world <= 1:
+        return local["ms"], list(local["completion_ms"]), local["problems"]
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, local)
+    return (max(p["ms"] for p in parts), [c for p in parts for c in p["completion_ms"]],
+            sum(p["problems"] for p in parts))
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -419,7 +445,7 @@ def time_batch(geo, B, thetas, reps, dev):
 BATCH_BAND_LADDER = (1, 4, 16, 10 ** 6)   # band tried for a problem that is not positive definite at the previous
 
 
-def run_batch(geo, dev):
+def run_batch(geo, dev, rank=0, world=1):
     """Batched evaluation: the autotuner times one graph-captured evaluation per
     tile size in {64, 128, 256} (band 1) and keeps the fastest; each problem
     that is not positive definite in mixed precision at one band is re-evaluated
@@ -428,7 +454,11 @@ def run_batch(geo, dev):
     factors it."""
     import torch
     probs, thetas = batch_workload(geo, dev)
+    nall = len(probs)
     flops = sum(int(pr["z"].shape[0]) ** 3 / 3.0 for pr in probs)
+    if world > 1:   # independent problems: each rank a disjoint, cost-balanced share
+        mine = shard_problems([int(pr["z"].shape[0]) ** 3 for pr in probs], rank, world)
+        probs, thetas = [probs[b] for b in mine], [thetas[b] for b in mine]
     tune = {}
     for nb in (64, 128, 256):
         B = geo.Batch([dict(pr, nb=nb, band=1) for pr in probs], device=dev)
@@ -458,8 +488,11 @@ def run_batch(geo, dev):
     dms, _, ddone = time_batch(geo, D, thetas, 3, dev)
     del D
     torch.cuda.empty_cache()
-    good = completion[np.isfinite(completion)]
-    return {"workload": "256 datasets, n ~ U[500, 8000] uniform locations, sigma2 ~ U[0.5, 2], beta ~ U[0.02, 0.3], "
+    ms_all, comp_all, nprob_all = gather_shards(
+        {"ms": t_total, "completion_ms": completion[np.isfinite(completion)].tolist(), "problems": len(probs)}, world)
+    good = np.array(comp_all)
+    t_total = ms_all
+    return {"ranks": world, "problems": nprob_all, "workload": "256 datasets, n ~ U[500, 8000] uniform locations, sigma2 ~ U[0.5, 2], beta ~ U[0.02, 0.3], "
                         "nu in {1/2, 1, 3/2}; one graph-captured evaluation = generation + one persistent launch "
                         "(factorization, forward solve, log-det and Eq. 2 of every problem)",
             "autotune_ms_by_tile": tune, "tile": nb, "band_stages": stages,
@@ -468,7 +501,7 @@ def run_batch(geo, dev):
             "unfactored": len(todo), "ms_per_batch": t_total,
             "per_problem_completion_p50_ms": float(np.percentile(good, 50)) if good.size else None,
             "per_problem_completion_p99_ms": float(np.percentile(good, 99)) if good.size else None,
-            "evals_per_s": len(probs) / (t_total / 1000.0), "tflops": flops / (t_total / 1000.0) / 1e12,
+            "evals_per_s": nall / (t_total / 1000.0), "tflops": flops / (t_total / 1000.0) / 1e12,
             "fp64_ms": statistics.median(dms), "fp64_evals_per_s": len(probs) / (statistics.median(dms) / 1000.0),
             "fp64_per_problem_completion_p50_ms": float(np.nanpercentile(ddone, 50)),
             "fp64_per_problem_completion_p99_ms": float(np.nanpercentile(ddone, 99)),
@@ -778,7 +811,13 @@ def main():
             far.append(ent)
             del tsf
 
+    # batched problems are independent: with several ranks each evaluates a
+    # disjoint share (every rank takes part in the gather)
+    batch = run_batch(geo, dev, rank, world) if not args.no_batch else None
+
     if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     p50 = statistics.median(step_ms)
     p99 = sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)]
@@ -816,8 +855,8 @@ def main():
         out["far_tier_sweep"] = far
         ok = [e for e in far if e.get("passes_1e-6_gate")]
         out["far_tier_best"] = min(ok, key=lambda e: e["seconds_per_eval"]) if ok else None
-    if not args.no_batch and world == 1:
-        out["batch"] = run_batch(geo, dev)
+    if batch is not None:
+        out["batch"] = batch
     if not args.no_serve and world == 1:
         out["serving"] = run_serve(geo, dev, args.serve_window)
     print(json.dumps(out), flush=True)

@@ -84,3 +84,41 @@ def test_dag_traffic_is_keyed_by_the_kernel_sources():
     assert h == bench.dag_source_hash()          # stable
     for key, val in bench.DAG_TRAFFIC.items():
         assert len(key) == 16 and val > 0
+
+
+def _shard_rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    costs = [float(n) ** 3 for n in (500, 8000, 3000, 3000, 700, 6000, 1200)]
+    mine = bench.shard_problems(costs, rank, world)
+    local = {"ms": 100.0 + 10 * rank, "completion_ms": [float(b) for b in mine], "problems": len(mine)}
+    q.put((rank, mine, bench.gather_shards(local, world)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_batch_shards_are_disjoint_balanced_and_gathered():
+    """Batched problems are independent units: each rank takes a disjoint,
+    cost-balanced share, and every rank gathers the slowest rank's time and
+    every problem's completion."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_rank, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    out = sorted(q.get(timeout=120) for _ in range(world))
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    shares = [o[1] for o in out]
+    assert sorted(shares[0] + shares[1]) == list(range(7)) and not set(shares[0]) & set(shares[1])
+    costs = [float(n) ** 3 for n in (500, 8000, 3000, 3000, 700, 6000, 1200)]
+    work = [sum(costs[b] for b in sh) for sh in shares]
+    assert max(work) <= sum(costs) / world + max(costs)          # the greedy's bound
+    assert shares[0] == [1]                                      # the largest problem alone on one rank
+    for _, _, (ms, comp, nprob) in out:
+        assert ms == 110.0 and nprob == 7 and sorted(comp) == [float(b) for b in range(7)]
