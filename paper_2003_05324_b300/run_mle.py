@@ -21,6 +21,11 @@ evaluation budget).  --out appends every JSON line to a file.
 keeps geo_mle's evaluation journal in DIR after every chunk: a run that is
 stopped resumes from the journal (the journaled evaluations are replayed, not
 recomputed) and gives the same estimate as an uninterrupted one.
+
+--mp-record FILE takes the mixed-precision estimate from a JSON line that an
+earlier run wrote (the first line of FILE whose "estimate" is "mixed
+precision" and whose n, nb and band match) instead of running it again, so
+the all-FP64 estimate can run on its own.
 """
 import argparse
 import json
@@ -52,6 +57,7 @@ def main():
     ap.add_argument("--out", default=None, help="append the JSON lines to this file")
     ap.add_argument("--journal-dir", default=None, help="keep resumable evaluation journals here")
     ap.add_argument("--chunk", type=int, default=10, help="evaluations per chunk with --journal-dir")
+    ap.add_argument("--mp-record", default=None, help="take the mixed-precision estimate from this JSON-lines file")
     a = ap.parse_args()
 
     def emit(rec):
@@ -114,8 +120,20 @@ def main():
                "inband_updates": "fp64 pipe" if a.dmma else "tensor cores (FP64-accurate)"}
         return ts, rec
 
-    ts, mp = estimate(a.band, "mixed precision")
-    emit(mp)
+    if a.mp_record:
+        mp, ts = None, None
+        for line in open(a.mp_record):
+            rec = json.loads(line)
+            if rec.get("estimate") == "mixed precision" and (rec["n"], rec["nb"], rec["band"]) == (n, a.nb, a.band):
+                mp = rec
+                break
+        if mp is None:
+            raise SystemExit("no mixed-precision estimate for n=%d nb=%d band=%d in %s" % (n, a.nb, a.band, a.mp_record))
+        if a.compare_fp64:
+            raise SystemExit("--compare-fp64 needs the mixed-precision store: run without --mp-record")
+    else:
+        ts, mp = estimate(a.band, "mixed precision")
+        emit(mp)
     th = mp["theta_hat"]
     if a.compare_fp64:
         l_mp_hat = mp["loglik"]
