@@ -157,6 +157,10 @@ typedef struct geo_trace_rec {
 #define GEO_FLAG_TEST_STALL 16
 /* Default bound of a device-side wait of the persistent scheduler. */
 #define GEO_DEFAULT_TIMEOUT_NS 10000000000LL
+/* Fewest CTAs a partial launch (geo_batch_set_ctas) may use: three CUDA-core
+ * groups carry a diagonal tile's two chain tasks and the sub-tasks those wait
+ * for, and one more serves the FP64 bulk queue. */
+#define GEO_MIN_CTAS 4
 
 /* A1, "appropriate ordering" (Section VI): Z-order permutation of n locations.
  * Each coordinate c (expected in [0,1]) is quantised to q = clamp(floor(c*2^16),
@@ -377,11 +381,14 @@ int geo_mle(geo_tiles* t, const double* d_x, const double* d_y, const double* d_
  *   the first item's (geo_tiles_set_timeout_ns).
  * geo_batch_set_ctas: run this workspace's factorization launches on `ctas`
  *   CTAs (one per SM at most) instead of one per SM (ctas = 0, the default, a
- *   cooperative launch of every SM).  With 1 <= ctas < SM count the launch is a
- *   plain one: launches on other streams (another batch, kriging) run beside
- *   it on the remaining SMs.  The schedule needs no co-residency (every wait
- *   is on a task already taken by a running worker), so it completes with any
- *   number of resident CTAs.
+ *   cooperative launch of every SM).  With GEO_MIN_CTAS <= ctas < SM count the
+ *   launch is a plain one: launches on other streams (another batch, kriging)
+ *   run beside it on the remaining SMs.  The schedule needs no co-residency
+ *   beyond GEO_MIN_CTAS workers: the queues are claimed in a topological
+ *   order, at most a third of the CUDA-core groups (at least three) work in
+ *   the priority queue while FP64 bulk items exist, and the forward-solve
+ *   queue is taken only when ready, so every wait is on a task a running
+ *   worker holds or can take.  1 <= ctas < GEO_MIN_CTAS is refused (-2).
  * geo_batch_release: forget the workspace's binding (host bookkeeping only;
  *   the caller frees d_work).
  * All return 0, -k for a bad argument k, or GEO_ERR_CUDA. */

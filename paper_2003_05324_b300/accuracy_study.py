@@ -23,6 +23,8 @@ parameter theta2 (weak / medium / strong correlation) and seed,
 Every row is printed as one JSON line (and appended to --out), followed by a
 summary table: the largest relative distance of each method's estimate to
 DP's, the mean MSPE and its ratio to DP's, and the evaluations per estimate.
+With --resume the rows already in --out are kept and only the missing
+(theta2, seed, method) rows are computed; the summary covers all of them.
 """
 import argparse
 import json
@@ -76,11 +78,17 @@ def cv_mspe(x, y, z, theta, nb, band, flags, folds, seed, dev):
     return se / n
 
 
-def run_study(m, nb, betas, seeds, evals, methods, folds=10, dev=None, emit=print):
+def run_study(m, nb, betas, seeds, evals, methods, folds=10, dev=None, emit=print, done=()):
+    """The rows of every (theta2, seed, method) not in `done` (rows of an
+    earlier run, returned with the new ones)."""
     dev = dev or torch.device("cuda")
-    rows = []
+    rows = list(done)
+    have = {(r["theta2"], r["seed"], r["method"]) for r in rows}
     for beta in betas:
         for seed in seeds:
+            todo = [name for name in methods if (beta, seed, name) not in have]
+            if not todo:
+                continue
             x, y = inputs.jittered_grid(m, seed=seed)
             perm = geo.morton_order(x, y)
             x, y = x[perm], y[perm]
@@ -88,7 +96,7 @@ def run_study(m, nb, betas, seeds, evals, methods, folds=10, dev=None, emit=prin
             z = exact_field(x, y, th_true, nb, seed + 1000, dev)
             n = len(z)
             X, Y, Z = (torch.as_tensor(v, device=dev) for v in (x, y, z))
-            for name in methods:
+            for name in todo:
                 band, flags = METHODS[name]
                 ts = geo.TileStore(n, nb, band, geo.GEO_LP_SPLIT_BF16, device=dev)
                 if flags:
@@ -157,7 +165,15 @@ def main():
     ap.add_argument("--folds", type=int, default=10)
     ap.add_argument("--methods", nargs="+", default=["DP", "MP b=1", "DST d=1"], choices=list(METHODS))
     ap.add_argument("--out", default=None, help="append every JSON line to this file")
+    ap.add_argument("--resume", action="store_true", help="keep the rows already in --out, compute the rest")
     a = ap.parse_args()
+    done = []
+    if a.resume and a.out:
+        try:
+            with open(a.out) as fh:
+                done = [r for r in map(json.loads, filter(str.strip, fh)) if "method" in r and "summary" not in r]
+        except FileNotFoundError:
+            pass
 
     def emit(line):
         print(line, flush=True)
@@ -165,7 +181,7 @@ def main():
             with open(a.out, "a") as fh:
                 fh.write(line + "\n")
 
-    rows = run_study(a.m, a.nb, a.betas, a.seeds, a.evals, a.methods, a.folds, emit=emit)
+    rows = run_study(a.m, a.nb, a.betas, a.seeds, a.evals, a.methods, a.folds, emit=emit, done=done)
     for s in summary(rows, a.betas, a.methods):
         emit(json.dumps({"summary": s}))
 

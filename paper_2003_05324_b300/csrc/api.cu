@@ -710,7 +710,7 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
 
 int geo_batch_set_ctas(const void* d_work, int ctas) {
     if (!d_work) return -1;
-    if (ctas < 0) return -2;
+    if (ctas < 0 || (ctas > 0 && ctas < GEO_MIN_CTAS)) return -2;
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto& kv : g_batches)
         if (kv.first == d_work) {

@@ -43,12 +43,18 @@
 //                                          factorization; its head is claimed
 //                                          only once its inputs are final
 // (with the in-band updates on the tensor cores, C(k) and B(k) are empty).
-// At most PRIO_LIMIT CUDA-core groups work in the priority queue at once (its
-// tasks form narrow dependency chains; the others keep the FP64 pipes busy with
-// bulk items), and a bulk item of step k is claimed only after the priority head
-// has passed A(k)'s solves.  Every wait is therefore on a task already taken by
-// a co-resident worker whose own waits resolve earlier: the schedule cannot
-// deadlock.  Failure (non-SPD pivot, timeout) sets the status words; all
+// While a bulk queue exists at most a third of the CUDA-core groups (at least
+// three, at most PRIO_LIMIT) work in the priority queue at once (its tasks form
+// narrow dependency chains; the others keep the FP64 pipes busy with bulk
+// items), and a bulk item of step k is claimed only after the priority head has
+// passed A(k)'s solves.  Every wait is then on a task a running worker holds or
+// can take: PC(k) and PC2(k) wait on sub-tasks queued after them, which a third
+// priority worker takes in order; a priority task of step k+1 may wait on bulk
+// items of step k, which the groups kept out of the priority queue take; tensor
+// items and bulk items wait only on solves already claimed.  With at least
+// GEO_MIN_CTAS = 4 CTAs, co-resident or not, the schedule cannot deadlock (with
+// two, both CUDA-core groups can sit in PC(k) and PC2(k) waiting for sub-tasks
+// no one is left to take).  Failure (non-SPD pivot, timeout) sets the status words; all
 // workers poll them and leave, the tensor group draining its copies and MMAs
 // and freeing tensor memory first.
 #include <math.h>
@@ -1000,6 +1006,8 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
     int* inflight = A.ctr + 3;
     int* y_head = A.ctr + 5;
     __shared__ long long t_claim, t_ready;
+    // groups allowed in the priority queue at once while bulk items exist
+    const int prio_cap = A.n_bulk > 0 ? max(3, min(PRIO_LIMIT, (int)gridDim.x / 3)) : DAG_THREADS * 4096;
     for (;;) {
         // ---- claim: the forward-solve queue's head when its dependencies are
         // met (so it never holds a worker waiting), else the priority queue while
@@ -1021,7 +1029,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 }
                 const int ph = ld_volatile(prio_head);
                 if (ph < A.n_prio) {
-                    if (atomicAdd(inflight, 1) < (A.n_bulk > 0 ? PRIO_LIMIT : DAG_THREADS * 4096)) {
+                    if (atomicAdd(inflight, 1) < prio_cap) {
                         idx = atomicAdd(prio_head, 1);
                         if (idx < A.n_prio) {
                             kind = 0;
@@ -1989,10 +1997,9 @@ cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task*
     prof_begin(4, s);
     if (ctas > 0 && ctas < nsm) {
         // a share of the SMs: a plain launch, so that launches on other streams
-        // run beside it.  The schedule needs no co-residency: a worker waits
-        // only on tasks already taken by running workers (the queues are in
-        // topological order and the solve queue is taken only when ready), so
-        // any number of resident CTAs >= 1 completes it.
+        // run beside it.  The schedule needs no co-residency: with at least
+        // GEO_MIN_CTAS workers (the caller's check) every wait is on a task a
+        // running worker holds or can take.
         e = cudaLaunchKernel(fn, dim3(ctas), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);
     } else {
         e = cudaLaunchCooperativeKernel(fn, dim3(nsm), dim3(DAG_THREADS), args, DAG_DYN_SMEM, s);

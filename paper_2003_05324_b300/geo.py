@@ -32,6 +32,7 @@ GEO_FLAG_FP64_DMMA = 4
 GEO_FLAG_DST = 8
 GEO_FLAG_TEST_STALL = 16
 GEO_DEFAULT_TIMEOUT_NS = 10_000_000_000
+GEO_MIN_CTAS = 4             # fewest CTAs of a partial batch launch (Batch(ctas=...))
 
 
 class GeoError(RuntimeError):

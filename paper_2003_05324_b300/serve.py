@@ -80,7 +80,8 @@ class Server:
         """datasets: list of dicts with host arrays x, y, z (Morton-ordered), the
         theta of the resident kriging factor, optional per-dataset nb and
         krige=False to keep no resident factor (log-likelihood requests only).
-        lanes: concurrent likelihood launches, each on an equal share of the SMs."""
+        lanes: concurrent likelihood launches, each on an equal share of the SMs
+        (at most SM count / GEO_MIN_CTAS lanes)."""
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -107,7 +108,7 @@ class Server:
         self.pool = collections.defaultdict(list)      # dataset -> free stores
         self.allocated = self.resident_bytes           # resident factors + pooled/busy stores + workspaces
         nsm = torch.cuda.get_device_properties(self.device).multi_processor_count
-        self.nlanes = max(1, int(lanes))
+        self.nlanes = max(1, min(int(lanes), nsm // geo.GEO_MIN_CTAS))   # each share >= GEO_MIN_CTAS SMs
         share = [nsm // self.nlanes + (1 if q < nsm % self.nlanes else 0) for q in range(self.nlanes)]
         self.lanes = [dict(stream=torch.cuda.Stream(device=self.device),
                            ctas=0 if self.nlanes == 1 else share[q], inflight=None) for q in range(self.nlanes)]

@@ -107,6 +107,11 @@ def test_entry_points_reject_null_arguments_without_device_work():
     assert L.geo_batch_bind(1, items, None, 0, None) == -2
     assert L.geo_loglik_batch(1, items, None, None, None, None, None) == -3
     assert L.geo_batch_set_ctas(None, 4) == -1
+    fake = ctypes.c_void_p(4096)                   # never bound: looked up only after the argument checks
+    for bad in (-1, 1, geo.GEO_MIN_CTAS - 1):
+        assert L.geo_batch_set_ctas(fake, bad) == -2
+    assert L.geo_batch_set_ctas(fake, geo.GEO_MIN_CTAS) == -1
+    assert L.geo_batch_set_ctas(fake, 0) == -1
     assert L.geo_batch_release(None) == -1
     assert L.geo_mle_default_opts(None) == -1
 

@@ -137,9 +137,18 @@ def test_per_problem_completion_stamps(G):
     assert np.array_equal(out[0], single(G, small)) and np.array_equal(out[1], single(G, big))
 
 
-def test_partial_sm_launch_equals_full(G, probs):
+@pytest.mark.parametrize("ctas", [16, 4])
+def test_partial_sm_launch_equals_full(G, probs, ctas):
     """A launch on a share of the SMs (geo_batch_set_ctas, a plain launch) gives
-    the same bits as the cooperative launch on every SM."""
+    the same bits as the cooperative launch on every SM, down to GEO_MIN_CTAS
+    CTAs, with FP64 bulk items in the batch (the problem with the in-band updates
+    on the FP64 pipe) and without."""
     full = G.Batch(probs).loglik([G.Theta(*pr["theta"]) for pr in probs])
-    part = G.Batch(probs, ctas=16).loglik([G.Theta(*pr["theta"]) for pr in probs])
+    part = G.Batch(probs, ctas=ctas).loglik([G.Theta(*pr["theta"]) for pr in probs])
+    assert not np.isnan(full).any()
+    assert np.array_equal(full, part, equal_nan=True)
+    tensor_only = [pr for pr in probs if not pr["flags"]]
+    assert len(tensor_only) < len(probs)
+    full = G.Batch(tensor_only).loglik([G.Theta(*pr["theta"]) for pr in tensor_only])
+    part = G.Batch(tensor_only, ctas=ctas).loglik([G.Theta(*pr["theta"]) for pr in tensor_only])
     assert np.array_equal(full, part, equal_nan=True)

@@ -44,3 +44,8 @@ def test_study_driver_small(S):
     summ = S.summary(rows, [0.1], ["DP", "MP b=1", "DST d=1"])
     assert {s["method"] for s in summ} == {"DP", "MP b=1", "DST d=1"}
     assert np.isclose(next(s for s in summ if s["method"] == "DP")["mean_mspe_ratio_to_dp"], 1.0)
+    # resuming with every row done computes nothing and returns the same rows
+    again = []
+    rows2 = S.run_study(40, 200, [0.1], [0], 60, ["DP", "MP b=1", "DST d=1"], folds=10, emit=again.append,
+                        done=rows)
+    assert again == [] and rows2 == rows
