@@ -246,11 +246,15 @@ TC_PAIRS_STEPWISE = 10       # BF16 slice products per off-band update (step-by-
 EX_PAIRS = 28                # BF16 slice products per FP64-accurate in-band update
 
 # DRAM bytes (read + write) of one launch of the factorization kernel on this
-# workload (n = 40,000, tile 500, band 1, default flags), from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the
-# kernel's sources: a changed kernel reports null.
+# workload (n = 40,000, tile 500, band 1, default flags), keyed by a hash of the
+# kernel's sources: a changed kernel reports null.  The figure is scaled from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
+# kernel at n = 25,600 (p = 52) by the number of off-band tile updates
+# (p (p^2 - 1) / 6: 23,426 there, 85,320 here): 3.376 MB per update.  The
+# per-update figure falls slowly with size (3.71 / 3.57 / 3.38 MB at
+# p = 13 / 29 / 52), so this slightly overstates the full-size traffic.
 DAG_SOURCES = ("dag.cu", "dag.cuh", "tc_common.cuh", "geo_internal.cuh", "ysolve.cuh")
-DAG_TRAFFIC = {"a7682de87ec2fb56": 156.28e9 + 108.67e9}
+DAG_TRAFFIC = {"086983db711c7931": (46047660288 + 33044942080) / 23426 * 85320}
 
 
 def dag_source_hash():
@@ -395,8 +399,9 @@ def kernel_rows(ts, args, kern):
                 args.lp == "bf16" and not (args.dmma or args.gen64):
             t = DAG_TRAFFIC.get(dag_source_hash())
             roofline["traffic"] = t
-            roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this "
-                                          "kernel build" if t is not None else "no capture of this kernel build")
+            roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel build "
+                                          "at n=25600, scaled by the off-band update count (85320 / 23426)"
+                                          if t is not None else "no capture of this kernel build")
     return rows, roofline
 
 
