@@ -3,16 +3,24 @@
 loglik_n40000.json: the benchmark's workload -- n = 40,000 (200 x 200 jittered
 grid, seed 0, Morton order), Matern sigma2 = 1, beta = 0.1, nu = 0.5, no
 nugget, measurements from the seeded spectral field simulation (seed 1) --
-with the FP64 log-likelihood of Eq. 2 (dense Cholesky) and the oracle's
-Algorithm 1 value for tile 500 and band 1.
+with the FP64 log-likelihood of Eq. 2 and the oracle's Algorithm 1 value for
+tile 500 and band 1.
 
-At this size the oracle's one-shot `covariance` would hold four dense n x n
-arrays at once, so the matrix is assembled from row blocks of the oracle's
-cross-covariance (with no nugget the diagonal entries are C(0) = sigma2 either
-way).  Each value runs in its own process so that at most ~42 GB is held:
+At this size two things differ from the smaller golden script:
 
-    python tests/golden/make_golden_n40000.py          # both, then merge (~20 min on 8 cores)
-    python tests/golden/make_golden_n40000.py dense    # one part, printed as JSON
+* the oracle's one-shot `covariance` would hold four dense n x n arrays at
+  once, so the matrix is assembled from row blocks of the oracle's
+  cross-covariance (with no nugget the diagonal entries are C(0) = sigma2
+  either way);
+* the host LAPACK's dense dpotrf ends in a segmentation fault on a 40,000 x
+  40,000 matrix, so the FP64 factor is the oracle's tile Cholesky with every
+  tile FP64 (Algorithm 1 with band >= p: 500 x 500 LAPACK calls only), which
+  the CPU tests pin to the dense factor.
+
+Each value runs in its own process so that at most ~45 GB is held:
+
+    python tests/golden/make_golden_n40000.py          # both, then merge (~30 min on 8 cores)
+    python tests/golden/make_golden_n40000.py fp64     # one part, printed as JSON
     python tests/golden/make_golden_n40000.py mp
 """
 import json
@@ -55,10 +63,7 @@ def part(which):
     th = O.Theta(*THETA)
     t0 = time.time()
     S = covariance_blocked(x, y, th)
-    if which == "dense":
-        L, info = O.dense_factor(S)
-    else:
-        L, info = O.mp_tile_cholesky(S, NB, BAND)
+    L, info = O.mp_tile_cholesky(S, NB, 10 ** 6 if which == "fp64" else BAND)
     assert info == 0, info
     del S
     ld, q = O.factor_logdet_quad(L, z)
@@ -71,12 +76,12 @@ def main():
         print(json.dumps(part(sys.argv[1])), flush=True)
         return
     res = {}
-    for which in ("dense", "mp"):
+    for which in ("fp64", "mp"):
         out = subprocess.run([sys.executable, os.path.abspath(__file__), which], capture_output=True, text=True,
                              check=True).stdout
         res[which] = json.loads(out.strip().splitlines()[-1])
     n = M * M
-    fp64, mp = res["dense"], res["mp"]
+    fp64, mp = res["fp64"], res["mp"]
     doc = {"n": n, "nb": NB, "theta": list(THETA), "grid": "200x200 jittered, seed 0, Morton",
            "z": "matern_field_rff(sigma2=1, beta=0.1, nu=0.5, seed=1), permuted with the points",
            "fp64": {k: fp64[k] for k in ("loglik", "logdet", "quad")},

@@ -200,3 +200,34 @@ def test_golden_dense_fp64_loglik_n22500(G):
         assert err <= 1e-6, (band, err, alg1)
         del ts
     print("n=22500 |dl|/|l| (GPU mixed precision, oracle Algorithm 1) by band:", report)
+
+
+def test_golden_fp64_loglik_n40000(G):
+    """The benchmark's workload (n = 40,000: 200 x 200 jittered grid, seed 0,
+    Morton order; tile 500) against the oracle's values in
+    tests/golden/loglik_n40000.json (tests/golden/make_golden_n40000.py,
+    oracle calls only): the all-FP64 GPU path meets the 1e-10 gate.  The
+    oracle's own Algorithm 1 (band 1) misses the 1e-6 gate at this size
+    (|dl|/|l| = 3.0e-6: FP32 storage of 97 % of the matrix), so the
+    mixed-precision GPU path is held to the gate or to the oracle's
+    Algorithm 1 error on the same data, whichever is larger."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "loglik_n40000.json")))
+    x, y = inputs.jittered_grid(200, seed=0)
+    z = inputs.matern_field_rff(x, y, 1.0, 0.1, 0.5, seed=1)
+    perm = O.morton_order(x, y)
+    x, y, z = x[perm], y[perm], z[perm]
+    X, Y, Z = dev(x), dev(y), dev(z)
+    th = G.Theta(*g["theta"])
+    want = g["fp64"]["loglik"]
+    ts = G.TileStore(len(z), g["nb"], 10 ** 6, G.GEO_LP_SPLIT_BF16)
+    l = ts.loglik(X, Y, Z, th)[0]
+    assert abs(l - want) <= 1e-10 * abs(want), (l, want)
+    del ts
+    ts = G.TileStore(len(z), g["nb"], 1, G.GEO_LP_SPLIT_BF16)
+    l = ts.loglik(X, Y, Z, th)[0]
+    err = abs(l - want) / abs(want)
+    alg1 = abs(g["mp"]["1"]["loglik"] - want) / abs(want)
+    assert err <= max(1e-6, alg1), (err, alg1)
+    print("n=40000 |dl|/|l|: GPU mixed precision %.3g, oracle Algorithm 1 %.3g" % (err, alg1))
