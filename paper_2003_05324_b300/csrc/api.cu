@@ -675,6 +675,8 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
         P.tmap = (const CUtensorMap*)(base + m.off_maps) + 3 * (size_t)b;
         memcpy(&maps[3 * (size_t)b], t->tmap, 3 * sizeof(CUtensorMap));
         P.z = items[b].d_z;   // the forward solve runs inside the launch
+        P.y0 = plan.ybeg[(size_t)b];
+        P.y1 = plan.ybeg[(size_t)b + 1];
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(base + m.off_probs, probs.data(), sizeof(ProbDev) * probs.size(),

@@ -101,10 +101,11 @@ SchedGeom sched_geom(int p, int nb, int band, int pp, bool ex, bool dst) {
     g.chunks_sp = ceil_div(nb, SP_TRSM_ROWS);
     g.chunks_y = ceil_div(nb, 128);
     // counters: grab counters, upd[p*p], tcnt[p*p], pot[p*ns*ns], sub[p*p*maxitems],
-    // ycnt[p*chunks_y], ydone[p] + the number of finished YD tasks
+    // ycnt[p*chunks_y], ydone[p] + the number of finished YD tasks + the head of
+    // the problem's own solve queue
     g.max_items = std::max(g.items64, g.items_tc);
     g.n_counters = 16 + 2 * (long long)p * p + (long long)p * g.ns * g.ns + (long long)p * p * g.max_items +
-                   (long long)p * g.chunks_y + p + 1;
+                   (long long)p * g.chunks_y + p + 2;
     long long n_prio = 0, n_bulk = 0, n_tct = 0, n_y = 0;
     // with DST, panel tiles (i,k) at i - k >= band are zero: no solve, no
     // update reads them, no forward-solve contribution
@@ -212,6 +213,7 @@ constexpr int DAG_THREADS = TC_THREADS + G2_THREADS;
 constexpr int RING = 8;
 constexpr size_t DAG_DYN_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 512 /*barriers, ring*/;
 
+constexpr int Y_SCAN = 2;       // problems whose solve-queue head a claim attempt looks at
 constexpr int PRIO_LIMIT = 48;   // workers allowed inside priority tasks at once when a bulk queue exists
 
 struct DagArgs {
@@ -1004,7 +1006,9 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
     int* prio_head = A.ctr + 0;
     int* bulk_head = A.ctr + 2;
     int* inflight = A.ctr + 3;
-    int* y_head = A.ctr + 5;
+    int* y_taken = A.ctr + 5;   // forward-solve tasks taken, all problems
+    const int nq = A.probs ? A.nprob : 1;
+    int yrot = (int)blockIdx.x % nq;   // (thread 0) next problem whose solve queue to look at
     __shared__ long long t_claim, t_ready;
     // groups allowed in the priority queue at once while bulk items exist
     const int prio_cap = A.n_bulk > 0 ? max(3, min(PRIO_LIMIT, (int)gridDim.x / 3)) : DAG_THREADS * 4096;
@@ -1019,13 +1023,27 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
             const long long dl = gtimer() + A.wait_ns;
             for (unsigned spin = 0; kind < 0; ++spin) {
                 if (aborted(A) || (!A.probs && failed(A.one.L))) break;
-                const int yh = A.n_y > 0 ? ld_volatile(y_head) : 0;
-                // (a solve task of a failed problem is taken at once and dropped below)
-                if (yh < A.n_y && (failed(prob_of(A, A.yq[yh].pid).L) || y_ready(prob_of(A, A.yq[yh].pid), A.yq[yh])) &&
-                    atomicCAS(y_head, yh, yh + 1) == yh) {
-                    idx = yh;
-                    kind = 2;
-                    break;
+                // each problem has its own solve queue (a segment of yq, taken in
+                // order, its head only when ready); look at Y_SCAN problems per
+                // attempt, in a rotation that starts at this CTA's index, so that
+                // no problem's head waits behind another's.  (A solve task of a
+                // failed problem is taken at once and dropped below.)
+                const int yt = A.n_y > 0 ? ld_volatile(y_taken) : 0;
+                if (yt < A.n_y) {
+                    for (int q = 0; q < min(Y_SCAN, nq) && kind < 0; ++q) {
+                        const int pid = yrot;
+                        yrot = yrot + 1 == nq ? 0 : yrot + 1;
+                        const ProbDev& P = prob_of(A, pid);
+                        const int h = ld_volatile(P.yhead);
+                        if (P.y0 + h >= P.y1) continue;
+                        const G2Task& ty = A.yq[P.y0 + h];
+                        if ((failed(P.L) || y_ready(P, ty)) && atomicCAS(P.yhead, h, h + 1) == h) {
+                            atomicAdd(y_taken, 1);
+                            idx = P.y0 + h;
+                            kind = 2;
+                        }
+                    }
+                    if (kind >= 0) break;
                 }
                 const int ph = ld_volatile(prio_head);
                 if (ph < A.n_prio) {
@@ -1048,7 +1066,7 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                             break;
                         }
                     }
-                } else if (ph >= A.n_prio && yh >= A.n_y) {
+                } else if (ph >= A.n_prio && yt >= A.n_y) {
                     break;   // every queue exhausted
                 }
                 __nanosleep(256);
@@ -1836,6 +1854,7 @@ void bind_counters(ProbDev& P, int* base) {
     P.sub = P.pot + (size_t)p * P.g.ns * P.g.ns;
     P.ycnt = P.sub + (size_t)p * p * P.g.max_items;
     P.ydone = P.ycnt + (size_t)p * P.g.chunks_y;
+    P.yhead = P.ydone + p + 1;   // the problem's own forward-solve queue: tasks taken
 }
 
 cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, const double* z, double* res,
@@ -1856,6 +1875,8 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
     A.yq = z ? sv.yq : nullptr;
     A.n_y = z ? sv.geom.n_y : 0;
     bind_counters(A.one, sv.counters + 16);
+    A.one.y0 = 0;
+    A.one.y1 = (int)A.n_y;
     A.probs = nullptr;
     A.prio = sv.prio;
     A.bulk = sv.bulk;
@@ -1901,11 +1922,11 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
     }
     // every queue of a problem is ordered by step; step k of all problems
     // precedes step k+1 of any (staggering the problems' steps against each
-    // other was measured to make no difference).  The forward-solve queues are
-    // merged the same way: each problem's solve runs inside the launch, and
-    // its result is written as soon as its own last block row is solved.
+    // other was measured to make no difference).  Each problem's solve runs
+    // inside the launch from its own queue, and its result is written as soon
+    // as its own last block row is solved.
     out.yq.clear();
-    std::vector<size_t> ip((size_t)nprob, 0), ib((size_t)nprob, 0), it((size_t)nprob, 0), iy((size_t)nprob, 0);
+    std::vector<size_t> ip((size_t)nprob, 0), ib((size_t)nprob, 0), it((size_t)nprob, 0);
     for (int k = 0; k < pmax; ++k) {
         for (int b = 0; b < nprob; ++b) {
             const std::vector<G2Task>& q = prio[(size_t)b];
@@ -1935,26 +1956,18 @@ void sched_merge(const std::vector<SchedGeom>& g, const std::vector<int>& band, 
                 out.tct.push_back(v);
             }
         }
-        // the step's diagonal solves of every problem first, then their block-row
-        // updates: the queue's head is taken only when ready, so a head waiting
-        // for one problem's diagonal solve must not hold back the others'
-        for (int b = 0; b < nprob; ++b) {
-            const std::vector<G2Task>& q = yq[(size_t)b];
-            if (iy[(size_t)b] < q.size() && q[iy[(size_t)b]].k == k && q[iy[(size_t)b]].type == T_YD) {
-                G2Task tk = q[iy[(size_t)b]++];
-                tk.pid = b;
-                out.yq.push_back(tk);
-            }
-        }
-        for (int b = 0; b < nprob; ++b) {
-            const std::vector<G2Task>& q = yq[(size_t)b];
-            while (iy[(size_t)b] < q.size() && q[iy[(size_t)b]].k == k) {
-                G2Task tk = q[iy[(size_t)b]++];
-                tk.pid = b;
-                out.yq.push_back(tk);
-            }
+    }
+    // the forward-solve queues stay one segment per problem, each taken by its
+    // own head (ybeg[b] .. ybeg[b + 1])
+    out.ybeg.assign((size_t)nprob + 1, 0);
+    for (int b = 0; b < nprob; ++b) {
+        out.ybeg[(size_t)b] = (int)out.yq.size();
+        for (G2Task tk : yq[(size_t)b]) {
+            tk.pid = b;
+            out.yq.push_back(tk);
         }
     }
+    out.ybeg[(size_t)nprob] = (int)out.yq.size();
 }
 
 cudaError_t run_potrf_dag_batch(const ProbDev* d_probs, int nprob, const G2Task* prio, long long n_prio,

@@ -50,7 +50,8 @@ struct SchedView {
 struct ProbDev {
     Layout L;
     SchedGeom g;
-    int *upd, *tcnt, *pot, *sub, *ycnt, *ydone;
+    int *upd, *tcnt, *pot, *sub, *ycnt, *ydone, *yhead;
+    int y0, y1;    // its forward-solve tasks: yq[y0 .. y1)
     const double* z;
     double* res;   // (log|Sigma|, Z' Sigma^-1 Z, Eq. 2) of the fused solve
     const int* trsm_end;
@@ -74,7 +75,8 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
 // merges the problems' queues step by step (each problem keeps its own
 // topological order, so the merge is one too).
 struct BatchPlan {
-    std::vector<G2Task> prio, bulk, yq;   // yq: the problems' forward-solve queues, merged by step
+    std::vector<G2Task> prio, bulk, yq;   // yq: the problems' forward-solve queues, one segment each
+    std::vector<int> ybeg;                // problem b's segment: yq[ybeg[b] .. ybeg[b + 1])
     std::vector<int4> tct;            // (i, j, k, problem)
     std::vector<std::vector<int>> trsm_end;
     int per = 1;                      // tensor items per target (largest over the problems)
