@@ -79,6 +79,30 @@ constexpr int GEN_COLS = 32;
 // theta: from `dth` when given (device memory: batched evaluations), else `th`.
 // With reset_status, the first CTA also clears the problem's status words (the
 // batched path has no separate reset).
+// Tile of grid row t.  The in-band (FP64) tiles, whose entries take the slow
+// FP64 pipe, are spread evenly over the grid instead of following the
+// column-major order, in which the last diagonal tiles crowd the end of the
+// launch onto a few SMs: in-band tile q (diagonal by diagonal) sits at grid
+// row floor(q T / n_dp) of the T rows, and the off-band tiles fill the other
+// rows in column-major order.
+__device__ void gen_tile_of(int t, int p, int band, int& i, int& j) {
+    const long long b = min(band, p);
+    const long long n_dp = b * p - b * (b - 1) / 2, T = (long long)p * (p + 1) / 2;
+    const long long q = ((long long)t * n_dp + T - 1) / T;   // in-band tiles at rows < t
+    if (q < n_dp && (q * T) / n_dp == t) {                     // row t holds in-band tile q
+        long long r = q;
+        int d = 0;
+        while (r >= p - d) { r -= p - d; ++d; }
+        j = (int)r;
+        i = j + d;
+        return;
+    }
+    long long o = t - q;                                       // off-band tile o, column-major
+    j = 0;
+    while (o >= p - j - b) { o -= p - j - b; ++j; }
+    i = j + (int)b + (int)o;
+}
+
 __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, const double* __restrict__ x,
                                                                    const double* __restrict__ y, geo_theta th,
                                                                    const geo_theta* __restrict__ dth,
@@ -93,10 +117,8 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
     __syncthreads();
     const MaternP mp = smp;
     const int nb = L.nb, p = L.p;
-    // decode tile index -> (i, j), lower triangle, column-major over tiles
-    int t = blockIdx.y, j = 0;
-    while (t >= p - j) { t -= p - j; ++j; }
-    const int i = j + t;
+    int i, j;
+    gen_tile_of(blockIdx.y, p, L.band, i, j);
     const int c0 = blockIdx.x * GEN_COLS;
     if (c0 >= nb) return;
     const int cols = min(GEN_COLS, nb - c0);
