@@ -386,6 +386,34 @@ def krige(xo, yo, z, theta: Theta, xn, yn):
     return C @ alpha
 
 
+def krige_dst(xo, yo, z, theta: Theta, xn, yn, nb, d):
+    """Simple kriging under the DST approximation (Section V-B), read so that
+    the new locations are treated like the observed ones: the covariance
+    between a new location s and an observed one is C(||s - s_a||) when the
+    tile of s -- the tile of its nearest observed location (the lowest index
+    on a tie) -- is within d tiles of a's tile, else 0, exactly as
+    dst_covariance truncates the observed covariance.  Z_new = C_dst
+    Sigma_dst^-1 Z with the float64 factor of the truncated matrix.  A new
+    location that coincides with an observed one (no nugget) gets its
+    observation back, for every d."""
+    xo = np.asarray(xo, dtype=np.float64)
+    yo = np.asarray(yo, dtype=np.float64)
+    S = dst_covariance(covariance(xo, yo, theta=theta), nb, d)
+    L, info = dense_factor(S)
+    if info != 0:
+        raise np.linalg.LinAlgError(f"truncated covariance not positive definite (info={info})")
+    yv = sla.solve_triangular(L, np.asarray(z, dtype=np.float64), lower=True)
+    alpha = sla.solve_triangular(L.T, yv, lower=False)
+    xn = np.asarray(xn, dtype=np.float64)
+    yn = np.asarray(yn, dtype=np.float64)
+    C = covariance(xn, yn, xo, yo, theta=theta)
+    r2 = (xn[:, None] - xo[None, :]) ** 2 + (yn[:, None] - yo[None, :]) ** 2
+    home = np.argmin(r2, axis=1) // nb              # argmin takes the lowest index on a tie
+    blk = np.arange(len(xo)) // nb
+    C[np.abs(home[:, None] - blk[None, :]) >= d] = 0.0
+    return C @ alpha
+
+
 # ------------------------------------------------------- profile (Eq. 3) ---
 def profile_sigma2(x, y, z, beta, nu, nugget_ratio=0.0):
     """theta1_opt = Z' S~^-1 Z / n with S~ the covariance at unit variance

@@ -368,6 +368,41 @@ def test_krige_far_point_predicts_zero_mean():
     assert zhat[0] == 0.0
 
 
+def test_krige_dst_interpolates_and_reduces_to_full_kriging():
+    """DST kriging: a new location on an observed one returns its observation
+    for every d; with d covering every tile it is plain kriging."""
+    x, y = inputs.uniform_points(90, seed=24)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.white_noise(90, seed=25)
+    th = O.Theta(1.0, 0.05, 0.5, 0.0)
+    pick = np.array([0, 11, 45, 89])
+    for d in (1, 2, 3):
+        np.testing.assert_allclose(O.krige_dst(x, y, z, th, x[pick], y[pick], 30, d), z[pick], atol=1e-9)
+    xn, yn = inputs.uniform_points(7, seed=26)
+    np.testing.assert_allclose(O.krige_dst(x, y, z, th, xn, yn, 30, 3), O.krige(x, y, z, th, xn, yn),
+                               rtol=1e-12, atol=1e-14)
+
+
+def test_krige_dst_d1_is_kriging_from_the_home_block():
+    """With d = 1 (independent blocks) the prediction at s is ordinary kriging
+    from the observations of the block that holds s's nearest observed point
+    alone."""
+    x, y = inputs.uniform_points(120, seed=27)
+    perm = O.morton_order(x, y)
+    x, y = x[perm], y[perm]
+    z = inputs.white_noise(120, seed=28)
+    th = O.Theta(1.3, 0.1, 1.5, 1e-6)
+    nb = 40
+    xn, yn = inputs.uniform_points(9, seed=29)
+    got = O.krige_dst(x, y, z, th, xn, yn, nb, 1)
+    for q in range(9):
+        a = int(np.argmin((x - xn[q]) ** 2 + (y - yn[q]) ** 2))
+        b = slice((a // nb) * nb, (a // nb + 1) * nb)
+        want = O.krige(x[b], y[b], z[b], th, xn[q:q + 1], yn[q:q + 1])[0]
+        assert abs(got[q] - want) <= 1e-10 * max(1.0, abs(want)), (q, got[q], want)
+
+
 # ------------------------------------------- MLE: the Nelder-Mead simplex ---
 def test_nelder_mead_convex_quadratic():
     a = np.array([0.7, -1.3, 2.1])
