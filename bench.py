@@ -535,8 +535,9 @@ def far_tile_count(x, y, nb, far_band, far_dist):
                 f = f or math.hypot(gx, gy) >= far_dist
             cnt += f
     return cnt, p * (p - 1) // 2
-SERVE_SWEEP_RATES = (2.0, 5.0, 10.0, 20.0, 50.0)
+SERVE_SWEEP_RATES = (2.0, 5.0, 7.0, 10.0, 14.0, 20.0)
 SERVE_SWEEP_WINDOW = 4.0
+SERVE_DRAIN_S = 1.0   # a rate is sustained when the window's requests are all served within this after it
 
 
 def run_serve(geo, dev, window):
@@ -587,19 +588,23 @@ def run_serve(geo, dev, window):
 
     reqs = arrivals(200.0, window, rng)
     results, stats = S.run(reqs, admit_until=window)
-    # arrival-rate sweep (same datasets and request mix, seed 8): the highest
-    # rate at which every request that arrived in the window was served is the
-    # sustainable knee; above it the queue grows with the window
+    # arrival-rate sweep (same datasets and request mix, seed 8): every request
+    # that arrives in the window is served (the queue drains after it); a rate
+    # is sustained when the last of them completes within SERVE_DRAIN_S of the
+    # end of the window -- above the knee the backlog, and with it the drain
+    # time and the latency, grows with the window
     sweep = []
     rng_s = np.random.default_rng(8)
     for rate in SERVE_SWEEP_RATES:
         rq = arrivals(rate, SERVE_SWEEP_WINDOW, rng_s)
         b0 = S.batches
-        _, st = S.run(rq, admit_until=SERVE_SWEEP_WINDOW)
+        _, st = S.run(rq)
         sweep.append({"rate_per_s": rate, "requests": len(rq), "completed": st["completed"],
-                      "queued": st["queued"], "rejected": st["rejected"], "launches": S.batches - b0,
+                      "rejected": st["rejected"], "launches": S.batches - b0,
+                      "drain_s": st["wall_s"] - SERVE_SWEEP_WINDOW,
                       "evals_per_s": st["evals_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"]})
-    ok = [r["rate_per_s"] for r in sweep if r["queued"] == 0 and r["completed"] + r["rejected"] == r["requests"]]
+    ok = [r["rate_per_s"] for r in sweep
+          if r["completed"] + r["rejected"] == r["requests"] and r["drain_s"] <= SERVE_DRAIN_S]
     # kriging accuracy: MSPE of the served (mixed-precision) predictions and of
     # the FP64 path's, against the held-out field values
     mspe = []
@@ -619,7 +624,7 @@ def run_serve(geo, dev, window):
         del ts
     stats.update({"arrival_rate_per_s": 200, "window_s": window, "requests": len(reqs),
                   "datasets_n": ns, "hbm_budget_gb": 120, "kriging_mspe": mspe,
-                  "rate_sweep": sweep, "sweep_window_s": SERVE_SWEEP_WINDOW,
+                  "rate_sweep": sweep, "sweep_window_s": SERVE_SWEEP_WINDOW, "sweep_drain_limit_s": SERVE_DRAIN_S,
                   "sustainable_rate_per_s": max(ok) if ok else None,
                   "note": "offered load exceeds capacity: requests still queued at the end are reported, not served"})
     return stats

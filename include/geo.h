@@ -220,8 +220,9 @@ int geo_tiles_set_far(geo_tiles* t, int far_band, const double* d_x, const doubl
 
 /* A2, Eq. 1: write Sigma_ab = C(||s_a - s_b||; theta) (+ nugget if a == b) into
  * every lower tile, each directly in its own precision (the FP64 -> FP32
- * conversion of Algorithm 1's first loop is fused into generation).
- * d_x, d_y: device FP64[n].  Asynchronous. */
+ * conversion of Algorithm 1's first loop is fused into generation).  The
+ * strictly upper triangle of a diagonal tile, which no later step reads, is
+ * written as 0.  d_x, d_y: device FP64[n].  Asynchronous. */
 int geo_matern_tiles(geo_tiles* t, const double* d_x, const double* d_y, geo_theta theta, void* stream);
 
 /* Scatter a dense symmetric n x n FP64 matrix (device, column-major, ld = n,
@@ -362,12 +363,14 @@ int geo_mle(geo_tiles* t, const double* d_x, const double* d_y, const double* d_
  *
  * geo_batch_workspace: bytes of device workspace for these items (host only).
  * geo_batch_bind: write the merged task queues (factorization and forward
- *   solve), the per-problem views and tensor maps into d_work (blocking).  The
- *   stores' flags are read here.
- * geo_loglik_batch: enqueue one evaluation (asynchronous, nprob + 1 kernel
+ *   solve), the per-problem views, tensor maps and generator table into d_work
+ *   (blocking); GEO_ERR_TOO_LARGE if the problems' generation needs more than
+ *   2^31 - 1 CTAs.  The stores' flags are read here.
+ * geo_loglik_batch: enqueue one evaluation (asynchronous, two kernel
  *   launches and three memsets, no host synchronization, so it can be captured
- *   in a CUDA graph): generation of every problem from d_theta[b] (device
- *   memory: a replay of a captured graph may use new values), then one
+ *   in a CUDA graph): one launch generating every problem's tiles from
+ *   d_theta[b] (device memory: a replay of a captured graph may use new
+ *   values; the problems' CTAs share the launch), then one
  *   persistent launch that factors every problem and runs its forward solve,
  *   log-determinant and assembly as soon as its own factor is ready, writing
  *   d_out[3b .. 3b+2] = (l, log|Sigma|, Z' Sigma^-1 Z) (device FP64[3 nprob]);

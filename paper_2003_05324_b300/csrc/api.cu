@@ -575,8 +575,9 @@ int geo_profile_read(int kind, double* h_ms, long long* h_launches) {
 namespace {
 struct BatchMeta {
     int nprob;
-    size_t off_probs, off_maps, off_tend, off_prio, off_bulk, off_tct, off_y, off_ctr, total;
+    size_t off_probs, off_maps, off_tend, off_prio, off_bulk, off_tct, off_y, off_gen, off_ctr, total;
     long long n_prio, n_bulk, n_tct, n_y;
+    long long gen_blocks;   // CTAs of the batch's one generator launch
     int per;
     size_t counter_bytes;
     int ctas;   // CTAs of the factorization launch (0: one per SM, cooperative)
@@ -624,6 +625,8 @@ int batch_meta(int nprob, const geo_batch_item* items, BatchMeta& m, std::vector
     b = align256(b + sizeof(int4) * (size_t)std::max(m.n_tct, 1LL));
     m.off_y = b;
     b = align256(b + sizeof(G2Task) * (size_t)std::max(m.n_y, 1LL));
+    m.off_gen = b;
+    b = align256(b + sizeof(GenJob) * (size_t)nprob);
     m.off_ctr = b;
     m.counter_bytes = sizeof(int) * (size_t)ctot;
     b = align256(b + m.counter_bytes);
@@ -660,7 +663,9 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
     char* base = (char*)d_work;
     std::vector<ProbDev> probs((size_t)nprob);
     std::vector<CUtensorMap> maps(3 * (size_t)nprob);
+    std::vector<GenJob> gen((size_t)nprob);
     std::vector<int> tend;
+    long long gblk = 0;
     int* ctr = (int*)(base + m.off_ctr) + 16;
     for (int b = 0; b < nprob; ++b) {
         const geo_tiles* t = items[b].t;
@@ -677,7 +682,10 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
         P.z = items[b].d_z;   // the forward solve runs inside the launch
         P.y0 = plan.ybeg[(size_t)b];
         P.y1 = plan.ybeg[(size_t)b + 1];
+        gen[(size_t)b] = {items[b].d_x, items[b].d_y, gblk};
+        gblk += gen_blocks(P.L);
     }
+    if (gblk > 0x7fffffffLL) return GEO_ERR_TOO_LARGE;   // one generator launch holds every problem's CTAs
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(base + m.off_probs, probs.data(), sizeof(ProbDev) * probs.size(),
                                     cudaMemcpyHostToDevice, s);
@@ -697,9 +705,12 @@ int geo_batch_bind(int nprob, const geo_batch_item* items, void* d_work, size_t 
     if (!e && !plan.yq.empty())
         e = cudaMemcpyAsync(base + m.off_y, plan.yq.data(), sizeof(G2Task) * plan.yq.size(),
                             cudaMemcpyHostToDevice, s);
+    if (!e)
+        e = cudaMemcpyAsync(base + m.off_gen, gen.data(), sizeof(GenJob) * gen.size(), cudaMemcpyHostToDevice, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return GEO_ERR_CUDA;
     m.ctas = 0;
+    m.gen_blocks = gblk;
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto& kv : g_batches)
         if (kv.first == d_work) {
@@ -753,13 +764,15 @@ int geo_loglik_batch(int nprob, const geo_batch_item* items, const geo_theta* d_
     }
     cudaStream_t s = (cudaStream_t)stream;
     char* base = (char*)d_work;
-    const geo_theta dummy = {1.0, 1.0, 0.5, 0.0};
     bool small_dp = false;
     for (int b = 0; b < nprob; ++b) {
         const Layout L = make_layout(items[b].t);
         small_dp = small_dp || dag_small_dp(L.nb, L.band);
-        if (launch_matern_tiles(L, items[b].d_x, items[b].d_y, dummy, d_theta + b, 1, s)) return GEO_ERR_CUDA;
     }
+    // every problem's generation in one launch (theta from d_theta[b])
+    if (launch_matern_batch((const ProbDev*)(base + m.off_probs), (const GenJob*)(base + m.off_gen), nprob,
+                            m.gen_blocks, d_theta, s))
+        return GEO_ERR_CUDA;
     if (run_potrf_dag_batch((const ProbDev*)(base + m.off_probs), nprob, (const G2Task*)(base + m.off_prio),
                             m.n_prio, (const G2Task*)(base + m.off_bulk), m.n_bulk,
                             (const int4*)(base + m.off_tct), m.n_tct, m.per, (const G2Task*)(base + m.off_y),

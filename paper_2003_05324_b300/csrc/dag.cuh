@@ -71,6 +71,21 @@ void sched_build(const SchedGeom& g, int band, std::vector<G2Task>& prio, std::v
 cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& sv, const double* z, double* res,
                           cudaStream_t s);
 
+// Batched generation: problem b's coordinates and the index of its first CTA
+// in the one generator launch of a batch (block0 increasing, from 0).
+struct GenJob {
+    const double* x;
+    const double* y;
+    long long block0;
+};
+// CTAs of one problem's generation (column chunks x lower tiles).
+long long gen_blocks(const Layout& L);
+// Generate every problem's tiles (theta of problem b from dth[b], device
+// memory) in one launch of total_blocks CTAs; also clears each problem's
+// status words.
+cudaError_t launch_matern_batch(const ProbDev* d_probs, const GenJob* d_jobs, int nprob, long long total_blocks,
+                                const geo_theta* dth, cudaStream_t s);
+
 // Batched launch: every problem's tasks in one persistent kernel.  The host
 // merges the problems' queues step by step (each problem keeps its own
 // topological order, so the merge is one too).

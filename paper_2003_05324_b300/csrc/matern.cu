@@ -19,6 +19,7 @@
 // are computed in FP32 arithmetic from FP64 coordinate differences.
 #include <math.h>
 
+#include "dag.cuh"
 #include "geo_internal.cuh"
 #include "matern_dev.cuh"
 
@@ -76,9 +77,6 @@ MaternP make_matern(const geo_theta& th) {
 constexpr int GEN_THREADS = 256;
 constexpr int GEN_COLS = 32;
 
-// theta: from `dth` when given (device memory: batched evaluations), else `th`.
-// With reset_status, the first CTA also clears the problem's status words (the
-// batched path has no separate reset).
 // Tile of grid row t.  The in-band (FP64) tiles, whose entries take the slow
 // FP64 pipe, are spread evenly over the grid instead of following the
 // column-major order, in which the last diagonal tiles crowd the end of the
@@ -103,23 +101,12 @@ __device__ void gen_tile_of(int t, int p, int band, int& i, int& j) {
     i = j + (int)b + (int)o;
 }
 
-__global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, const double* __restrict__ x,
-                                                                   const double* __restrict__ y, geo_theta th,
-                                                                   const geo_theta* __restrict__ dth,
-                                                                   int reset_status, ExpTab etab) {
-    __shared__ MaternP smp;
-    __shared__ ExpTab stab;
-    if (threadIdx.x == 0) smp = make_matern_dev(dth ? *dth : th);
-    static_assert(sizeof(ExpTab) % sizeof(float) == 0, "ExpTab words");
-    for (int w = threadIdx.x; w < (int)(sizeof(ExpTab) / sizeof(float)); w += GEN_THREADS)
-        reinterpret_cast<float*>(&stab)[w] = reinterpret_cast<const float*>(&etab)[w];
-    if (reset_status && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < ST_WORDS) L.status[threadIdx.x] = 0;
-    __syncthreads();
+// The entries of columns c0 .. c0 + 31 of tile (i, j), one CTA.
+__device__ __forceinline__ void gen_block(const Layout& L, const double* __restrict__ x,
+                                          const double* __restrict__ y, const MaternP& smp, const ExpTab& stab,
+                                          int i, int j, int c0) {
     const MaternP mp = smp;
-    const int nb = L.nb, p = L.p;
-    int i, j;
-    gen_tile_of(blockIdx.y, p, L.band, i, j);
-    const int c0 = blockIdx.x * GEN_COLS;
+    const int nb = L.nb;
     if (c0 >= nb) return;
     const int cols = min(GEN_COLS, nb - c0);
     __shared__ double cx[GEN_COLS], cy[GEN_COLS];
@@ -153,6 +140,7 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
                 double v;
                 if (!va || !vb) v = (ga == gb) ? 1.0 : 0.0;          // decoupled padding rows
                 else if (ga == gb) v = mp.sigma2 + mp.nugget;
+                else if (i == j && a < c0 + c) v = 0.0;   // upper triangle of a diagonal tile: never read
                 else {
                     const double dx = xa - cx[c], dy = ya - cy[c];
                     const double r = sqrt(dx * dx + dy * dy);
@@ -223,10 +211,81 @@ __global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, con
     }
 }
 
+// Prologue of both generator kernels: theta (from `dth` when given: device
+// memory, for batched evaluations and graph replays; else `th`) and the
+// exponential tables in shared memory; with reset_status the problem's first
+// CTA also clears its status words (the batched path has no separate reset).
+__device__ __forceinline__ void gen_prologue(const Layout& L, const geo_theta& th, const geo_theta* dth,
+                                             bool reset, const ExpTab& etab, MaternP& smp, ExpTab& stab) {
+    if (threadIdx.x == 0) smp = make_matern_dev(dth ? *dth : th);
+    static_assert(sizeof(ExpTab) % sizeof(float) == 0, "ExpTab words");
+    for (int w = threadIdx.x; w < (int)(sizeof(ExpTab) / sizeof(float)); w += GEN_THREADS)
+        reinterpret_cast<float*>(&stab)[w] = reinterpret_cast<const float*>(&etab)[w];
+    if (reset && threadIdx.x < ST_WORDS) L.status[threadIdx.x] = 0;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(GEN_THREADS) matern_tiles_kernel(Layout L, const double* __restrict__ x,
+                                                                   const double* __restrict__ y, geo_theta th,
+                                                                   const geo_theta* __restrict__ dth,
+                                                                   int reset_status, ExpTab etab) {
+    __shared__ MaternP smp;
+    __shared__ ExpTab stab;
+    gen_prologue(L, th, dth, reset_status && blockIdx.x == 0 && blockIdx.y == 0, etab, smp, stab);
+    int i, j;
+    gen_tile_of(blockIdx.y, L.p, L.band, i, j);
+    gen_block(L, x, y, smp, stab, i, j, blockIdx.x * GEN_COLS);
+}
+
+// Every problem of a batch in one launch: the CTAs of problem b are
+// jobs[b].block0 .. jobs[b + 1].block0 - 1 (each problem's grid of the single
+// launch, flattened column chunk fastest), so the slow blocks of one problem
+// run beside the others' instead of one launch after another; theta of
+// problem b from dth[b].
+__global__ void __launch_bounds__(GEN_THREADS) matern_batch_kernel(const ProbDev* __restrict__ probs,
+                                                                   const GenJob* __restrict__ jobs, int nprob,
+                                                                   const geo_theta* __restrict__ dth,
+                                                                   ExpTab etab) {
+    __shared__ MaternP smp;
+    __shared__ ExpTab stab;
+    __shared__ int sb;
+    const long long blk = blockIdx.x;
+    if (threadIdx.x == 0) {   // the job holding this CTA: the last b with block0 <= blk
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (jobs[mid].block0 <= blk) lo = mid;
+            else hi = mid - 1;
+        }
+        sb = lo;
+    }
+    __syncthreads();
+    const int b = sb;
+    const Layout& L = probs[b].L;
+    const long long local = blk - jobs[b].block0;
+    const int ncx = (L.nb + GEN_COLS - 1) / GEN_COLS;
+    gen_prologue(L, geo_theta{}, dth + b, local == 0, etab, smp, stab);
+    int i, j;
+    gen_tile_of((int)(local / ncx), L.p, L.band, i, j);
+    gen_block(L, jobs[b].x, jobs[b].y, smp, stab, i, j, (int)(local % ncx) * GEN_COLS);
+}
+
 cudaError_t launch_matern_tiles(const Layout& L, const double* x, const double* y, const geo_theta& th,
                                 const geo_theta* dth, int reset_status, cudaStream_t s) {
     dim3 grid((L.nb + GEN_COLS - 1) / GEN_COLS, L.p * (L.p + 1) / 2);
     matern_tiles_kernel<<<grid, GEN_THREADS, 0, s>>>(L, x, y, th, dth, reset_status, exp_table());
+    count_launch();
+    return cudaGetLastError();
+}
+
+long long gen_blocks(const Layout& L) {
+    return (long long)((L.nb + GEN_COLS - 1) / GEN_COLS) * ((long long)L.p * (L.p + 1) / 2);
+}
+
+cudaError_t launch_matern_batch(const ProbDev* d_probs, const GenJob* d_jobs, int nprob, long long total_blocks,
+                                const geo_theta* dth, cudaStream_t s) {
+    if (total_blocks < 1 || total_blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    matern_batch_kernel<<<(unsigned)total_blocks, GEN_THREADS, 0, s>>>(d_probs, d_jobs, nprob, dth, exp_table());
     count_launch();
     return cudaGetLastError();
 }

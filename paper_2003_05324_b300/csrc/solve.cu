@@ -191,7 +191,11 @@ __global__ void __launch_bounds__(256) trsv_t_update_kernel(Layout L, int i, dou
     if (lane == 0) w[(size_t)j * nb + c] -= acc;
 }
 
-// zhat_q = sum_a C(||s_new_q - s_a||) alpha_a, one CTA per new point.
+// zhat_q = sum_a C(||s_new_q - s_a||) alpha_a, one CTA per new point.  Under
+// the DST approximation (Section V-B) the sum runs over the observed points
+// whose tile is within `band` tiles of the new point's tile -- the tile of its
+// nearest observed point, the lowest index on a tie -- as the truncated
+// covariance does for the observed points themselves.
 __global__ void __launch_bounds__(256) krige_cross_kernel(Layout L, const double* __restrict__ x,
                                                           const double* __restrict__ y,
                                                           const double* __restrict__ alpha, MaternP mp,
@@ -199,8 +203,49 @@ __global__ void __launch_bounds__(256) krige_cross_kernel(Layout L, const double
                                                           const double* __restrict__ yn, double* __restrict__ zhat) {
     const int q = blockIdx.x, tid = threadIdx.x;
     const double xq = xn[q], yq = yn[q];
+    int lo = 0, hi = L.n;
+    if (L.flags & GEO_FLAG_DST) {
+        double best = INFINITY;
+        int bi = 0x7fffffff;
+        for (int a = tid; a < L.n; a += 256) {   // squares and sum rounded separately (no contraction)
+            const double dx = __dsub_rn(xq, x[a]), dy = __dsub_rn(yq, y[a]);
+            const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            if (r2 < best) {   // a increases: the first minimum is the lowest index
+                best = r2;
+                bi = a;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double b2 = __shfl_down_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+            if (b2 < best || (b2 == best && i2 < bi)) {
+                best = b2;
+                bi = i2;
+            }
+        }
+        __shared__ double sb[8];
+        __shared__ int si[8], home;
+        if ((tid & 31) == 0) {
+            sb[tid >> 5] = best;
+            si[tid >> 5] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double b = sb[0];
+            int i = si[0];
+            for (int w2 = 1; w2 < 8; ++w2)
+                if (sb[w2] < b || (sb[w2] == b && si[w2] < i)) {
+                    b = sb[w2];
+                    i = si[w2];
+                }
+            home = i / L.nb;
+        }
+        __syncthreads();
+        lo = max(0, home - L.band + 1) * L.nb;
+        hi = min(L.n, (home + L.band) * L.nb);
+    }
     double acc = 0.0;
-    for (int a = tid; a < L.n; a += 256) {
+    for (int a = lo + tid; a < hi; a += 256) {
         const double dx = xq - x[a], dy = yq - y[a];
         const double r = sqrt(dx * dx + dy * dy);
         const double c = (r == 0.0) ? mp.sigma2 : matern_fp64(r * mp.inv_beta, mp);

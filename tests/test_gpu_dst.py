@@ -147,3 +147,28 @@ def test_dst_fused_solve_sums_every_block_row(G):
     for _ in range(10):
         l, _, _ = ts.loglik(X, Y, Z, th)
         assert abs(l - want) <= 1e-10 * abs(want)
+
+
+@pytest.mark.parametrize("nb,d,theta", [
+    (200, 1, (1.0, 0.1, 0.5, 0.0)),      # IND: kriging from the home block alone
+    (200, 2, (1.0, 0.03, 0.5, 0.0)),
+    (96, 3, (1.2, 0.02, 1.0, 1e-6)),     # ragged last tile, K_1 path (smallest eigenvalue 0.10)
+])
+def test_dst_krige_matches_oracle(G, nb, d, theta):
+    """Kriging under the DST approximation: the new location's covariances
+    are truncated like the observed ones (kept within d tiles of the tile of
+    its nearest observed point); against oracle.krige_dst to 1e-8, and a new
+    location on an observed one gets its observation back."""
+    x, y, z = grid(40 if nb == 200 else 32)
+    xn, yn = inputs.uniform_points(25, seed=31)
+    xn = np.concatenate([xn, x[[0, 500, len(x) - 1]]])
+    yn = np.concatenate([yn, y[[0, 500, len(x) - 1]]])
+    th = O.Theta(*theta)
+    want = O.krige_dst(x, y, z, th, xn, yn, nb, d)
+    ts = dst_store(G, len(z), nb, d)
+    ts.matern(dev(x), dev(y), G.Theta(*theta))
+    ts.potrf()
+    got = ts.krige(dev(x), dev(y), dev(z), G.Theta(*theta), dev(xn), dev(yn)).cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-8, atol=1e-10 * np.abs(want).max()), np.abs(got - want).max()
+    if theta[3] == 0.0:
+        np.testing.assert_allclose(got[-3:], z[[0, 500, len(x) - 1]], atol=1e-7)
