@@ -1,20 +1,21 @@
 // Off-band (FP32-accurate) update of Algorithm 1 (sgemm) on the tcgen05 tensor
-// cores.  Each FP32 panel row is scaled by a power of two 2^E (|v| 2^-E < 1/2)
-// and cut into three rounded 8-bit integer slices a0, a1, a2 (|a_s| <= 128),
-// stored exactly in BF16 as P0 = a0, P1 = a1 2^-8, P2 = a2 2^-16, so that
-// v = 2^(E-8) (P0 + P1 + P2) to 2^-25 of the row's scale.  Then
-//   C <- C - 2^(E_r+E_c-16) [ sum P0 P0'  +  sum (P1P1' + P0P2' + P2P0' + P0P1' + P1P0') ].
-// The first sum is of integers below 2^23 for K <= 1024, so the tensor cores
+// cores, step-by-step path (GEO_FLAG_STEPWISE).  Each panel row is scaled by a
+// power of two 2^E (|v| 2^-E < 1/2) and cut into rounded 8-bit integer slices
+// a0, a1, ... (|a_s| <= 128; the split writes seven, this update reads the
+// first four), stored exactly in BF16 as P_s = a_s 2^-8s, so that
+// v = 2^(E-8) (P0 + P1 + P2 + P3) to 2^-33 of the row's scale.  Then
+//   C <- C - 2^(E_r+E_c-16) [ P0 P0' + sum over the nine pairs (a, b), 1 <= a + b <= 3, of Pa Pb' ].
+// P0 P0' is a sum of integers below 2^23 for K <= 1024, so the tensor cores
 // accumulate it exactly (their FP32 accumulation truncates; exact sums make that
-// moot); the second, 2^-8 smaller, goes to its own accumulator.  The dropped
-// pairs weigh 2^-24 of the leading one: the update is FP32-accurate and free of
-// the accumulation bias a single truncating accumulator would add.
+// moot); the other pairs, 2^-8 and more smaller, go to a second accumulator.
+// The dropped pairs weigh 2^-32 of the leading one: the update is FP32-accurate
+// and free of the accumulation bias a single truncating accumulator would add.
 #pragma once
 #include "geo_internal.cuh"
 
 namespace geo {
 
-// Write the three BF16 planes of every panel tile (i, k), i > k.
+// Write the BF16 slice planes of every panel tile (i, k), i > k.
 cudaError_t launch_split_panel(const Layout& L, int k, cudaStream_t s);
 
 // Encode the TMA descriptor of the bound planes buffer into t->tmap (host).
