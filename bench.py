@@ -250,11 +250,11 @@ EX_PAIRS = 28                # BF16 slice products per FP64-accurate in-band upd
 # kernel's sources: a changed kernel reports null.  The figure is scaled from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
 # kernel at n = 25,600 (p = 52) by the number of off-band tile updates
-# (p (p^2 - 1) / 6: 23,426 there, 85,320 here): 3.376 MB per update.  The
+# (p (p^2 - 1) / 6: 23,426 there, 85,320 here): 3.380 MB per update.  The
 # per-update figure falls slowly with size (3.71 / 3.57 / 3.38 MB at
 # p = 13 / 29 / 52), so this slightly overstates the full-size traffic.
 DAG_SOURCES = ("dag.cu", "dag.cuh", "tc_common.cuh", "geo_internal.cuh", "ysolve.cuh")
-DAG_TRAFFIC = {"086983db711c7931": (46047660288 + 33044942080) / 23426 * 85320}
+DAG_TRAFFIC = {"bd050c17c86bdaab": (46108520960 + 33065969408) / 23426 * 85320}
 
 
 def dag_source_hash():
