@@ -1028,8 +1028,17 @@ __device__ void g2_worker(const DagArgs& A, G2Smem& S) {
                 // attempt, in a rotation that starts at this CTA's index, so that
                 // no problem's head waits behind another's.  (A solve task of a
                 // failed problem is taken at once and dropped below.)
-                const int yt = A.n_y > 0 ? ld_volatile(y_taken) : 0;
-                if (yt < A.n_y) {
+                int yt = 0;   // solve tasks taken so far, all problems
+                if (A.n_y > 0 && nq == 1) {   // one problem: its head is that count (one load)
+                    const ProbDev& P = prob_of(A, 0);
+                    const int h = ld_volatile(P.yhead);
+                    yt = h;
+                    if (h < A.n_y && (failed(P.L) || y_ready(P, A.yq[h])) && atomicCAS(P.yhead, h, h + 1) == h) {
+                        idx = h;
+                        kind = 2;
+                        break;
+                    }
+                } else if (A.n_y > 0 && (yt = ld_volatile(y_taken)) < A.n_y) {
                     for (int q = 0; q < min(Y_SCAN, nq) && kind < 0; ++q) {
                         const int pid = yrot;
                         yrot = yrot + 1 == nq ? 0 : yrot + 1;
@@ -1875,6 +1884,7 @@ cudaError_t run_potrf_dag(const geo_tiles* t, const Layout& L, const SchedView& 
     A.yq = z ? sv.yq : nullptr;
     A.n_y = z ? sv.geom.n_y : 0;
     bind_counters(A.one, sv.counters + 16);
+    A.one.yhead = sv.counters + 5;   // one problem: the solve head beside the launch's other queue heads
     A.one.y0 = 0;
     A.one.y1 = (int)A.n_y;
     A.probs = nullptr;
