@@ -412,8 +412,12 @@ int geo_batch_release(const void* d_work);
 /* A13, prediction (Section VIII-D; simple kriging reading): with t holding the
  * factor of Sigma(theta) over the observed locations (d_x, d_y, n = t->lay.n)
  * and observations d_z, write d_zhat[m] = Sigma_new,obs Sigma^-1 Z for the m
- * new locations (d_xnew, d_ynew).  d_work: device FP64 scratch of
- * 2 * p * nb doubles.  Asynchronous. */
+ * new locations (d_xnew, d_ynew).  With GEO_FLAG_DST on t (Section V-B) the
+ * factor is that of the truncated covariance, and Sigma_new,obs is truncated
+ * the same way: a new location keeps its covariances with the observed
+ * points whose tile is within `band` tiles of its own tile, the tile of its
+ * nearest observed point (lowest index on a tie).  d_work: device FP64
+ * scratch of 2 * p * nb doubles.  Asynchronous. */
 int geo_krige(const geo_tiles* t, const double* d_x, const double* d_y, const double* d_z,
               geo_theta theta, const double* d_xnew, const double* d_ynew, int m,
               double* d_zhat, double* d_work, void* stream);
