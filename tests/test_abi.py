@@ -174,3 +174,15 @@ def test_mle_journal_validation_without_device_work():
     assert geo.lib.geo_mle(ctypes.byref(t), d, d, d, th, ctypes.byref(o), ctypes.byref(r), None) == -6
     o.journal_len = ctypes.POINTER(ctypes.c_int)()   # journal without a length
     assert geo.lib.geo_mle(ctypes.byref(t), d, d, d, th, ctypes.byref(o), ctypes.byref(r), None) == -6
+
+
+def test_binding_constants_match_the_header():
+    """Every #define GEO_* value of include/geo.h has the same value in the
+    Python binding (the binding restates them for marshalling only)."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "geo.h")).read()
+    found = re.findall(r"^#define (GEO_[A-Z0-9_]+) (-?\d+)(?:LL)?\b", hdr, flags=re.M)
+    assert len(found) >= 17
+    for name, value in found:
+        assert getattr(geo, name) == int(value), name
