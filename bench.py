@@ -290,6 +290,16 @@ def algorithmic_flops(p, nb, band):
     return f64, f64u, f32, lp
 
 
+def tensor_work_band1(n, nb):
+    """Algorithmic tensor-core work (BF16-rate flops) of one band-1
+    factorization with the in-band updates on the tensor cores, in closed form
+    (the counts of algorithmic_flops at band 1): p (p - 1) / 2 dsyrk of nb^3
+    flops at EX_PAIRS products and C(p, 3) off-band updates of 2 nb^3 at
+    TC_PAIRS products."""
+    p = -(-n // nb)
+    return (p * (p - 1) / 2.0) * nb ** 3 * EX_PAIRS + (p * (p - 1) * (p - 2) / 6.0) * 2.0 * nb ** 3 * TC_PAIRS
+
+
 def measured_hbm_gbs():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -487,6 +497,17 @@ def run_batch(geo, dev, rank=0, world=1):
             completion[todo[q]] = t_total + done[q]
         stages.append({"band": band if band < 10 ** 6 else "all FP64", "problems": len(todo), "factored": len(ok),
                        "ms": statistics.median(ms), "p99_ms": max(ms)})
+        if band == 1 and ok:
+            # tensor roofline of the band-1 launch: the factored problems'
+            # algorithmic tensor work over the time from the launch's start to
+            # the last of their completions (the failed ones' partial work is
+            # not counted: a lower bound on the achieved rate)
+            work = sum(tensor_work_band1(int(probs[todo[q]]["z"].shape[0]), nb) for q in ok)
+            t_dag = max(done[q] for q in ok) / 1000.0
+            pk, src = measured_peaks()
+            stages[-1]["tensor_roofline"] = {"bound": "tensor", "work_flops": work, "dag_ms": t_dag * 1e3,
+                                             "achieved": work / t_dag / 1e12, "peak": pk, "unit": "TFLOP/s",
+                                             "frac": work / t_dag / 1e12 / pk, "peak_source": "bf16 " + src}
         t_total += statistics.median(ms)
         todo = [todo[q] for q in range(len(todo)) if q not in set(ok)]
     D = geo.Batch([dict(pr, nb=nb, band=10 ** 6) for pr in probs], device=dev)

@@ -143,3 +143,14 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["n"] == bench.CPU_SAMPLE_M ** 2
+
+
+def test_batch_tensor_work_closed_form_matches_the_task_counts():
+    """The batch roofline's closed-form tensor work of a band-1 factorization
+    equals the task-by-task count the single-problem roofline uses."""
+    import bench
+    for p in (1, 2, 3, 5, 9, 20):
+        nb = 128
+        f64, f64u, f32, lp = bench.algorithmic_flops(p, nb, 1)
+        want = lp * bench.TC_PAIRS + f64u * bench.EX_PAIRS
+        assert abs(bench.tensor_work_band1(p * nb - 3, nb) - want) <= 1e-9 * max(1.0, want)
