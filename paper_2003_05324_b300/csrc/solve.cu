@@ -241,8 +241,9 @@ __global__ void __launch_bounds__(256) krige_cross_kernel(Layout L, const double
             home = i / L.nb;
         }
         __syncthreads();
-        lo = max(0, home - L.band + 1) * L.nb;
-        hi = min(L.n, (home + L.band) * L.nb);
+        const int b = min(L.band, L.p);   // (a band past p keeps every tile)
+        lo = max(0, home - b + 1) * L.nb;
+        hi = min(L.n, (home + b) * L.nb);
     }
     double acc = 0.0;
     for (int a = lo + tid; a < hi; a += 256) {
