@@ -406,8 +406,8 @@ def mle(x, y, z, theta0: Theta, nb: int, band: int, lp_mode: int = GEO_LP_SPLIT_
 
 
 class Batch:
-    """Many log-likelihood problems evaluated through one persistent
-    factorization launch (geo_loglik_batch).
+    """Many log-likelihood problems evaluated through one generator launch and
+    one persistent factorization launch (geo_loglik_batch).
 
     problems: list of dicts with device tensors x, y, z (Morton-ordered) and
     optional nb (default 128), band (default 1), flags, or an existing
@@ -415,8 +415,8 @@ class Batch:
     workspace and the per-problem theta buffer are allocated once; each
     evaluation only enqueues work, so `capture()` can record it in a CUDA graph
     and `replay(thetas)` re-runs it with new parameters.  ctas: run the
-    factorization launch on that many SMs (0: all, cooperative), leaving the
-    others to launches on other streams.
+    factorization launch on that many SMs (0: all, cooperative; otherwise at
+    least GEO_MIN_CTAS), leaving the others to launches on other streams.
     """
 
     def __init__(self, problems, nb: int = 128, band: int = 1, device="cuda", ctas: int = 0):
